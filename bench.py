@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 Yee FDTD step (one JSON line on rank 0).
+
+Workload (default): a 512^3-cell PEC cavity, FP32 storage, background eps_r = 1
+plus 32 seeded dielectric spheres (radius 8-40 cells, eps_r in {2.25, 4.0}),
+mu_r = 1, dt = 0.5/sqrt(3), uniform[-1, 1) random initial fields.  One bench
+step is one solve of 200 leapfrog steps followed by the FP64 energy check.
+
+  value       Gcell-updates/s = cells * 200 * steps * ranks / time, inputs resident in HBM
+  e2e         the same, with the host->device load of the fields (pinned memory) and the
+              device->host read of the energy inside every timed step
+  roofline    fused step kernel: algorithmic bytes per launch / mean launch time vs measured HBM copy peak
+  cpu_baseline  the FP64 oracle (OpenMP, all host cores) on a bounded sample of the workload
+
+Multi-GPU (torchrun): each rank solves its own cavity (independent replicas, no
+collective on the data path); value sums all ranks over the max-over-ranks time.
+`--impl reference` times the oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import cavity_inputs as ci  # noqa: E402
+
+WORKLOADS = {
+    # name: (nx, ny, nz, leapfrog steps per bench step, storage, sphere seed, field seed)
+    "single512": dict(n=(512, 512, 512), steps=200, storage=0, sphere_seed=1, field_seed=2, spheres=32),
+    "precision384_f16": dict(n=(384, 384, 384), steps=1000, storage=1, sphere_seed=3, field_seed=4, spheres=32),
+    "precision384_bf16": dict(n=(384, 384, 384), steps=1000, storage=2, sphere_seed=3, field_seed=4, spheres=32),
+}
+# Launch configuration of the fused kernel that the bench times (the full-size parity test uses the same).
+BENCH_TUNING = dict(kernel=2, tile_y=8, stages=4, zchunk=0, ctas_per_sm=0, use_graph=1)
+ID_BYTES = 1  # material id per cell
+
+# DRAM traffic per fused launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the
+# SHA-256 of the kernel source it was measured on; ignored (reported null) once the source changes.
+MEASURED_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    p = os.path.join(ROOT, "paper_2504_09118_gb300", "csrc", "k_fused.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def sphere_coefs(w):
+    nx, ny, nz = w["n"]
+    sph = ci.sphere_list(w["sphere_seed"], w["spheres"], (nx, ny, nz), 8.0, 40.0)
+    return ci.sphere_coefficients(sph, nx, ny, nz, ci.COURANT_HALF_DT)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str | None):
+        self.proc = None
+        self.path = path or os.path.join("/tmp", f"fdtd_clocks_{os.getpid()}.csv")
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        try:
+            self.fh.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            rows = []
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(w, budget_s: float = 12.0):
+    """Time the FP64 oracle (OpenMP build, all host cores) on a bounded z-slab of the workload."""
+    import oracle
+    nx, ny, _ = w["n"]
+    nzs = 16
+    ce, ch = (None, None)
+    sph = ci.sphere_list(w["sphere_seed"], w["spheres"], w["n"], 8.0, 40.0)
+    ce_s, ch_s = ci.sphere_coefficients(sph, nx, ny, nzs, ci.COURANT_HALF_DT)
+    f = oracle.as_f64(ci.random_fields(w["field_seed"], nx, ny, nzs))
+    ce64 = [c.astype(np.float64) for c in ce_s]
+    t0 = time.perf_counter()
+    oracle.step(f, ce64, ch_s, 1, omp=True)
+    one = time.perf_counter() - t0
+    steps = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.step(f, ce64, ch_s, steps, omp=True)
+    dt = time.perf_counter() - t0
+    rate = nx * ny * nzs * steps / dt / 1e9
+    return {"value": round(rate, 4), "unit": "Gcell-updates/s", "cores": oracle.threads(True), "kind": "oracle",
+            "sample": f"{nx}x{ny}x{nzs} slab of the {w['n'][0]}x{w['n'][1]}x{w['n'][2]} workload "
+                      f"(same sphere layout), FP64 OpenMP oracle, {steps} steps in {dt:.1f} s"}
+
+
+def run_reference(args, w, wname):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    nx, ny, nz = w["n"]
+    nzs = 16
+    sph = ci.sphere_list(w["sphere_seed"], w["spheres"], w["n"], 8.0, 40.0)
+    ce_s, ch_s = ci.sphere_coefficients(sph, nx, ny, nzs, ci.COURANT_HALF_DT)
+    ce64 = [c.astype(np.float64) for c in ce_s]
+    f = oracle.as_f64(ci.random_fields(w["field_seed"], nx, ny, nzs))
+    per_step = 2  # oracle leapfrog steps per bench step: a bounded sample of the solve
+    for _ in range(args.warmup):
+        oracle.step(f, ce64, ch_s, 1, omp=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(f, ce64, ch_s, per_step, omp=True)
+        oracle.energy(f, ce64, ch_s, ci.COURANT_HALF_DT)
+    dt = time.perf_counter() - t0
+    val = nx * ny * nzs * per_step * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": "Gcell-updates/s", "value": round(val, 4), "unit": "Gcell-updates/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "cells": [nx, ny, nz], "sample_cells": [nx, ny, nzs],
+                       "leapfrog_steps_per_bench_step": per_step},
+            "cpu_baseline": {"value": round(val, 4), "unit": "Gcell-updates/s", "cores": oracle.threads(True),
+                             "kind": "oracle", "sample": f"{nx}x{ny}x{nzs} slab, {per_step} FP64 steps + energy per bench step"},
+            "e2e": {"value": round(val, 4), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="single512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clocks-csv", default=None)
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w, args.workload)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2504_09118_gb300 import Cavity, binding
+
+    nx, ny, nz = w["n"]
+    cells = nx * ny * nz
+    per = w["steps"]
+    ce, ch = sphere_coefs(w)
+    fields = ci.random_fields(w["field_seed"] + rank, nx, ny, nz)
+    stream = torch.cuda.Stream()
+    cav = Cavity(nx, ny, nz, ci.COURANT_HALF_DT, 1.0, ce, ch, w["storage"], stream)
+    cav.tune(**BENCH_TUNING)
+    cav.set_fields(fields)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def bench_step():
+        cav.step(per)
+        return cav.energy()
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k_ms = []
+    with ClockSampler(local, args.clocks_csv) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ka.record(stream)
+            cav.step(per)
+            kb.record(stream)
+            cav.energy()           # synchronises; part of the timed step (FP64 check, a7)
+            k_ms.append(ka.elapsed_time(kb))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = cells * per * args.steps * ws / (ms / 1e3) / 1e9
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel (the fused step): algorithmic bytes per launch / mean launch time
+    esz = 4 if w["storage"] == 0 else 2
+    alg_bytes = cells * (12 * esz + ID_BYTES)
+    launch_s = statistics.mean(k_ms) / 1e3 / per
+    achieved = alg_bytes / launch_s / 1e9
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
+    tr = MEASURED_TRAFFIC.get((args.workload, kernel_source_hash()))
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": tr,
+                "peak_source": "measured" if peaks else "fallback",
+                "alg_bytes_per_launch": alg_bytes, "mean_launch_us": round(launch_s * 1e6, 2)}
+
+    # end to end through the C ABI with host buffers: H2D of the fields + solve + D2H of the energy
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(a).pin_memory() for a in fields]
+        host = [p.numpy() for p in pinned]
+        for _ in range(1):
+            cav.set_fields(host)
+            bench_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            cav.set_fields(host)
+            bench_step()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": round(cells * per * args.steps * ws / e2e_s / 1e9, 3), "unit": "Gcell-updates/s",
+               "h2d_bytes_per_step": int(sum(a.nbytes for a in host)), "d2h_bytes_per_step": 8}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+    if rank == 0:
+        line = {"metric": "Gcell-updates/s", "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {0: "f32", 1: "f16-storage/f32-math", 2: "bf16-storage/f32-math"}[w["storage"]],
+                "data": "synthetic",
+                "config": {"workload": args.workload, "cells": [nx, ny, nz], "leapfrog_steps_per_bench_step": per,
+                           "coefficients": "32 dielectric spheres, 1-byte material id", "parallelism": f"replicas x{ws}",
+                           "l2": "inputs larger than L2 (6.4 GB of fields per step)",
+                           "tuning": BENCH_TUNING, "hbm_fraction_of_roofline": round(achieved / peak, 4)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": args.steps * (per + 2)}
+        print(json.dumps(line), flush=True)
+    cav.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * fdtd.h - C ABI of the GB300 (sm_103a) Yee FDTD library (libfdtd.so).
+ *
+ * The library advances Maxwell's curl equations (J = 0) on a perfectly
+ * conducting (PEC) box cavity with the Yee leapfrog scheme of He, Andersson and
+ * Markidis, "Optimizing FDTD Solvers for Electromagnetics: A Compiler-Guided
+ * Approach with High-Level Tensor Abstractions" (arXiv 2504.09118):
+ *   Sec. 2, Eq. 1   - the curl equations;
+ *   Sec. 2, Eq. 2   - the staggered update of the six components;
+ *   Sec. 2.1, Listing 1 - one step = H from curl E, boundary, E from curl H, boundary;
+ *   Sec. 4          - the benchmark workload: a PEC cavity from a random state.
+ *
+ * Units and conventions
+ *   nx, ny, nz are cell counts; dx = dy = dz = dx.  State after n steps is
+ *   (H^{n-1/2}, E^n).  One step:
+ *     H -= ch * curl E   (all H in their Yee extent; normal H on a face is unchanged)
+ *     E += ce * curl H   (E tangential to a face stays exactly 0: PEC)
+ *   ce = dt/(eps*dx) at each E position, ch = dt/(mu*dx) at each H position.
+ *
+ * Canonical layout (every field and coefficient array crossing this ABI)
+ *   float[(nz+1)*(ny+1)*(nx+1)], C order, x fastest: element (i,j,k) is at
+ *   ((k*(ny+1) + j)*(nx+1) + i).  Component c at (i,j,k) sits at its Yee position
+ *     Ex (i+1/2, j, k)     i<nx,  j<=ny, k<=nz
+ *     Ey (i, j+1/2, k)     i<=nx, j<ny,  k<=nz
+ *     Ez (i, j, k+1/2)     i<=nx, j<=ny, k<nz
+ *     Hx (i, j+1/2, k+1/2) i<=nx, j<ny,  k<nz
+ *     Hy (i+1/2, j, k+1/2) i<nx,  j<=ny, k<nz
+ *     Hz (i+1/2, j+1/2, k) i<nx,  j<ny,  k<=nz
+ *   Entries outside a component's extent are ignored on input and written 0
+ *   on output.  Field arrays are passed as f[6] = {Ex, Ey, Ez, Hx, Hy, Hz}.
+ *
+ * Errors: every int-returning call returns FDTD_OK (0) or a negative status
+ * and never aborts.  A failed call leaves a message in fdtd_last_error(ctx).
+ * Device-side errors (a bounded wait that ran out) are latched in a device
+ * status word and reported by the next call that synchronises the stream.
+ *
+ * Threading: a context (or batch) must not be used from two host threads at once.
+ */
+#ifndef FDTD_H
+#define FDTD_H
+
+#if defined(__GNUC__)
+#define FDTD_API __attribute__((visibility("default")))
+#else
+#define FDTD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdtd_ctx fdtd_ctx;
+typedef struct fdtd_batch fdtd_batch;
+
+/* Storage precision of the fields in device memory.  Arithmetic is always FP32;
+ * FP16/BF16 store each component scaled by a power of two s_c chosen at
+ * fdtd_set_fields (s_c = 2^(8 - ceil(log2 max|F_c|))), rounded to nearest even. */
+enum fdtd_storage { FDTD_F32 = 0, FDTD_F16 = 1, FDTD_BF16 = 2 };
+
+enum fdtd_status {
+    FDTD_OK = 0,
+    FDTD_ERR_ARG = -1,       /* invalid argument (NULL, size, enum, mismatched batch member) */
+    FDTD_ERR_OOM = -2,       /* device allocation failed */
+    FDTD_ERR_CUDA = -3,      /* a CUDA runtime/driver call failed */
+    FDTD_ERR_TIMEOUT = -4,   /* a kernel's bounded wait ran out; fields of that step are undefined */
+    FDTD_ERR_STATE = -5,     /* call not valid in the current state (e.g. step before set_fields) */
+    FDTD_ERR_UNSTABLE = -6   /* Courant bound violated: max sqrt(3 ce ch) > 1 */
+};
+
+/* Step kernels (fdtd_tuning.kernel). */
+enum fdtd_kernel {
+    FDTD_KERNEL_AUTO = 0,    /* fused kernel with the library's default tile */
+    FDTD_KERNEL_SIMPLE = 1,  /* two launches per step (H, then E), one thread per cell; unfused baseline */
+    FDTD_KERNEL_FUSED = 2    /* one TMA-pipelined launch per step: H then E fused in a z-march */
+};
+
+/* Launch configuration of the step kernel; zero fields take the default. */
+typedef struct fdtd_tuning {
+    int kernel;       /* enum fdtd_kernel */
+    int tile_y;       /* fused: cells per tile along y (4, 8 or 16); x tile is fixed at 64 */
+    int zchunk;       /* fused: planes per tile along z (>= 1); 0 = choose for load balance */
+    int ctas_per_sm;  /* fused: persistent CTAs per SM (1 or 2); 0 = as many as fit */
+    int stages;       /* fused: TMA pipeline depth in planes (3..8, lowered to fit shared memory); 0 = default */
+    int use_graph;    /* 1 = replay fdtd_step / fdtd_batch_step through a captured CUDA graph */
+} fdtd_tuning;
+
+/*
+ * fdtd_create - allocate a cavity of nx*ny*nz cells on the current device.
+ *   dt, dx      time step and cell size (> 0).
+ *   ce[3]       host canonical arrays of dt/(eps*dx) at the Ex, Ey, Ez
+ *               positions, or NULL for vacuum (dt/dx everywhere).
+ *   ch[3]       host canonical arrays of dt/(mu*dx) at the Hx, Hy, Hz
+ *               positions, or NULL for vacuum.
+ *   storage     enum fdtd_storage.
+ *   cuda_stream cudaStream_t to issue all work on (NULL = legacy default stream).
+ * The library copies the coefficients (compressing them to a one-byte material
+ * id per cell plus a table when at most 256 distinct per-cell tuples occur)
+ * and owns all device memory until fdtd_destroy.  Fields start at zero.
+ * Returns FDTD_ERR_UNSTABLE (and no context) when some cell has
+ * sqrt(3 * ce * ch) > 1 for a co-located pair, FDTD_ERR_ARG for sizes < 1 or
+ * > 32768 or non-positive coefficients.  On error *out is NULL.
+ */
+FDTD_API int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx,
+                const float *const ce[3], const float *const ch[3], int storage, void *cuda_stream);
+
+/*
+ * fdtd_set_fields - load the state (H^{n-1/2}, E^n) and reset the step counter.
+ *   f[6]       canonical FP32 arrays; host pointers when on_device == 0, CUDA
+ *              device pointers when on_device == 1.  Read during the call only.
+ * Tangential E on the faces is written as 0 whatever the input holds.
+ * Synchronises the stream before returning.
+ */
+FDTD_API int fdtd_set_fields(fdtd_ctx *ctx, const float *const f[6], int on_device);
+
+/*
+ * fdtd_step - advance nsteps >= 0 leapfrog steps (Listing 1 order), asynchronously
+ * on the context's stream.  Launch errors are returned here; device-side errors
+ * at the next synchronising call.
+ */
+FDTD_API int fdtd_step(fdtd_ctx *ctx, int nsteps);
+
+/*
+ * fdtd_get_fields - write the current state into f[6] (canonical FP32; host or
+ * device pointers as on_device says).  Entries outside each extent are 0.
+ * Synchronises the stream; returns a latched device error if one occurred.
+ */
+FDTD_API int fdtd_get_fields(fdtd_ctx *ctx, float *const f[6], int on_device);
+
+/*
+ * fdtd_energy - discrete Yee energy of the current state, accumulated in FP64:
+ *   W^n = 1/2 sum eps |E^n|^2 + 1/2 sum mu H^{n-1/2} . H^{n+1/2},
+ *   eps = dt/(ce dx), mu = dt/(ch dx), cell volume 1, with H^{n+1/2} formed on the
+ *   fly.  It is the invariant of the Eq. 2 leapfrog on a lossless PEC cavity.
+ * Synchronises the stream.
+ */
+FDTD_API int fdtd_energy(fdtd_ctx *ctx, double *W);
+
+/*
+ * fdtd_divergence - L2 norms (FP64) of the discrete divergences:
+ *   divE at interior nodes: sum_c E_c/ce_c (node) - E_c/ce_c (node - e_c);
+ *   divH at every cell:     sum_c H_c/ch_c (cell + e_c) - H_c/ch_c (cell).
+ * Both are invariant under exact Yee stepping.  Synchronises the stream.
+ */
+FDTD_API int fdtd_divergence(fdtd_ctx *ctx, double *divE_l2, double *divH_l2);
+
+/* fdtd_sync - wait for the context's stream; returns a latched device error, if any. */
+FDTD_API int fdtd_sync(fdtd_ctx *ctx);
+
+/* fdtd_set_tuning - choose the step kernel and its launch shape (NULL = defaults). */
+FDTD_API int fdtd_set_tuning(fdtd_ctx *ctx, const fdtd_tuning *t);
+
+/* fdtd_steps_done - steps taken since the last fdtd_set_fields (-1 for a NULL ctx). */
+FDTD_API long long fdtd_steps_done(const fdtd_ctx *ctx);
+
+/* fdtd_device_bytes - device memory the context holds (fields, ping-pong copy, coefficients). */
+FDTD_API long long fdtd_device_bytes(const fdtd_ctx *ctx);
+
+/* fdtd_destroy - free the context and its device memory (synchronises first). NULL is a no-op. */
+FDTD_API void fdtd_destroy(fdtd_ctx *ctx);
+
+/* fdtd_last_error - message of the last failed call on ctx (or of the last
+ * failed fdtd_create when ctx is NULL); valid until the next call on ctx. */
+FDTD_API const char *fdtd_last_error(const fdtd_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent cavities advanced by one persistent launch per
+ * step over a packed list of equal-size tiles (all members must share the
+ * storage precision and stream).  A member keeps its own fields; adding or
+ * removing members between steps is allowed (continuous batching).
+ * ------------------------------------------------------------------------ */
+
+/* fdtd_batch_create - empty batch for members of the given storage, on cuda_stream. */
+FDTD_API int fdtd_batch_create(fdtd_batch **out, int storage, void *cuda_stream);
+
+/* fdtd_batch_add - add a cavity (after its fdtd_set_fields); it keeps its state and step count. */
+FDTD_API int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *ctx);
+
+/* fdtd_batch_remove - remove a member; it can be stepped or read on its own afterwards. */
+FDTD_API int fdtd_batch_remove(fdtd_batch *b, fdtd_ctx *ctx);
+
+/* fdtd_batch_step - advance every member nsteps steps, asynchronously on the batch stream. */
+FDTD_API int fdtd_batch_step(fdtd_batch *b, int nsteps);
+
+/* fdtd_batch_set_tuning - launch shape for the batch kernel (kernel must be FUSED or AUTO). */
+FDTD_API int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t);
+
+/* fdtd_batch_size - number of members (-1 for NULL). */
+FDTD_API int fdtd_batch_size(const fdtd_batch *b);
+
+/* fdtd_batch_sync - wait for the batch stream; returns a latched device error, if any. */
+FDTD_API int fdtd_batch_sync(fdtd_batch *b);
+
+/* fdtd_batch_destroy - release the batch (members are not destroyed). */
+FDTD_API void fdtd_batch_destroy(fdtd_batch *b);
+
+/* fdtd_batch_last_error - message of the last failed batch call. */
+FDTD_API const char *fdtd_batch_last_error(const fdtd_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics
+ * ------------------------------------------------------------------------ */
+
+/* fdtd_debug_inject_timeout - make the next fused step's first TMA stage never
+ * be issued so that its bounded wait runs out after about limit_us microseconds;
+ * the step then returns FDTD_ERR_TIMEOUT at the next synchronising call and the
+ * context stays usable (its fields are undefined until the next set_fields).
+ * Fault injection on the host side of a wait: no GPU fault is involved. */
+FDTD_API int fdtd_debug_inject_timeout(fdtd_ctx *ctx, int limit_us);
+
+/* fdtd_version - library version string. */
+FDTD_API const char *fdtd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDTD_H */

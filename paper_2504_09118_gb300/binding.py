@@ -1,0 +1,295 @@
+"""ctypes binding of libfdtd.so: the C ABI of include/fdtd.h under the same names.
+
+Argument marshalling only.  Every computation happens in the CUDA library;
+when the library cannot be built or loaded, importing a function raises.
+PyTorch is optional here: device tensors are accepted wherever the C ABI takes
+device pointers (on_device=1), and a torch.cuda.Stream (or a raw handle) may be
+passed as the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FDTD_F32, FDTD_F16, FDTD_BF16 = 0, 1, 2
+FDTD_OK, FDTD_ERR_ARG, FDTD_ERR_OOM, FDTD_ERR_CUDA, FDTD_ERR_TIMEOUT, FDTD_ERR_STATE, FDTD_ERR_UNSTABLE = (
+    0, -1, -2, -3, -4, -5, -6)
+FDTD_KERNEL_AUTO, FDTD_KERNEL_SIMPLE, FDTD_KERNEL_FUSED = 0, 1, 2
+STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT", -5: "ERR_STATE",
+                -6: "ERR_UNSTABLE"}
+
+# Every entry point declared in include/fdtd.h (checked against the header by the tests).
+EXPORTS = (
+    "fdtd_create", "fdtd_set_fields", "fdtd_step", "fdtd_get_fields", "fdtd_energy", "fdtd_divergence",
+    "fdtd_sync", "fdtd_set_tuning", "fdtd_steps_done", "fdtd_device_bytes", "fdtd_destroy", "fdtd_last_error",
+    "fdtd_batch_create", "fdtd_batch_add", "fdtd_batch_remove", "fdtd_batch_step", "fdtd_batch_set_tuning",
+    "fdtd_batch_size", "fdtd_batch_sync", "fdtd_batch_destroy", "fdtd_batch_last_error",
+    "fdtd_debug_inject_timeout", "fdtd_version",
+)
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fdtd_tuning(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("stages", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfdtd.so (building it first when the sources are newer and nvcc exists)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not _build.up_to_date():
+                try:
+                    _build.build()
+                except Exception as e:   # no silent fallback: the CUDA library is the only implementation
+                    if not os.path.exists(_build.LIB):
+                        raise ImportError(f"libfdtd.so is missing and could not be built: {e}") from e
+            L = ctypes.CDLL(_build.LIB)
+            vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+            L.fdtd_create.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, vp, vp, i, vp]
+            L.fdtd_set_fields.argtypes = [vp, vp, i]
+            L.fdtd_step.argtypes = [vp, i]
+            L.fdtd_get_fields.argtypes = [vp, vp, i]
+            L.fdtd_energy.argtypes = [vp, ctypes.POINTER(d)]
+            L.fdtd_divergence.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
+            L.fdtd_sync.argtypes = [vp]
+            L.fdtd_set_tuning.argtypes = [vp, ctypes.POINTER(fdtd_tuning)]
+            L.fdtd_steps_done.argtypes = [vp]
+            L.fdtd_steps_done.restype = ll
+            L.fdtd_device_bytes.argtypes = [vp]
+            L.fdtd_device_bytes.restype = ll
+            L.fdtd_destroy.argtypes = [vp]
+            L.fdtd_destroy.restype = None
+            L.fdtd_last_error.argtypes = [vp]
+            L.fdtd_last_error.restype = ctypes.c_char_p
+            L.fdtd_batch_create.argtypes = [ctypes.POINTER(vp), i, vp]
+            L.fdtd_batch_add.argtypes = [vp, vp]
+            L.fdtd_batch_remove.argtypes = [vp, vp]
+            L.fdtd_batch_step.argtypes = [vp, i]
+            L.fdtd_batch_set_tuning.argtypes = [vp, ctypes.POINTER(fdtd_tuning)]
+            L.fdtd_batch_size.argtypes = [vp]
+            L.fdtd_batch_sync.argtypes = [vp]
+            L.fdtd_batch_destroy.argtypes = [vp]
+            L.fdtd_batch_destroy.restype = None
+            L.fdtd_batch_last_error.argtypes = [vp]
+            L.fdtd_batch_last_error.restype = ctypes.c_char_p
+            L.fdtd_debug_inject_timeout.argtypes = [vp, i]
+            L.fdtd_version.restype = ctypes.c_char_p
+            _LIB = L
+        return _LIB
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    h = getattr(stream, "cuda_stream", None)
+    if h is None:
+        raise TypeError("stream must be a torch.cuda.Stream or an int handle")
+    return int(h) or None
+
+
+def _check(ctx, rc: int) -> None:
+    if rc != FDTD_OK:
+        msg = lib().fdtd_last_error(ctx)
+        raise FdtdError(rc, msg.decode() if msg else "")
+
+
+def _host_f32(a, shape):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if a.shape != shape and a.size != int(np.prod(shape)):
+        raise ValueError(f"array of shape {a.shape} does not match canonical shape {shape}")
+    return a
+
+
+def _ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*ptrs)
+
+
+def fdtd_create(nx: int, ny: int, nz: int, dt: float, dx: float = 1.0, ce=None, ch=None,
+                storage: int = FDTD_F32, stream=None):
+    """Create a cavity; ce/ch are None or three canonical host arrays.  Returns the context handle."""
+    L = lib()
+    shape = (nz + 1, ny + 1, nx + 1)
+    keep = []
+
+    def arr3(c):
+        if c is None:
+            return None
+        if np.isscalar(c):
+            c = [c, c, c]
+        vs = [np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float32), shape)) for v in c]
+        keep.extend(vs)
+        return _ptr_array([v.ctypes.data for v in vs])
+
+    ce_p, ch_p = arr3(ce), arr3(ch)
+    out = ctypes.c_void_p()
+    rc = L.fdtd_create(ctypes.byref(out), int(nx), int(ny), int(nz), float(dt), float(dx),
+                       ctypes.cast(ce_p, ctypes.c_void_p) if ce_p is not None else None,
+                       ctypes.cast(ch_p, ctypes.c_void_p) if ch_p is not None else None,
+                       int(storage), _stream_handle(stream))
+    _check(None, rc)
+    return out.value
+
+
+def _field_ptrs(fields, shape, on_device: bool, writable: bool):
+    if len(fields) != 6:
+        raise ValueError("need six fields Ex, Ey, Ez, Hx, Hy, Hz")
+    if on_device:
+        ptrs = []
+        for t in fields:
+            if str(t.dtype) != "torch.float32" or not t.is_contiguous() or t.numel() != int(np.prod(shape)):
+                raise ValueError("device fields must be contiguous float32 tensors of the canonical size")
+            ptrs.append(t.data_ptr())
+        return ptrs, fields
+    arrs = []
+    for a in fields:
+        if writable:
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous and a.size == int(np.prod(shape))):
+                raise ValueError("host output fields must be C-contiguous float32 arrays of the canonical size")
+            arrs.append(a)
+        else:
+            arrs.append(_host_f32(a, shape))
+    return [a.ctypes.data for a in arrs], arrs
+
+
+def fdtd_set_fields(ctx, fields, on_device: int = 0, dims=None) -> None:
+    nx, ny, nz = dims if dims is not None else _dims_of(fields)
+    ptrs, keep = _field_ptrs(fields, (nz + 1, ny + 1, nx + 1), bool(on_device), False)
+    _check(ctx, lib().fdtd_set_fields(ctx, ctypes.cast(_ptr_array(ptrs), ctypes.c_void_p), int(on_device)))
+    del keep
+
+
+def fdtd_get_fields(ctx, fields, on_device: int = 0, dims=None) -> None:
+    nx, ny, nz = dims if dims is not None else _dims_of(fields)
+    ptrs, keep = _field_ptrs(fields, (nz + 1, ny + 1, nx + 1), bool(on_device), True)
+    _check(ctx, lib().fdtd_get_fields(ctx, ctypes.cast(_ptr_array(ptrs), ctypes.c_void_p), int(on_device)))
+    del keep
+
+
+def _dims_of(fields):
+    s = tuple(fields[0].shape)
+    if len(s) != 3:
+        raise ValueError("pass dims=(nx, ny, nz) for flat field arrays")
+    return s[2] - 1, s[1] - 1, s[0] - 1
+
+
+def fdtd_step(ctx, nsteps: int) -> None:
+    _check(ctx, lib().fdtd_step(ctx, int(nsteps)))
+
+
+def fdtd_energy(ctx) -> float:
+    w = ctypes.c_double()
+    _check(ctx, lib().fdtd_energy(ctx, ctypes.byref(w)))
+    return w.value
+
+
+def fdtd_divergence(ctx) -> tuple[float, float]:
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().fdtd_divergence(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def fdtd_sync(ctx) -> None:
+    _check(ctx, lib().fdtd_sync(ctx))
+
+
+def fdtd_set_tuning(ctx, kernel=0, tile_y=0, zchunk=0, ctas_per_sm=0, stages=0, use_graph=0) -> None:
+    t = fdtd_tuning(kernel, tile_y, zchunk, ctas_per_sm, stages, use_graph)
+    _check(ctx, lib().fdtd_set_tuning(ctx, ctypes.byref(t)))
+
+
+def fdtd_steps_done(ctx) -> int:
+    return int(lib().fdtd_steps_done(ctx))
+
+
+def fdtd_device_bytes(ctx) -> int:
+    return int(lib().fdtd_device_bytes(ctx))
+
+
+def fdtd_destroy(ctx) -> None:
+    if ctx:
+        lib().fdtd_destroy(ctx)
+
+
+def fdtd_last_error(ctx=None) -> str:
+    m = lib().fdtd_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def fdtd_debug_inject_timeout(ctx, limit_us: int) -> None:
+    _check(ctx, lib().fdtd_debug_inject_timeout(ctx, int(limit_us)))
+
+
+def fdtd_version() -> str:
+    return lib().fdtd_version().decode()
+
+
+# ---------------------------------------------------------------- batches
+def _bcheck(b, rc):
+    if rc != FDTD_OK:
+        m = lib().fdtd_batch_last_error(b)
+        raise FdtdError(rc, m.decode() if m else "")
+
+
+def fdtd_batch_create(storage: int = FDTD_F32, stream=None):
+    out = ctypes.c_void_p()
+    rc = lib().fdtd_batch_create(ctypes.byref(out), int(storage), _stream_handle(stream))
+    if rc != FDTD_OK:
+        raise FdtdError(rc, "fdtd_batch_create failed")
+    return out.value
+
+
+def fdtd_batch_add(b, ctx) -> None:
+    _bcheck(b, lib().fdtd_batch_add(b, ctx))
+
+
+def fdtd_batch_remove(b, ctx) -> None:
+    _bcheck(b, lib().fdtd_batch_remove(b, ctx))
+
+
+def fdtd_batch_step(b, nsteps: int) -> None:
+    _bcheck(b, lib().fdtd_batch_step(b, int(nsteps)))
+
+
+def fdtd_batch_set_tuning(b, kernel=0, tile_y=0, zchunk=0, ctas_per_sm=0, stages=0, use_graph=0) -> None:
+    t = fdtd_tuning(kernel, tile_y, zchunk, ctas_per_sm, stages, use_graph)
+    _bcheck(b, lib().fdtd_batch_set_tuning(b, ctypes.byref(t)))
+
+
+def fdtd_batch_size(b) -> int:
+    return int(lib().fdtd_batch_size(b))
+
+
+def fdtd_batch_sync(b) -> None:
+    _bcheck(b, lib().fdtd_batch_sync(b))
+
+
+def fdtd_batch_destroy(b) -> None:
+    if b:
+        lib().fdtd_batch_destroy(b)
+
+
+def fdtd_batch_last_error(b) -> str:
+    m = lib().fdtd_batch_last_error(b)
+    return m.decode() if m else ""

@@ -1,0 +1,69 @@
+"""Cavity: an owning Python handle around one fdtd_ctx of the C ABI."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding as B
+
+
+class Cavity:
+    """A PEC box cavity of nx*ny*nz cells stepped on the GPU.
+
+    ce/ch: None (vacuum), a scalar, or three canonical (nz+1, ny+1, nx+1) arrays of
+    dt/(eps dx) at E positions and dt/(mu dx) at H positions.
+    """
+
+    def __init__(self, nx, ny, nz, dt, dx=1.0, ce=None, ch=None, storage=B.FDTD_F32, stream=None):
+        self.dims = (int(nx), int(ny), int(nz))
+        self.dt, self.dx, self.storage = float(dt), float(dx), int(storage)
+        self.shape = (nz + 1, ny + 1, nx + 1)
+        self.handle = B.fdtd_create(nx, ny, nz, dt, dx, ce, ch, storage, stream)
+
+    def set_fields(self, fields, on_device=False):
+        B.fdtd_set_fields(self.handle, fields, int(on_device), dims=self.dims)
+
+    def get_fields(self, out=None, on_device=False):
+        if out is None:
+            out = [np.empty(self.shape, dtype=np.float32) for _ in range(6)]
+        B.fdtd_get_fields(self.handle, out, int(on_device), dims=self.dims)
+        return out
+
+    def step(self, n=1):
+        B.fdtd_step(self.handle, n)
+
+    def energy(self):
+        return B.fdtd_energy(self.handle)
+
+    def divergence(self):
+        return B.fdtd_divergence(self.handle)
+
+    def sync(self):
+        B.fdtd_sync(self.handle)
+
+    def tune(self, **kw):
+        B.fdtd_set_tuning(self.handle, **kw)
+
+    @property
+    def steps_done(self):
+        return B.fdtd_steps_done(self.handle)
+
+    @property
+    def device_bytes(self):
+        return B.fdtd_device_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.fdtd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

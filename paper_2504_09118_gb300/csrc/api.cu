@@ -1,0 +1,970 @@
+// C ABI of libfdtd (declared in include/fdtd.h): context lifecycle, layout
+// conversion, step dispatch (fused TMA kernel, or the unfused baseline), FP64
+// reductions, CUDA-graph replay and batches of cavities.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fdtd.h"
+#include "launch.h"
+
+using namespace fdtd;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+int num_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+size_t esize(int storage) { return storage == FDTD_F32 ? 4 : 2; }
+
+struct GraphKey {
+    int steps, parity;
+    bool operator<(const GraphKey &o) const { return steps != o.steps ? steps < o.steps : parity < o.parity; }
+};
+
+}  // namespace
+
+struct fdtd_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    double dt = 0, dx = 0;
+    int storage = 0;
+    cudaStream_t stream = nullptr;
+    int pitch = 0;
+    size_t arr_elems = 0;
+    void *fields[2][6] = {};
+    float *face[3] = {}, *face_ch[3] = {};
+    int coef_mode = COEF_SCALAR;
+    float ce_s[3] = {}, ch_s[3] = {};
+    uint8_t *id = nullptr;
+    float *table = nullptr;
+    int ntab = 0;
+    float *coef_full[6] = {};
+    float scale[6] = {1, 1, 1, 1, 1, 1};
+    int cur = 0;
+    long long steps = 0;
+    bool has_fields = false;
+    int *d_status = nullptr;
+    double *d_partial = nullptr, *d_out = nullptr;
+    float *d_stage = nullptr;    // canonical staging buffer for host transfers (lazy)
+    unsigned *d_max = nullptr;
+    CUtensorMap *d_maps = nullptr;
+    CavityDesc *d_desc = nullptr;
+    TileDesc *d_tiles = nullptr;
+    int ntiles = 0, grid = 0, tiles_ty = 0, maps_ty = 0;
+    fdtd_tuning tuning{};
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    int inject_us = 0;
+    long long bytes = 0;
+    fdtd_batch *batch = nullptr;
+    std::string err;
+};
+
+struct fdtd_batch {
+    int storage = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<fdtd_ctx *> members;
+    std::vector<int> off;            // parity offset of each member
+    int parity = 0;                  // launch parity of the next step
+    fdtd_tuning tuning{};
+    CavityDesc *d_desc = nullptr;
+    int desc_cap = 0;
+    TileDesc *d_tiles = nullptr;
+    int tiles_cap = 0, ntiles = 0, grid = 0;
+    bool dirty = true;
+    int *d_status = nullptr;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::string err;
+};
+
+namespace {
+
+int fail(fdtd_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_error = buf;
+    return code;
+}
+int bfail(fdtd_batch *b, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    return code;
+}
+
+#define CK(ctx, call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? FDTD_ERR_OOM : FDTD_ERR_CUDA, "%s: %s", #call, \
+                        cudaGetErrorString(e_));                                                        \
+    } while (0)
+
+cudaError_t dmalloc(fdtd_ctx *c, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) c->bytes += (long long)bytes;
+    return e;
+}
+
+CavityDesc make_desc(const fdtd_ctx *c, int parity_off) {
+    CavityDesc d{};
+    d.nx = c->nx;
+    d.ny = c->ny;
+    d.nz = c->nz;
+    d.pitch = c->pitch;
+    d.plane = (long long)c->pitch * c->ny;
+    d.coef_mode = c->coef_mode;
+    d.ntab = c->ntab;
+    d.parity_off = parity_off;
+    for (int q = 0; q < 3; ++q) {
+        d.ce[q] = c->ce_s[q];
+        d.ch[q] = c->ch_s[q];
+        d.face[q] = c->face[q];
+        d.face_ch[q] = c->face_ch[q];
+    }
+    for (int f = 0; f < 6; ++f) {
+        d.scale[f] = c->scale[f];
+        d.inv_scale[f] = 1.0f / c->scale[f];
+        d.buf[0][f] = c->fields[0][f];
+        d.buf[1][f] = c->fields[1][f];
+        d.coef[f] = c->coef_full[f];
+    }
+    d.id = c->id;
+    d.table = c->table;
+    d.maps = c->d_maps;
+    return d;
+}
+
+int upload_desc(fdtd_ctx *c) {
+    CavityDesc d = make_desc(c, 0);
+    CK(c, cudaMemcpyAsync(c->d_desc, &d, sizeof d, cudaMemcpyHostToDevice, c->stream));
+    return FDTD_OK;
+}
+
+// Encode the 13 tensor maps of a cavity for a given tile height.
+int encode_maps(fdtd_ctx *c, int tile_y) {
+    if (c->maps_ty == tile_y) return FDTD_OK;
+    auto enc = get_encode();
+    if (!enc) return fail(c, FDTD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    int bx, by, hx;
+    fused_box(c->storage, tile_y, &bx, &by, &hx);
+    std::vector<CUtensorMap> maps(kMapsPerCavity);
+    const size_t es = esize(c->storage);
+    const CUtensorMapDataType dt = c->storage == FDTD_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : c->storage == FDTD_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    cuuint64_t gdim[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz};
+    cuuint32_t estr[3] = {1, 1, 1};
+    for (int cp = 0; cp < 2; ++cp)
+        for (int f = 0; f < 6; ++f) {
+            cuuint64_t gstr[2] = {(cuuint64_t)c->pitch * es, (cuuint64_t)c->pitch * c->ny * es};
+            cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+            CUresult r = enc(&maps[cp * 6 + f], dt, 3, c->fields[cp][f], gdim, gstr, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(c, FDTD_ERR_CUDA, "tensor map encode failed (%d)", (int)r);
+        }
+    if (c->id) {
+        cuuint64_t gstr[2] = {(cuuint64_t)c->pitch, (cuuint64_t)c->pitch * c->ny};
+        cuuint32_t box[3] = {(cuuint32_t)(kTileX + 16), (cuuint32_t)by, 1};
+        CUresult r = enc(&maps[12], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->id, gdim, gstr, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(c, FDTD_ERR_CUDA, "id tensor map encode failed (%d)", (int)r);
+    } else {
+        memset(&maps[12], 0, sizeof(CUtensorMap));
+    }
+    CK(c, cudaMemcpyAsync(c->d_maps, maps.data(), sizeof(CUtensorMap) * kMapsPerCavity, cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->maps_ty = tile_y;
+    return FDTD_OK;
+}
+
+struct Shape {
+    int tile_y, stages, ctas_per_sm;
+};
+
+Shape resolve_shape(int storage, const fdtd_tuning &t) {
+    static std::mutex mu;
+    static std::map<int, int> occ_cache;   // (storage, tile_y, stages) -> max CTAs per SM
+    Shape s;
+    s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 16) ? t.tile_y : 8;
+    s.stages = (t.stages >= 3 && t.stages <= 8) ? t.stages : 4;
+    while (s.stages > 3 && fused_smem_bytes(storage, s.tile_y, s.stages) > 227 * 1024) --s.stages;
+    const int key = (storage * 64 + s.tile_y) * 16 + s.stages;
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = occ_cache.find(key);
+        if (it != occ_cache.end()) {
+            occ = it->second;
+        } else {
+            if (fused_occupancy(storage, s.tile_y, s.stages, &occ) != cudaSuccess || occ < 1) occ = 1;
+            occ_cache[key] = occ;
+        }
+    }
+    s.ctas_per_sm = t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, occ) : occ;
+    return s;
+}
+
+// Planes per tile for a cavity given the column count and grid size (load balance vs prologue overhead).
+int choose_zlen(long long cols, int nz, int grid, int zchunk) {
+    if (zchunk > 0) return std::min(zchunk, nz);
+    long long best = -1;
+    int bestL = nz;
+    for (int L = nz; L >= 1; --L) {
+        const long long nch = (nz + L - 1) / L;
+        const long long waves = (cols * nch + grid - 1) / grid;
+        const long long cost = waves * (L + 1);
+        if (best < 0 || cost < best) {
+            best = cost;
+            bestL = L;
+        }
+    }
+    return bestL;
+}
+
+void append_tiles(std::vector<TileDesc> &v, int cav, int nx, int ny, int nz, int tile_y, int zlen) {
+    for (int z0 = 0; z0 < nz; z0 += zlen)
+        for (int y0 = 0; y0 < ny; y0 += tile_y)
+            for (int x0 = 0; x0 < nx; x0 += kTileX) {
+                TileDesc t{};
+                t.cav = cav;
+                t.x0 = x0;
+                t.y0 = y0;
+                t.kz0 = z0;
+                t.kz1 = std::min(nz, z0 + zlen);
+                v.push_back(t);
+            }
+}
+
+int build_tiles(fdtd_ctx *c) {
+    Shape s = resolve_shape(c->storage, c->tuning);
+    if (c->tiles_ty == s.tile_y && c->d_tiles && c->grid) return FDTD_OK;
+    int rc = encode_maps(c, s.tile_y);
+    if (rc) return rc;
+    const int G = num_sms() * s.ctas_per_sm;
+    const long long cols = (long long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + s.tile_y - 1) / s.tile_y);
+    const int zlen = choose_zlen(cols, c->nz, G, c->tuning.zchunk);
+    std::vector<TileDesc> v;
+    append_tiles(v, 0, c->nx, c->ny, c->nz, s.tile_y, zlen);
+    if (c->d_tiles) cudaFree(c->d_tiles);
+    c->d_tiles = nullptr;
+    CK(c, cudaMalloc(&c->d_tiles, sizeof(TileDesc) * v.size()));
+    CK(c, cudaMemcpyAsync(c->d_tiles, v.data(), sizeof(TileDesc) * v.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->ntiles = (int)v.size();
+    c->grid = std::min<int>(c->ntiles, G);
+    c->tiles_ty = s.tile_y;
+    return FDTD_OK;
+}
+
+void drop_graphs(std::map<GraphKey, cudaGraphExec_t> &g) {
+    for (auto &kv : g) cudaGraphExecDestroy(kv.second);
+    g.clear();
+}
+
+bool use_fused(const fdtd_ctx *c) {
+    return c->coef_mode != COEF_FULL && c->tuning.kernel != FDTD_KERNEL_SIMPLE;
+}
+
+// One step of a single context (no graph).
+int launch_one(fdtd_ctx *c, int parity, int inject_us) {
+    if (!use_fused(c)) {
+        CK(c, launch_simple_step(c->storage, make_desc(c, 0), c->cur, c->stream));
+        return FDTD_OK;
+    }
+    Shape s = resolve_shape(c->storage, c->tuning);
+    FusedLaunch L{};
+    L.cav = c->d_desc;
+    L.tiles = c->d_tiles;
+    L.ntiles = c->ntiles;
+    L.parity = parity;
+    L.status = c->d_status;
+    L.tile_y = s.tile_y;
+    L.stages = s.stages;
+    L.grid = c->grid;
+    L.inject_timeout_us = inject_us;
+    CK(c, launch_fused_step(c->storage, L, c->stream));
+    return FDTD_OK;
+}
+
+int check_status(fdtd_ctx *c, int *d_status, cudaStream_t s) {
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    if (h) {
+        CK(c, cudaMemsetAsync(d_status, 0, sizeof(int), s));
+        CK(c, cudaStreamSynchronize(s));
+        if (h & STATUS_TIMEOUT)
+            return fail(c, FDTD_ERR_TIMEOUT, "a step kernel's bounded wait ran out (status 0x%x)", h);
+        return fail(c, FDTD_ERR_CUDA, "device status 0x%x", h);
+    }
+    return FDTD_OK;
+}
+
+int ensure_stage(fdtd_ctx *c) {
+    if (c->d_stage) return FDTD_OK;
+    const size_t n = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+    CK(c, dmalloc(c, (void **)&c->d_stage, n * sizeof(float)));
+    return FDTD_OK;
+}
+
+// Compress per-position coefficients: one byte per active cell + table when <= 256 distinct tuples.
+struct Tuple {
+    float v[6];
+    bool operator==(const Tuple &o) const { return memcmp(v, o.v, sizeof v) == 0; }
+};
+struct TupleHash {
+    size_t operator()(const Tuple &t) const {
+        uint64_t h = 1469598103934665603ull;
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(t.v);
+        for (size_t i = 0; i < sizeof t.v; ++i) h = (h ^ p[i]) * 1099511628211ull;
+        return (size_t)h;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *fdtd_version(void) { return "fdtd-gb300 0.1 (sm_103a)"; }
+
+const char *fdtd_last_error(const fdtd_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, const float *const ce[3],
+                const float *const ch[3], int storage, void *cuda_stream) {
+    if (!out) return fail(nullptr, FDTD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 32768 || ny > 32768 || nz > 32768)
+        return fail(nullptr, FDTD_ERR_ARG, "cell counts must be in [1, 32768], got %d x %d x %d", nx, ny, nz);
+    if (!(dt > 0) || !(dx > 0) || !std::isfinite(dt) || !std::isfinite(dx))
+        return fail(nullptr, FDTD_ERR_ARG, "dt and dx must be positive and finite");
+    if (storage < FDTD_F32 || storage > FDTD_BF16) return fail(nullptr, FDTD_ERR_ARG, "bad storage %d", storage);
+    bool have_ce = ce && ce[0] && ce[1] && ce[2];
+    bool have_ch = ch && ch[0] && ch[1] && ch[2];
+    if ((ce && !have_ce && (ce[0] || ce[1] || ce[2])) || (ch && !have_ch && (ch[0] || ch[1] || ch[2])))
+        return fail(nullptr, FDTD_ERR_ARG, "coefficient arrays must be all three or none");
+
+    const size_t CX = nx + 1, CY = ny + 1;
+    auto cidx = [&](int i, int j, int k) { return ((size_t)k * CY + j) * CX + i; };
+    const float vac = (float)(dt / dx);
+
+    // ---- coefficient validation, Courant check and compression (host)
+    std::vector<uint8_t> ids;
+    std::vector<Tuple> table;
+    bool full = false;
+    if (have_ce || have_ch) {
+        ids.resize((size_t)nx * ny * nz);
+        std::unordered_map<Tuple, int, TupleHash> map;
+        Tuple last{};
+        int last_id = -1;
+        double worst = 0.0;
+        for (int k = 0; k < nz && !full; ++k)
+            for (int j = 0; j < ny && !full; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    Tuple t;
+                    const size_t q = cidx(i, j, k);
+                    for (int c = 0; c < 3; ++c) {
+                        t.v[c] = have_ce ? ce[c][q] : vac;
+                        t.v[3 + c] = have_ch ? ch[c][q] : vac;
+                    }
+                    int id;
+                    if (last_id >= 0 && t == last) {
+                        id = last_id;
+                    } else {
+                        for (int c = 0; c < 6; ++c)
+                            if (!(t.v[c] > 0.f) || !std::isfinite(t.v[c]))
+                                return fail(nullptr, FDTD_ERR_ARG, "coefficient %d at (%d,%d,%d) is not positive", c,
+                                            i, j, k);
+                        const double me = std::max({t.v[0], t.v[1], t.v[2]});
+                        const double mh = std::max({t.v[3], t.v[4], t.v[5]});
+                        worst = std::max(worst, 3.0 * me * mh);
+                        auto it = map.find(t);
+                        if (it == map.end()) {
+                            if ((int)table.size() >= kMaxTable) {
+                                full = true;
+                                break;
+                            }
+                            id = (int)table.size();
+                            map.emplace(t, id);
+                            table.push_back(t);
+                        } else {
+                            id = it->second;
+                        }
+                        last = t;
+                        last_id = id;
+                    }
+                    ids[((size_t)k * ny + j) * nx + i] = (uint8_t)id;
+                }
+        if (full) {
+            // per-position arrays: validate and Courant-check every active cell
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        const size_t q = cidx(i, j, k);
+                        double me = 0, mh = 0;
+                        for (int c = 0; c < 3; ++c) {
+                            const float a = have_ce ? ce[c][q] : vac, b = have_ch ? ch[c][q] : vac;
+                            if (!(a > 0.f) || !(b > 0.f) || !std::isfinite(a) || !std::isfinite(b))
+                                return fail(nullptr, FDTD_ERR_ARG, "coefficient at (%d,%d,%d) is not positive", i,
+                                            j, k);
+                            me = std::max(me, (double)a);
+                            mh = std::max(mh, (double)b);
+                        }
+                        worst = std::max(worst, 3.0 * me * mh);
+                    }
+        }
+        if (worst > 1.0 + 1e-6)
+            return fail(nullptr, FDTD_ERR_UNSTABLE, "Courant bound violated: max sqrt(3 ce ch) = %.6f > 1",
+                        std::sqrt(worst));
+        // far-face ch values (Hx at i = nx, Hy at j = ny, Hz at k = nz) are used by energy and divergence
+        if (have_ch) {
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j <= ny; ++j)
+                    for (int i = 0; i <= nx; ++i) {
+                        const bool fx = i == nx && j < ny, fy = j == ny && i < nx;
+                        if ((fx && !(ch[0][cidx(i, j, k)] > 0.f)) || (fy && !(ch[1][cidx(i, j, k)] > 0.f)))
+                            return fail(nullptr, FDTD_ERR_ARG, "ch on a far face is not positive");
+                    }
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i)
+                    if (!(ch[2][cidx(i, j, nz)] > 0.f)) return fail(nullptr, FDTD_ERR_ARG, "chz on face k=nz not positive");
+        }
+    } else {
+        if (3.0 * vac * vac > 1.0 + 1e-6)
+            return fail(nullptr, FDTD_ERR_UNSTABLE, "Courant bound violated: sqrt(3) dt/dx = %.6f > 1",
+                        std::sqrt(3.0) * vac);
+    }
+
+    fdtd_ctx *c = new fdtd_ctx();
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->dt = dt;
+    c->dx = dx;
+    c->storage = storage;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->pitch = (nx + 31) / 32 * 32;
+    c->arr_elems = (size_t)c->pitch * ny * nz;
+    for (int q = 0; q < 3; ++q) c->ce_s[q] = c->ch_s[q] = vac;
+    auto bail = [&](int code) {
+        fdtd_destroy(c);
+        return code;
+    };
+    auto cfail = [&](const char *what, cudaError_t e) {
+        fail(nullptr, e == cudaErrorMemoryAllocation ? FDTD_ERR_OOM : FDTD_ERR_CUDA, "%s: %s", what,
+             cudaGetErrorString(e));
+        return bail(e == cudaErrorMemoryAllocation ? FDTD_ERR_OOM : FDTD_ERR_CUDA);
+    };
+    cudaError_t e;
+    const size_t es = esize(storage);
+    for (int cp = 0; cp < 2; ++cp)
+        for (int f = 0; f < 6; ++f) {
+            if ((e = dmalloc(c, &c->fields[cp][f], c->arr_elems * es)) != cudaSuccess) return cfail("field alloc", e);
+            if ((e = cudaMemsetAsync(c->fields[cp][f], 0, c->arr_elems * es, c->stream)) != cudaSuccess)
+                return cfail("memset", e);
+        }
+    const size_t nface[3] = {(size_t)ny * nz, (size_t)nx * nz, (size_t)nx * ny};
+    for (int q = 0; q < 3; ++q) {
+        if ((e = dmalloc(c, (void **)&c->face[q], nface[q] * 4)) != cudaSuccess) return cfail("face alloc", e);
+        if ((e = cudaMemsetAsync(c->face[q], 0, nface[q] * 4, c->stream)) != cudaSuccess) return cfail("memset", e);
+    }
+    if (have_ce || have_ch) {
+        // face ch (Hx at i = nx, Hy at j = ny, Hz at k = nz)
+        for (int q = 0; q < 3; ++q) {
+            std::vector<float> fc(nface[q]);
+            for (size_t n = 0; n < nface[q]; ++n) {
+                size_t src;
+                if (q == 0) src = cidx(nx, (int)(n % ny), (int)(n / ny));
+                else if (q == 1) src = cidx((int)(n % nx), ny, (int)(n / nx));
+                else src = cidx((int)(n % nx), (int)(n / nx), nz);
+                fc[n] = have_ch ? ch[q][src] : vac;
+            }
+            if ((e = dmalloc(c, (void **)&c->face_ch[q], nface[q] * 4)) != cudaSuccess) return cfail("face alloc", e);
+            if ((e = cudaMemcpy(c->face_ch[q], fc.data(), nface[q] * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cfail("face copy", e);
+        }
+        if (!full) {
+            c->coef_mode = COEF_ID8;
+            c->ntab = (int)table.size();
+            std::vector<float> tab(8 * kMaxTable, 0.f);
+            for (int n = 0; n < c->ntab; ++n) {
+                for (int q = 0; q < 3; ++q) {
+                    tab[8 * n + q] = table[n].v[q];
+                    tab[8 * n + 4 + q] = table[n].v[3 + q];
+                }
+            }
+            if ((e = dmalloc(c, (void **)&c->table, tab.size() * 4)) != cudaSuccess) return cfail("table alloc", e);
+            if ((e = cudaMemcpy(c->table, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cfail("table copy", e);
+            if ((e = dmalloc(c, (void **)&c->id, c->arr_elems)) != cudaSuccess) return cfail("id alloc", e);
+            if ((e = cudaMemset(c->id, 0, c->arr_elems)) != cudaSuccess) return cfail("memset", e);
+            if ((e = cudaMemcpy2D(c->id, c->pitch, ids.data(), nx, nx, (size_t)ny * nz, cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+                return cfail("id copy", e);
+        } else {
+            c->coef_mode = COEF_FULL;
+            std::vector<float> row((size_t)c->pitch * ny * nz, 0.f);
+            for (int a = 0; a < 6; ++a) {
+                for (int k = 0; k < nz; ++k)
+                    for (int j = 0; j < ny; ++j)
+                        for (int i = 0; i < nx; ++i) {
+                            const size_t q = cidx(i, j, k);
+                            const float v = a < 3 ? (have_ce ? ce[a][q] : vac) : (have_ch ? ch[a - 3][q] : vac);
+                            row[((size_t)k * ny + j) * c->pitch + i] = v;
+                        }
+                if ((e = dmalloc(c, (void **)&c->coef_full[a], row.size() * 4)) != cudaSuccess)
+                    return cfail("coef alloc", e);
+                if ((e = cudaMemcpy(c->coef_full[a], row.data(), row.size() * 4, cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
+                    return cfail("coef copy", e);
+            }
+        }
+    }
+    if ((e = dmalloc(c, (void **)&c->d_status, sizeof(int))) != cudaSuccess) return cfail("status alloc", e);
+    if ((e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess) return cfail("memset", e);
+    const int nb = reduction_blocks();
+    if ((e = dmalloc(c, (void **)&c->d_partial, sizeof(double) * 3 * nb)) != cudaSuccess) return cfail("alloc", e);
+    if ((e = dmalloc(c, (void **)&c->d_out, sizeof(double) * 3)) != cudaSuccess) return cfail("alloc", e);
+    if ((e = dmalloc(c, (void **)&c->d_max, sizeof(unsigned) * 6)) != cudaSuccess) return cfail("alloc", e);
+    if ((e = dmalloc(c, (void **)&c->d_maps, sizeof(CUtensorMap) * kMapsPerCavity)) != cudaSuccess)
+        return cfail("alloc", e);
+    if ((e = dmalloc(c, (void **)&c->d_desc, sizeof(CavityDesc))) != cudaSuccess) return cfail("alloc", e);
+    if (int rc = upload_desc(c)) {
+        g_create_error = c->err;
+        return bail(rc);
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cfail("sync", e);
+    *out = c;
+    return FDTD_OK;
+}
+
+void fdtd_destroy(fdtd_ctx *c) {
+    if (!c) return;
+    if (c->batch) fdtd_batch_remove(c->batch, c);
+    cudaStreamSynchronize(c->stream);
+    drop_graphs(c->graphs);
+    for (int cp = 0; cp < 2; ++cp)
+        for (int f = 0; f < 6; ++f) cudaFree(c->fields[cp][f]);
+    for (int q = 0; q < 3; ++q) {
+        cudaFree(c->face[q]);
+        cudaFree(c->face_ch[q]);
+    }
+    for (int a = 0; a < 6; ++a) cudaFree(c->coef_full[a]);
+    cudaFree(c->id);
+    cudaFree(c->table);
+    cudaFree(c->d_status);
+    cudaFree(c->d_partial);
+    cudaFree(c->d_out);
+    cudaFree(c->d_stage);
+    cudaFree(c->d_max);
+    cudaFree(c->d_maps);
+    cudaFree(c->d_desc);
+    cudaFree(c->d_tiles);
+    delete c;
+}
+
+long long fdtd_steps_done(const fdtd_ctx *c) { return c ? c->steps : -1; }
+long long fdtd_device_bytes(const fdtd_ctx *c) { return c ? c->bytes : -1; }
+
+int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
+    if (!c) return FDTD_ERR_ARG;
+    fdtd_tuning n{};
+    if (t) n = *t;
+    if (n.kernel < 0 || n.kernel > FDTD_KERNEL_FUSED) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
+    if (n.tile_y && n.tile_y != 4 && n.tile_y != 8 && n.tile_y != 16)
+        return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16");
+    if (n.stages && (n.stages < 3 || n.stages > 8)) return fail(c, FDTD_ERR_ARG, "stages must be in [3, 8]");
+    if (n.zchunk < 0 || n.ctas_per_sm < 0) return fail(c, FDTD_ERR_ARG, "negative tuning value");
+    c->tuning = n;
+    c->tiles_ty = 0;   // force a tile rebuild
+    drop_graphs(c->graphs);
+    return FDTD_OK;
+}
+
+int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
+    if (!c || !f) return fail(c, FDTD_ERR_ARG, "NULL argument");
+    for (int q = 0; q < 6; ++q)
+        if (!f[q]) return fail(c, FDTD_ERR_ARG, "field %d is NULL", q);
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
+    const size_t n = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+    if (!on_device)
+        if (int rc = ensure_stage(c)) return rc;
+    // scales for 16-bit storage: s_c = 2^(8 - ceil(log2 max|F_c|))
+    if (c->storage != FDTD_F32) {
+        CK(c, cudaMemsetAsync(c->d_max, 0, sizeof(unsigned) * 6, c->stream));
+        for (int q = 0; q < 6; ++q) {
+            const float *src = f[q];
+            if (!on_device) {
+                CK(c, cudaMemcpyAsync(c->d_stage, f[q], n * 4, cudaMemcpyHostToDevice, c->stream));
+                src = c->d_stage;
+            }
+            CK(c, launch_maxabs(src, q, c->nx, c->ny, c->nz, c->d_max + q, c->stream));
+        }
+        unsigned hm[6];
+        CK(c, cudaMemcpyAsync(hm, c->d_max, sizeof hm, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        for (int q = 0; q < 6; ++q) {
+            float m;
+            memcpy(&m, &hm[q], 4);
+            if (!std::isfinite(m)) return fail(c, FDTD_ERR_ARG, "field %d holds a non-finite value", q);
+            c->scale[q] = m > 0.f ? std::ldexp(1.0f, 8 - (int)std::ceil(std::log2((double)m))) : 1.0f;
+        }
+    }
+    if (int rc = upload_desc(c)) return rc;
+    CavityDesc d = make_desc(c, 0);
+    for (int q = 0; q < 6; ++q) {
+        const float *src = f[q];
+        if (!on_device) {
+            CK(c, cudaMemcpyAsync(c->d_stage, f[q], n * 4, cudaMemcpyHostToDevice, c->stream));
+            src = c->d_stage;
+        }
+        CK(c, launch_pack(c->storage, d, 0, q, src, q >= 3 ? c->face[q - 3] : nullptr, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->cur = 0;
+    c->steps = 0;
+    c->has_fields = true;
+    return check_status(c, c->d_status, c->stream);
+}
+
+int fdtd_get_fields(fdtd_ctx *c, float *const f[6], int on_device) {
+    if (!c || !f) return fail(c, FDTD_ERR_ARG, "NULL argument");
+    for (int q = 0; q < 6; ++q)
+        if (!f[q]) return fail(c, FDTD_ERR_ARG, "field %d is NULL", q);
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
+    const size_t n = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+    if (!on_device)
+        if (int rc = ensure_stage(c)) return rc;
+    CavityDesc d = make_desc(c, 0);
+    for (int q = 0; q < 6; ++q) {
+        float *dst = on_device ? f[q] : c->d_stage;
+        CK(c, launch_unpack(c->storage, d, c->cur, q, dst, c->stream));
+        if (!on_device) CK(c, cudaMemcpyAsync(f[q], c->d_stage, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_status(c, c->d_status, c->stream);
+}
+
+int fdtd_step(fdtd_ctx *c, int nsteps) {
+    if (!c) return FDTD_ERR_ARG;
+    if (nsteps < 0) return fail(c, FDTD_ERR_ARG, "nsteps < 0");
+    if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; step the batch");
+    if (nsteps == 0) return FDTD_OK;
+    if (use_fused(c)) {
+        if (int rc = build_tiles(c)) return rc;
+    }
+    int left = nsteps;
+    if (c->inject_us > 0 && use_fused(c)) {
+        const int inj = c->inject_us;
+        c->inject_us = 0;
+        if (int rc = launch_one(c, c->cur, inj)) return rc;
+        c->cur ^= 1;
+        ++c->steps;
+        --left;
+    }
+    const bool fused = use_fused(c);
+    const int K = 16;
+    if (c->tuning.use_graph && fused && c->stream != nullptr && left >= K) {
+        GraphKey key{K, c->cur};
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            cudaGraph_t g;
+            CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = FDTD_OK;
+            for (int s = 0; s < K && !rc; ++s) rc = launch_one(c, c->cur ^ (s & 1), 0);
+            cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+            if (rc) return rc;
+            CK(c, ee);
+            cudaGraphExec_t ex;
+            CK(c, cudaGraphInstantiate(&ex, g, 0));
+            cudaGraphDestroy(g);
+            it = c->graphs.emplace(key, ex).first;
+        }
+        while (left >= K) {
+            CK(c, cudaGraphLaunch(it->second, c->stream));
+            left -= K;
+            c->steps += K;   // K even: parity unchanged
+        }
+    }
+    for (; left > 0; --left) {
+        if (int rc = launch_one(c, c->cur, 0)) return rc;
+        if (fused) c->cur ^= 1;
+        ++c->steps;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_sync(fdtd_ctx *c) {
+    if (!c) return FDTD_ERR_ARG;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_status(c, c->d_status, c->stream);
+}
+
+static int run_reductions(fdtd_ctx *c, double out[3]) {
+    if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
+    CK(c, launch_reductions(c->storage, make_desc(c, 0), c->cur, c->d_partial, reduction_blocks(), c->d_out,
+                            c->stream));
+    CK(c, cudaMemcpyAsync(out, c->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_status(c, c->d_status, c->stream);
+}
+
+int fdtd_energy(fdtd_ctx *c, double *W) {
+    if (!c || !W) return fail(c, FDTD_ERR_ARG, "NULL argument");
+    double o[3];
+    if (int rc = run_reductions(c, o)) return rc;
+    *W = 0.5 * (c->dt / c->dx) * o[0];
+    return FDTD_OK;
+}
+
+int fdtd_divergence(fdtd_ctx *c, double *de, double *dh) {
+    if (!c || !de || !dh) return fail(c, FDTD_ERR_ARG, "NULL argument");
+    double o[3];
+    if (int rc = run_reductions(c, o)) return rc;
+    *de = std::sqrt(o[1]);
+    *dh = std::sqrt(o[2]);
+    return FDTD_OK;
+}
+
+int fdtd_debug_inject_timeout(fdtd_ctx *c, int limit_us) {
+    if (!c) return FDTD_ERR_ARG;
+    if (limit_us < 1 || limit_us > 1000000) return fail(c, FDTD_ERR_ARG, "limit_us must be in [1, 1e6]");
+    if (!use_fused(c)) return fail(c, FDTD_ERR_STATE, "timeout injection needs the fused kernel");
+    c->inject_us = limit_us;
+    return FDTD_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+int fdtd_batch_create(fdtd_batch **out, int storage, void *cuda_stream) {
+    if (!out) return FDTD_ERR_ARG;
+    *out = nullptr;
+    if (storage < FDTD_F32 || storage > FDTD_BF16) return FDTD_ERR_ARG;
+    fdtd_batch *b = new fdtd_batch();
+    b->storage = storage;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess || cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(b->d_status);
+        delete b;
+        return FDTD_ERR_OOM;
+    }
+    *out = b;
+    return FDTD_OK;
+}
+
+int fdtd_batch_size(const fdtd_batch *b) { return b ? (int)b->members.size() : -1; }
+const char *fdtd_batch_last_error(const fdtd_batch *b) { return b ? b->err.c_str() : ""; }
+
+int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *c) {
+    if (!b || !c) return bfail(b, FDTD_ERR_ARG, "NULL argument");
+    if (c->batch) return bfail(b, FDTD_ERR_STATE, "context already belongs to a batch");
+    if (!c->has_fields) return bfail(b, FDTD_ERR_STATE, "context has no fields yet");
+    if (c->storage != b->storage) return bfail(b, FDTD_ERR_ARG, "storage mismatch");
+    if (c->stream != b->stream) return bfail(b, FDTD_ERR_ARG, "stream mismatch");
+    if (c->coef_mode == COEF_FULL) return bfail(b, FDTD_ERR_ARG, "per-position coefficient arrays are not batched");
+    // the member's current copy must be the one the batch's next launch reads
+    b->members.push_back(c);
+    b->off.push_back(b->parity ^ c->cur);
+    c->batch = b;
+    b->dirty = true;
+    return FDTD_OK;
+}
+
+int fdtd_batch_remove(fdtd_batch *b, fdtd_ctx *c) {
+    if (!b || !c) return bfail(b, FDTD_ERR_ARG, "NULL argument");
+    for (size_t n = 0; n < b->members.size(); ++n)
+        if (b->members[n] == c) {
+            cudaStreamSynchronize(b->stream);
+            c->cur = b->parity ^ b->off[n];
+            c->batch = nullptr;
+            b->members.erase(b->members.begin() + n);
+            b->off.erase(b->off.begin() + n);
+            b->dirty = true;
+            return FDTD_OK;
+        }
+    return bfail(b, FDTD_ERR_ARG, "context is not a member");
+}
+
+int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t) {
+    if (!b) return FDTD_ERR_ARG;
+    fdtd_tuning n{};
+    if (t) n = *t;
+    if (n.kernel == FDTD_KERNEL_SIMPLE) return bfail(b, FDTD_ERR_ARG, "batches use the fused kernel");
+    if (n.tile_y && n.tile_y != 4 && n.tile_y != 8 && n.tile_y != 16) return bfail(b, FDTD_ERR_ARG, "bad tile_y");
+    if (n.stages && (n.stages < 3 || n.stages > 8)) return bfail(b, FDTD_ERR_ARG, "bad stages");
+    b->tuning = n;
+    b->dirty = true;
+    return FDTD_OK;
+}
+
+static int batch_rebuild(fdtd_batch *b) {
+    if (!b->dirty) return FDTD_OK;
+    drop_graphs(b->graphs);
+    Shape s = resolve_shape(b->storage, b->tuning);
+    const int G = num_sms() * s.ctas_per_sm;
+    std::vector<CavityDesc> descs;
+    std::vector<TileDesc> tiles;
+    long long total_cols_planes = 0;
+    for (size_t n = 0; n < b->members.size(); ++n) {
+        fdtd_ctx *c = b->members[n];
+        if (int rc = encode_maps(c, s.tile_y)) return bfail(b, rc, "member %zu: %s", n, c->err.c_str());
+        descs.push_back(make_desc(c, b->off[n]));
+        total_cols_planes += (long long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + s.tile_y - 1) / s.tile_y) * c->nz;
+    }
+    // one z-length for all members so tiles carry similar work; about 8 tiles per CTA
+    int zlen = b->tuning.zchunk > 0 ? b->tuning.zchunk
+                                    : (int)std::max<long long>(8, total_cols_planes / std::max(1, 8 * G));
+    for (size_t n = 0; n < b->members.size(); ++n) {
+        fdtd_ctx *c = b->members[n];
+        append_tiles(tiles, (int)n, c->nx, c->ny, c->nz, s.tile_y, std::min(zlen, c->nz));
+    }
+    // longest tiles first, then round-robin over the persistent CTAs
+    std::stable_sort(tiles.begin(), tiles.end(),
+                     [](const TileDesc &a, const TileDesc &c) { return (a.kz1 - a.kz0) > (c.kz1 - c.kz0); });
+    if ((int)descs.size() > b->desc_cap) {
+        cudaFree(b->d_desc);
+        b->desc_cap = std::max<int>((int)descs.size(), 2 * b->desc_cap);
+        if (cudaMalloc(&b->d_desc, sizeof(CavityDesc) * b->desc_cap) != cudaSuccess)
+            return bfail(b, FDTD_ERR_OOM, "descriptor alloc");
+    }
+    if ((int)tiles.size() > b->tiles_cap) {
+        cudaFree(b->d_tiles);
+        b->tiles_cap = std::max<int>((int)tiles.size(), 2 * b->tiles_cap);
+        if (cudaMalloc(&b->d_tiles, sizeof(TileDesc) * b->tiles_cap) != cudaSuccess)
+            return bfail(b, FDTD_ERR_OOM, "tile alloc");
+    }
+    if (!descs.empty())
+        if (cudaMemcpyAsync(b->d_desc, descs.data(), sizeof(CavityDesc) * descs.size(), cudaMemcpyHostToDevice,
+                            b->stream) != cudaSuccess)
+            return bfail(b, FDTD_ERR_CUDA, "descriptor upload");
+    if (!tiles.empty())
+        if (cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(), cudaMemcpyHostToDevice,
+                            b->stream) != cudaSuccess)
+            return bfail(b, FDTD_ERR_CUDA, "tile upload");
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "sync");
+    b->ntiles = (int)tiles.size();
+    b->grid = std::min(b->ntiles, G);
+    b->dirty = false;
+    return FDTD_OK;
+}
+
+static int batch_launch(fdtd_batch *b, int parity) {
+    Shape s = resolve_shape(b->storage, b->tuning);
+    FusedLaunch L{};
+    L.cav = b->d_desc;
+    L.tiles = b->d_tiles;
+    L.ntiles = b->ntiles;
+    L.parity = parity;
+    L.status = b->d_status;
+    L.tile_y = s.tile_y;
+    L.stages = s.stages;
+    L.grid = b->grid;
+    cudaError_t e = launch_fused_step(b->storage, L, b->stream);
+    if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+    return FDTD_OK;
+}
+
+int fdtd_batch_step(fdtd_batch *b, int nsteps) {
+    if (!b || nsteps < 0) return bfail(b, FDTD_ERR_ARG, "bad argument");
+    if (b->members.empty() || nsteps == 0) return FDTD_OK;
+    if (int rc = batch_rebuild(b)) return rc;
+    int left = nsteps;
+    const int K = 16;
+    if (b->tuning.use_graph && b->stream != nullptr && left >= K) {
+        GraphKey key{K, b->parity};
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            cudaGraph_t g;
+            if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return bfail(b, FDTD_ERR_CUDA, "capture");
+            int rc = FDTD_OK;
+            for (int s = 0; s < K && !rc; ++s) rc = batch_launch(b, b->parity ^ (s & 1));
+            cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+            if (rc) return rc;
+            if (ee != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "end capture: %s", cudaGetErrorString(ee));
+            cudaGraphExec_t ex;
+            if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return bfail(b, FDTD_ERR_CUDA, "instantiate");
+            }
+            cudaGraphDestroy(g);
+            it = b->graphs.emplace(key, ex).first;
+        }
+        while (left >= K) {
+            if (cudaGraphLaunch(it->second, b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "graph launch");
+            left -= K;
+        }
+        for (fdtd_ctx *c : b->members) c->steps += nsteps - left;
+    }
+    for (; left > 0; --left) {
+        if (int rc = batch_launch(b, b->parity)) return rc;
+        b->parity ^= 1;
+        for (fdtd_ctx *c : b->members) ++c->steps;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_batch_sync(fdtd_batch *b) {
+    if (!b) return FDTD_ERR_ARG;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "sync");
+    int h = 0;
+    if (cudaMemcpy(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bfail(b, FDTD_ERR_CUDA, "status read");
+    if (h) {
+        cudaMemset(b->d_status, 0, sizeof(int));
+        return bfail(b, (h & STATUS_TIMEOUT) ? FDTD_ERR_TIMEOUT : FDTD_ERR_CUDA, "device status 0x%x", h);
+    }
+    return FDTD_OK;
+}
+
+void fdtd_batch_destroy(fdtd_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    while (!b->members.empty()) fdtd_batch_remove(b, b->members.back());
+    drop_graphs(b->graphs);
+    cudaFree(b->d_desc);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_status);
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// Layout conversion, the unfused one-thread-per-cell Yee step, and the FP64
+// energy/divergence reductions.
+//
+// The unfused step is two launches per step (Listing 1: curl H components,
+// then curl E components), each updating one copy of the fields in place; it
+// is the debugging baseline of the fused kernel and the path for coefficient
+// sets too varied for a one-byte material id (COEF_FULL).
+#include "launch.h"
+
+namespace fdtd {
+
+namespace {
+
+constexpr int BXs = 32, BYs = 8;
+
+__device__ __forceinline__ bool tangential(int comp, int i, int j, int k) {
+    return (comp == 0 && (j == 0 || k == 0)) || (comp == 1 && (i == 0 || k == 0)) ||
+           (comp == 2 && (i == 0 || j == 0));
+}
+
+template <typename T>
+__global__ void pack_kernel(const CavityDesc d, int copy, int comp, const float *__restrict__ canon, float *face) {
+    const int i = blockIdx.x * BXs + threadIdx.x, j = blockIdx.y * BYs + threadIdx.y, k = blockIdx.z;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    if (i > nx || j > ny) return;
+    float v = canon[((long long)k * (ny + 1) + j) * (nx + 1) + i];
+    if (i < nx && j < ny && k < nz) {
+        if (comp < 3 && tangential(comp, i, j, k)) v = 0.f;
+        st_field<T>(d, copy, comp, (long long)k * d.plane + (long long)j * d.pitch + i, v);
+        return;
+    }
+    // far-face normal H: store the value after the same storage rounding
+    float q = v;
+    if (Storage<T>::scaled) q = Storage<T>::load(Storage<T>::store(v * d.scale[comp])) * d.inv_scale[comp];
+    if (comp == 3 && i == nx && j < ny && k < nz) face[(long long)k * ny + j] = q;
+    if (comp == 4 && j == ny && i < nx && k < nz) face[(long long)k * nx + i] = q;
+    if (comp == 5 && k == nz && i < nx && j < ny) face[(long long)j * nx + i] = q;
+}
+
+template <typename T>
+__global__ void unpack_kernel(const CavityDesc d, int copy, int comp, float *__restrict__ canon) {
+    const int i = blockIdx.x * BXs + threadIdx.x, j = blockIdx.y * BYs + threadIdx.y, k = blockIdx.z;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    if (i > nx || j > ny) return;
+    float v = 0.f;
+    if (i < nx && j < ny && k < nz) {
+        v = ld_field<T>(d, copy, comp, (long long)k * d.plane + (long long)j * d.pitch + i);
+    } else if (comp == 3 && i == nx && j < ny && k < nz) {
+        v = d.face[0][(long long)k * ny + j];
+    } else if (comp == 4 && j == ny && i < nx && k < nz) {
+        v = d.face[1][(long long)k * nx + i];
+    } else if (comp == 5 && k == nz && i < nx && j < ny) {
+        v = d.face[2][(long long)j * nx + i];
+    }
+    canon[((long long)k * (ny + 1) + j) * (nx + 1) + i] = v;
+}
+
+__device__ __forceinline__ bool in_extent(int comp, int i, int j, int k, int nx, int ny, int nz) {
+    switch (comp) {
+        case 0: return i < nx;
+        case 1: return j < ny;
+        case 2: return k < nz;
+        case 3: return j < ny && k < nz;
+        case 4: return i < nx && k < nz;
+        default: return i < nx && j < ny;
+    }
+}
+
+__global__ void maxabs_kernel(const float *__restrict__ canon, int comp, int nx, int ny, int nz, unsigned *out) {
+    const int i = blockIdx.x * BXs + threadIdx.x, j = blockIdx.y * BYs + threadIdx.y, k = blockIdx.z;
+    float v = 0.f;
+    if (i <= nx && j <= ny && in_extent(comp, i, j, k, nx, ny, nz))
+        v = fabsf(canon[((long long)k * (ny + 1) + j) * (nx + 1) + i]);
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(out, __float_as_uint(v));
+}
+
+// H^{n+1/2} = H^{n-1/2} - ch curl E^n, one thread per cell (E beyond the active range is 0).
+template <typename T>
+__global__ void simple_h_kernel(const CavityDesc d, int copy) {
+    const int i = blockIdx.x * BXs + threadIdx.x, j = blockIdx.y * BYs + threadIdx.y, k = blockIdx.z;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    if (i >= nx || j >= ny) return;
+    const long long P = d.pitch, Z = d.plane;
+    const long long o = (long long)k * Z + (long long)j * P + i;
+    const float ex = ld_field<T>(d, copy, 0, o), ey = ld_field<T>(d, copy, 1, o), ez = ld_field<T>(d, copy, 2, o);
+    const float ex_j1 = j + 1 < ny ? ld_field<T>(d, copy, 0, o + P) : 0.f;
+    const float ex_k1 = k + 1 < nz ? ld_field<T>(d, copy, 0, o + Z) : 0.f;
+    const float ey_i1 = i + 1 < nx ? ld_field<T>(d, copy, 1, o + 1) : 0.f;
+    const float ey_k1 = k + 1 < nz ? ld_field<T>(d, copy, 1, o + Z) : 0.f;
+    const float ez_i1 = i + 1 < nx ? ld_field<T>(d, copy, 2, o + 1) : 0.f;
+    const float ez_j1 = j + 1 < ny ? ld_field<T>(d, copy, 2, o + P) : 0.f;
+    const float hx = ld_field<T>(d, copy, 3, o) - ld_coef(d, 3, o) * ((ez_j1 - ez) - (ey_k1 - ey));
+    const float hy = ld_field<T>(d, copy, 4, o) - ld_coef(d, 4, o) * ((ex_k1 - ex) - (ez_i1 - ez));
+    const float hz = ld_field<T>(d, copy, 5, o) - ld_coef(d, 5, o) * ((ey_i1 - ey) - (ex_j1 - ex));
+    st_field<T>(d, copy, 3, o, hx);
+    st_field<T>(d, copy, 4, o, hy);
+    st_field<T>(d, copy, 5, o, hz);
+}
+
+// E^{n+1} = E^n + ce curl H^{n+1/2} on entries not tangential to a face.
+template <typename T>
+__global__ void simple_e_kernel(const CavityDesc d, int copy) {
+    const int i = blockIdx.x * BXs + threadIdx.x, j = blockIdx.y * BYs + threadIdx.y, k = blockIdx.z;
+    const int nx = d.nx, ny = d.ny;
+    if (i >= nx || j >= ny) return;
+    const long long P = d.pitch, Z = d.plane;
+    const long long o = (long long)k * Z + (long long)j * P + i;
+    const float hx = ld_field<T>(d, copy, 3, o), hy = ld_field<T>(d, copy, 4, o), hz = ld_field<T>(d, copy, 5, o);
+    if (j >= 1 && k >= 1) {
+        const float c = (hz - ld_field<T>(d, copy, 5, o - P)) - (hy - ld_field<T>(d, copy, 4, o - Z));
+        st_field<T>(d, copy, 0, o, ld_field<T>(d, copy, 0, o) + ld_coef(d, 0, o) * c);
+    }
+    if (i >= 1 && k >= 1) {
+        const float c = (hx - ld_field<T>(d, copy, 3, o - Z)) - (hz - ld_field<T>(d, copy, 5, o - 1));
+        st_field<T>(d, copy, 1, o, ld_field<T>(d, copy, 1, o) + ld_coef(d, 1, o) * c);
+    }
+    if (i >= 1 && j >= 1) {
+        const float c = (hy - ld_field<T>(d, copy, 4, o - 1)) - (hx - ld_field<T>(d, copy, 3, o - P));
+        st_field<T>(d, copy, 2, o, ld_field<T>(d, copy, 2, o) + ld_coef(d, 2, o) * c);
+    }
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 1216;   // 8 x 152 SMs; fixed so that the summation order is reproducible
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kRedThreads / 32; ++i) r += sh[i];
+    return r;
+}
+
+// Per block: sum E^2/ce + sum H (H - ch curl E)/ch (energy without the 1/2 dt/dx factor),
+// sum divE^2 over interior nodes, sum divH^2 over cells.  Cells are visited in a fixed
+// grid-stride order; far-face H terms are appended after the cells.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) reduce_kernel(const CavityDesc d, int copy, double *partial) {
+    __shared__ double sh[kRedThreads / 32];
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const long long P = d.pitch, Z = d.plane;
+    const long long ncell = (long long)nx * ny * nz;
+    double se = 0.0, sde = 0.0, sdh = 0.0;
+    auto F = [&](int f, long long o) -> double { return (double)ld_field<T>(d, copy, f, o); };
+    auto C = [&](int c, long long o) -> double { return (double)ld_coef(d, c, o); };
+    auto faceB = [&](int c, long long fi) -> double {
+        const double ch = d.coef_mode == COEF_SCALAR ? (double)d.ch[c] : (double)d.face_ch[c][fi];
+        return (double)d.face[c][fi] / ch;
+    };
+    for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < ncell;
+         n += (long long)gridDim.x * kRedThreads) {
+        const int i = (int)(n % nx);
+        const long long t = n / nx;
+        const int j = (int)(t % ny), k = (int)(t / ny);
+        const long long o = (long long)k * Z + (long long)j * P + i;
+        const double ex = F(0, o), ey = F(1, o), ez = F(2, o);
+        const double cex = C(0, o), cey = C(1, o), cez = C(2, o);
+        se += ex * ex / cex + ey * ey / cey + ez * ez / cez;
+        const double ex_j1 = j + 1 < ny ? F(0, o + P) : 0.0, ex_k1 = k + 1 < nz ? F(0, o + Z) : 0.0;
+        const double ey_i1 = i + 1 < nx ? F(1, o + 1) : 0.0, ey_k1 = k + 1 < nz ? F(1, o + Z) : 0.0;
+        const double ez_i1 = i + 1 < nx ? F(2, o + 1) : 0.0, ez_j1 = j + 1 < ny ? F(2, o + P) : 0.0;
+        const double hx = F(3, o), hy = F(4, o), hz = F(5, o);
+        const double chx = C(3, o), chy = C(4, o), chz = C(5, o);
+        se += hx * (hx - chx * ((ez_j1 - ez) - (ey_k1 - ey))) / chx;
+        se += hy * (hy - chy * ((ex_k1 - ex) - (ez_i1 - ez))) / chy;
+        se += hz * (hz - chz * ((ey_i1 - ey) - (ex_j1 - ex))) / chz;
+        if (i >= 1 && j >= 1 && k >= 1) {
+            const double de = ex / cex - F(0, o - 1) / C(0, o - 1) + ey / cey - F(1, o - P) / C(1, o - P) +
+                              ez / cez - F(2, o - Z) / C(2, o - Z);
+            sde += de * de;
+        }
+        const double bx1 = i + 1 < nx ? F(3, o + 1) / C(3, o + 1) : faceB(0, (long long)k * ny + j);
+        const double by1 = j + 1 < ny ? F(4, o + P) / C(4, o + P) : faceB(1, (long long)k * nx + i);
+        const double bz1 = k + 1 < nz ? F(5, o + Z) / C(5, o + Z) : faceB(2, (long long)j * nx + i);
+        const double dh = bx1 - hx / chx + by1 - hy / chy + bz1 - hz / chz;
+        sdh += dh * dh;
+    }
+    // constant far-face normal H: curl E vanishes there, so its energy term is H^2/ch
+    const long long nfx = (long long)ny * nz, nfy = (long long)nx * nz, nfz = (long long)nx * ny;
+    for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < nfx + nfy + nfz;
+         n += (long long)gridDim.x * kRedThreads) {
+        int c;
+        long long fi;
+        if (n < nfx) { c = 0; fi = n; }
+        else if (n < nfx + nfy) { c = 1; fi = n - nfx; }
+        else { c = 2; fi = n - nfx - nfy; }
+        const double h = d.face[c][fi];
+        se += h * faceB(c, fi);
+    }
+    const double a = block_sum(se, sh);
+    const double b = block_sum(sde, sh);
+    const double e = block_sum(sdh, sh);
+    if (threadIdx.x == 0) {
+        partial[3 * blockIdx.x + 0] = a;
+        partial[3 * blockIdx.x + 1] = b;
+        partial[3 * blockIdx.x + 2] = e;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) reduce_final_kernel(const double *partial, int nblocks, double *out) {
+    __shared__ double sh[kRedThreads / 32];
+    for (int q = 0; q < 3; ++q) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += kRedThreads) v += partial[3 * b + q];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) out[q] = v;
+    }
+}
+
+template <typename T>
+cudaError_t simple_step_typed(const CavityDesc &d, int copy, cudaStream_t s) {
+    dim3 blk(BXs, BYs), grd((d.nx + BXs - 1) / BXs, (d.ny + BYs - 1) / BYs, d.nz);
+    simple_h_kernel<T><<<grd, blk, 0, s>>>(d, copy);
+    simple_e_kernel<T><<<grd, blk, 0, s>>>(d, copy);
+    return cudaGetLastError();
+}
+
+#define FDTD_STORAGE_DISPATCH(storage, ...)                 \
+    do {                                                     \
+        if (storage == 0) { using T = float; __VA_ARGS__; }         \
+        else if (storage == 1) { using T = __half; __VA_ARGS__; }   \
+        else { using T = __nv_bfloat16; __VA_ARGS__; }              \
+    } while (0)
+
+}  // namespace
+
+cudaError_t launch_pack(int storage, const CavityDesc &d, int copy, int comp, const float *canon, float *face,
+                        cudaStream_t s) {
+    dim3 blk(BXs, BYs), grd((d.nx + 1 + BXs - 1) / BXs, (d.ny + 1 + BYs - 1) / BYs, d.nz + 1);
+    FDTD_STORAGE_DISPATCH(storage, pack_kernel<T><<<grd, blk, 0, s>>>(d, copy, comp, canon, face));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int storage, const CavityDesc &d, int copy, int comp, float *canon, cudaStream_t s) {
+    dim3 blk(BXs, BYs), grd((d.nx + 1 + BXs - 1) / BXs, (d.ny + 1 + BYs - 1) / BYs, d.nz + 1);
+    FDTD_STORAGE_DISPATCH(storage, unpack_kernel<T><<<grd, blk, 0, s>>>(d, copy, comp, canon));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs(const float *canon, int comp, int nx, int ny, int nz, unsigned *out, cudaStream_t s) {
+    dim3 blk(BXs, BYs), grd((nx + 1 + BXs - 1) / BXs, (ny + 1 + BYs - 1) / BYs, nz + 1);
+    maxabs_kernel<<<grd, blk, 0, s>>>(canon, comp, nx, ny, nz, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_simple_step(int storage, const CavityDesc &d, int copy, cudaStream_t s) {
+    cudaError_t e;
+    FDTD_STORAGE_DISPATCH(storage, e = simple_step_typed<T>(d, copy, s));
+    return e;
+}
+
+int reduction_blocks() { return kRedBlocks; }
+
+cudaError_t launch_reductions(int storage, const CavityDesc &d, int copy, double *partial, int nblocks, double *out,
+                              cudaStream_t s) {
+    FDTD_STORAGE_DISPATCH(storage, reduce_kernel<T><<<nblocks, kRedThreads, 0, s>>>(d, copy, partial));
+    reduce_final_kernel<<<1, kRedThreads, 0, s>>>(partial, nblocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fdtd

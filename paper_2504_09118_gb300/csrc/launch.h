@@ -1,0 +1,42 @@
+// Host-side launchers of libfdtd's kernels (C++ linkage, internal to the library).
+#pragma once
+
+#include "fdtd_internal.cuh"
+
+namespace fdtd {
+
+// Canonical FP32 component -> active array (scaled, rounded to storage), tangential E zeroed,
+// far-face normal H -> face array (FP32, after the same rounding).
+cudaError_t launch_pack(int storage, const CavityDesc &d, int copy, int comp, const float *canon, float *face,
+                        cudaStream_t s);
+// Active array (+ face) -> canonical FP32 component, zero outside the extent.
+cudaError_t launch_unpack(int storage, const CavityDesc &d, int copy, int comp, float *canon, cudaStream_t s);
+// max |canon| over the component's extent, as float bits atomically max-ed into *out (must start at 0).
+cudaError_t launch_maxabs(const float *canon, int comp, int nx, int ny, int nz, unsigned *out, cudaStream_t s);
+// One unfused step in place on copy `copy`: H kernel then E kernel.
+cudaError_t launch_simple_step(int storage, const CavityDesc &d, int copy, cudaStream_t s);
+// FP64 reductions: energy terms (sum E^2/ce + sum H.(H - ch curl E)/ch) and the two divergence sums of squares.
+// partial must hold nblocks*3 doubles; out receives 3 doubles {energy_sum, divE2, divH2}.
+cudaError_t launch_reductions(int storage, const CavityDesc &d, int copy, double *partial, int nblocks, double *out,
+                              cudaStream_t s);
+int reduction_blocks();
+
+struct FusedLaunch {
+    const CavityDesc *cav;     // device array
+    const TileDesc *tiles;     // device array
+    int ntiles;
+    int parity;
+    int *status;
+    int tile_y;
+    int stages;
+    int grid;
+    int inject_timeout_us;     // >0: do not issue the CTA 0's first unit; wait limit in us
+};
+// Shared memory bytes and max co-resident CTAs per SM for a fused configuration.
+int fused_smem_bytes(int storage, int tile_y, int stages);
+cudaError_t fused_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
+cudaError_t launch_fused_step(int storage, const FusedLaunch &L, cudaStream_t s);
+// Box sizes used to encode the tensor maps of the fused kernel.
+void fused_box(int storage, int tile_y, int *box_x, int *box_y, int *halo_x);
+
+}  // namespace fdtd
