@@ -38,6 +38,8 @@ import cavity_inputs as ci  # noqa: E402
 WORKLOADS = {
     # name: (nx, ny, nz, leapfrog steps per bench step, storage, sphere seed, field seed)
     "single512": dict(n=(512, 512, 512), steps=200, storage=0, sphere_seed=1, field_seed=2, spheres=32),
+    # small case for ncu captures (fields 0.8 GB > L2, a few launches)
+    "single256": dict(n=(256, 256, 256), steps=20, storage=0, sphere_seed=1, field_seed=2, spheres=8),
     "precision384_f16": dict(n=(384, 384, 384), steps=1000, storage=1, sphere_seed=3, field_seed=4, spheres=32),
     "precision384_bf16": dict(n=(384, 384, 384), steps=1000, storage=2, sphere_seed=3, field_seed=4, spheres=32),
 }

@@ -78,8 +78,9 @@ struct fdtd_ctx {
     unsigned *d_max = nullptr;
     CUtensorMap *d_maps = nullptr;
     CavityDesc *d_desc = nullptr;
-    TileDesc *d_tiles = nullptr;
+    TileRec *d_tiles = nullptr;
     int ntiles = 0, grid = 0, tiles_ty = 0, maps_ty = 0;
+    int ch_uniform = 1;
     fdtd_tuning tuning{};
     std::map<GraphKey, cudaGraphExec_t> graphs;
     int inject_us = 0;
@@ -97,7 +98,7 @@ struct fdtd_batch {
     fdtd_tuning tuning{};
     CavityDesc *d_desc = nullptr;
     int desc_cap = 0;
-    TileDesc *d_tiles = nullptr;
+    TileRec *d_tiles = nullptr;
     int tiles_cap = 0, ntiles = 0, grid = 0;
     bool dirty = true;
     int *d_status = nullptr;
@@ -259,16 +260,40 @@ int choose_zlen(long long cols, int nz, int grid, int zchunk) {
     return bestL;
 }
 
-void append_tiles(std::vector<TileDesc> &v, int cav, int nx, int ny, int nz, int tile_y, int zlen) {
-    for (int z0 = 0; z0 < nz; z0 += zlen)
-        for (int y0 = 0; y0 < ny; y0 += tile_y)
-            for (int x0 = 0; x0 < nx; x0 += kTileX) {
-                TileDesc t{};
-                t.cav = cav;
+TileRec base_rec(const fdtd_ctx *c, int parity_off) {
+    TileRec r{};
+    r.nx = c->nx;
+    r.ny = c->ny;
+    r.pitch = c->pitch;
+    r.mode = c->coef_mode;
+    r.plane = (long long)c->pitch * c->ny;
+    r.ch_uniform = c->ch_uniform;
+    r.parity_off = parity_off;
+    for (int q = 0; q < 3; ++q) {
+        r.ce[q] = c->ce_s[q];
+        r.ch[q] = c->ch_s[q];
+    }
+    r.table = reinterpret_cast<const float4 *>(c->table);
+    r.maps = c->d_maps;
+    for (int f = 0; f < 6; ++f) {
+        r.dst[0][f] = c->fields[0][f];
+        r.dst[1][f] = c->fields[1][f];
+        r.scale[f] = c->scale[f];
+        r.inv_scale[f] = 1.0f / c->scale[f];
+    }
+    return r;
+}
+
+void append_tiles(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y, int zlen) {
+    const TileRec b = base_rec(c, parity_off);
+    for (int z0 = 0; z0 < c->nz; z0 += zlen)
+        for (int y0 = 0; y0 < c->ny; y0 += tile_y)
+            for (int x0 = 0; x0 < c->nx; x0 += kTileX) {
+                TileRec t = b;
                 t.x0 = x0;
                 t.y0 = y0;
                 t.kz0 = z0;
-                t.kz1 = std::min(nz, z0 + zlen);
+                t.kz1 = std::min(c->nz, z0 + zlen);
                 v.push_back(t);
             }
 }
@@ -281,12 +306,12 @@ int build_tiles(fdtd_ctx *c) {
     const int G = num_sms() * s.ctas_per_sm;
     const long long cols = (long long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + s.tile_y - 1) / s.tile_y);
     const int zlen = choose_zlen(cols, c->nz, G, c->tuning.zchunk);
-    std::vector<TileDesc> v;
-    append_tiles(v, 0, c->nx, c->ny, c->nz, s.tile_y, zlen);
+    std::vector<TileRec> v;
+    append_tiles(v, c, 0, s.tile_y, zlen);
     if (c->d_tiles) cudaFree(c->d_tiles);
     c->d_tiles = nullptr;
-    CK(c, cudaMalloc(&c->d_tiles, sizeof(TileDesc) * v.size()));
-    CK(c, cudaMemcpyAsync(c->d_tiles, v.data(), sizeof(TileDesc) * v.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMalloc(&c->d_tiles, sizeof(TileRec) * v.size()));
+    CK(c, cudaMemcpyAsync(c->d_tiles, v.data(), sizeof(TileRec) * v.size(), cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     c->ntiles = (int)v.size();
     c->grid = std::min<int>(c->ntiles, G);
@@ -311,8 +336,7 @@ int launch_one(fdtd_ctx *c, int parity, int inject_us) {
     }
     Shape s = resolve_shape(c->storage, c->tuning);
     FusedLaunch L{};
-    L.cav = c->d_desc;
-    L.tiles = c->d_tiles;
+    L.recs = c->d_tiles;
     L.ntiles = c->ntiles;
     L.parity = parity;
     L.status = c->d_status;
@@ -523,6 +547,13 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
         if (!full) {
             c->coef_mode = COEF_ID8;
             c->ntab = (int)table.size();
+            // ch identical in every cell (per component): the fused kernel then skips its ch lookups
+            c->ch_uniform = 1;
+            for (int n = 1; n < c->ntab; ++n)
+                for (int q = 0; q < 3; ++q)
+                    if (table[n].v[3 + q] != table[0].v[3 + q]) c->ch_uniform = 0;
+            if (c->ch_uniform)
+                for (int q = 0; q < 3; ++q) c->ch_s[q] = table[0].v[3 + q];
             std::vector<float> tab(8 * kMaxTable, 0.f);
             for (int n = 0; n < c->ntab; ++n) {
                 for (int q = 0; q < 3; ++q) {
@@ -842,7 +873,7 @@ static int batch_rebuild(fdtd_batch *b) {
     Shape s = resolve_shape(b->storage, b->tuning);
     const int G = num_sms() * s.ctas_per_sm;
     std::vector<CavityDesc> descs;
-    std::vector<TileDesc> tiles;
+    std::vector<TileRec> tiles;
     long long total_cols_planes = 0;
     for (size_t n = 0; n < b->members.size(); ++n) {
         fdtd_ctx *c = b->members[n];
@@ -855,11 +886,11 @@ static int batch_rebuild(fdtd_batch *b) {
                                     : (int)std::max<long long>(8, total_cols_planes / std::max(1, 8 * G));
     for (size_t n = 0; n < b->members.size(); ++n) {
         fdtd_ctx *c = b->members[n];
-        append_tiles(tiles, (int)n, c->nx, c->ny, c->nz, s.tile_y, std::min(zlen, c->nz));
+        append_tiles(tiles, c, b->off[n], s.tile_y, std::min(zlen, c->nz));
     }
     // longest tiles first, then round-robin over the persistent CTAs
     std::stable_sort(tiles.begin(), tiles.end(),
-                     [](const TileDesc &a, const TileDesc &c) { return (a.kz1 - a.kz0) > (c.kz1 - c.kz0); });
+                     [](const TileRec &a, const TileRec &c) { return (a.kz1 - a.kz0) > (c.kz1 - c.kz0); });
     if ((int)descs.size() > b->desc_cap) {
         cudaFree(b->d_desc);
         b->desc_cap = std::max<int>((int)descs.size(), 2 * b->desc_cap);
@@ -869,7 +900,7 @@ static int batch_rebuild(fdtd_batch *b) {
     if ((int)tiles.size() > b->tiles_cap) {
         cudaFree(b->d_tiles);
         b->tiles_cap = std::max<int>((int)tiles.size(), 2 * b->tiles_cap);
-        if (cudaMalloc(&b->d_tiles, sizeof(TileDesc) * b->tiles_cap) != cudaSuccess)
+        if (cudaMalloc(&b->d_tiles, sizeof(TileRec) * b->tiles_cap) != cudaSuccess)
             return bfail(b, FDTD_ERR_OOM, "tile alloc");
     }
     if (!descs.empty())
@@ -877,7 +908,7 @@ static int batch_rebuild(fdtd_batch *b) {
                             b->stream) != cudaSuccess)
             return bfail(b, FDTD_ERR_CUDA, "descriptor upload");
     if (!tiles.empty())
-        if (cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(), cudaMemcpyHostToDevice,
+        if (cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(TileRec) * tiles.size(), cudaMemcpyHostToDevice,
                             b->stream) != cudaSuccess)
             return bfail(b, FDTD_ERR_CUDA, "tile upload");
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "sync");
@@ -890,8 +921,7 @@ static int batch_rebuild(fdtd_batch *b) {
 static int batch_launch(fdtd_batch *b, int parity) {
     Shape s = resolve_shape(b->storage, b->tuning);
     FusedLaunch L{};
-    L.cav = b->d_desc;
-    L.tiles = b->d_tiles;
+    L.recs = b->d_tiles;
     L.ntiles = b->ntiles;
     L.parity = parity;
     L.status = b->d_status;

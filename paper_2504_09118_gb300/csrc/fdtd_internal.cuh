@@ -100,6 +100,23 @@ struct TileDesc {
     int pad[3];
 };
 
+// Everything the fused kernel needs about one tile, built on the host (256 bytes,
+// copied by the kernel's producer warp into shared memory when the tile starts).
+struct alignas(16) TileRec {
+    int x0, y0, kz0, kz1;
+    int nx, ny, pitch, mode;     // mode: CoefMode (COEF_SCALAR or COEF_ID8)
+    long long plane;             // pitch * ny
+    int ch_uniform;              // ch is the same in every cell (scalars in ch[])
+    int parity_off;              // source copy = launch parity ^ parity_off
+    float ce[3], ch[3];          // scalar coefficients (COEF_SCALAR; ch also when ch_uniform)
+    const float4 *table;         // COEF_ID8: per id two float4: (ce x,y,z,0), (ch x,y,z,0)
+    const CUtensorMap *maps;     // kMapsPerCavity tensor maps in global memory
+    void *dst[2][6];             // both copies of the six active arrays
+    float scale[6], inv_scale[6];
+    int pad[6];
+};
+static_assert(sizeof(TileRec) == 256, "TileRec must be 256 bytes");
+
 // Status bits latched by kernels into the device status word.
 enum : int { STATUS_TIMEOUT = 1, STATUS_BADINDEX = 2 };
 
@@ -117,14 +134,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// One bounded poll: the thread may sleep in hardware (up to the hint, 0.1 ms) until the phase completes.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
         : "memory");
     return ok != 0;
 }
@@ -141,7 +159,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (;;) {
-        for (int r = 0; r < 64; ++r)
+        for (int r = 0; r < 4; ++r)
             if (mbar_try_wait(bar, parity)) return true;
         if (global_timer_ns() - t0 > limit_ns) return false;
     }

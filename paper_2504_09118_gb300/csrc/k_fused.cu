@@ -1,29 +1,38 @@
 // Fused Yee step (H then E in one pass over HBM) for sm_103a.
 //
 // The update is Eq. 2 of the paper in the order of Listing 1: H^{n+1/2} from
-// curl E^n, then E^{n+1} from curl H^{n+1/2}, PEC by index predicates (tangential
-// E is never updated; normal H on a face sees a zero curl).  Reads copy s of
-// the six fields and writes copy 1-s (ping-pong), so a tile can recompute the
-// H values on its lower x/y halo from unmodified E instead of waiting for the
-// neighbouring tile.
+// curl E^n, then E^{n+1} from curl H^{n+1/2}; PEC by index predicates
+// (tangential E is never updated, normal H on a face sees a zero curl).  A
+// step reads copy s of the six fields and writes copy 1-s (ping-pong), so a
+// tile recomputes the H values on its lower x/y halo from unmodified E rather
+// than waiting for the neighbouring tile.
 //
-// Work decomposition: a tile is a 64 x TY column of cells over planes
-// [kz0, kz1).  Persistent CTAs take tiles round-robin (tile = blockIdx.x +
-// m * gridDim.x) and march each tile upward in z.  Plane k needs "unit" k (all
-// six fields and the material id at plane k, with a halo of one cell in x and
-// y, padded in x to the 16-byte TMA granule) and unit k+1 (E at k+1 for the z
-// derivative of the H update).  One thread streams units into an S-slot shared
-// memory ring with 3-D TMA loads completing on per-slot mbarriers; the stream
-// runs on across tile boundaries so the pipeline never drains between tiles.
-// H^{n+1/2}(k-1) at the thread's own cells stays in registers for the
-// z-derivative of the E update; a tile starting at kz0 > 0 first recomputes
-// plane kz0-1 (a "prologue" plane).
+// Work: a tile is a 64 x TY column of cells over planes [kz0, kz1); persistent
+// CTAs take tiles round-robin and march each one upward in z.  Plane k needs
+// "unit" k (six fields + material id at plane k, one-cell halo in x and y,
+// the x halo widened to the 16-byte TMA granule) and unit k+1 (E at k+1 for
+// the z derivative of H).
 //
-// Per plane and cell, HBM sees 6 loads and 6 stores of the storage type plus
-// one material-id byte (24+24+1 = 49 B/cell in FP32); halo rows are re-read
-// from L2.  Every mbarrier wait is bounded in wall time (globaltimer); on
-// expiry the CTA latches STATUS_TIMEOUT, drains its in-flight copies (bounded
-// again) and exits.
+// Warp roles (TY + 2 warps):
+//   * producer warp: walks the CTA's tiles, copies each tile's record (host
+//     built: origin, extents, pointers, scales, coefficients) into a small
+//     shared ring, and streams units into an S-slot ring with 3-D TMA loads
+//     (full[s] mbarrier: expect_tx + complete_tx), gated by empty[s];
+//   * TY row warps: warp w owns row y = w: it computes H on 2 x-adjacent cells
+//     per lane (64 cells), keeps them and the loaded E in registers, publishes
+//     H to a double-buffered shared plane, and after one named barrier updates
+//     E on the same cells; H^{n+1/2}(k-1) of its cells stays in registers for
+//     the z derivative of the next plane;
+//   * halo warp: H on the row y = -1 and the column x = -1 (needed by the E
+//     update of the first row/column), phase A only.
+// One named barrier per plane; a consumer warp releases a unit (arrive on
+// empty[s]) once it no longer reads it.
+//
+// Bytes per cell and plane: 6 loads + 6 stores of the storage type + one
+// material-id byte (49 B in FP32, 25 B in 16-bit storage); halo rows are
+// re-read from L2.  Every mbarrier wait is bounded in wall time (globaltimer):
+// on expiry the CTA latches STATUS_TIMEOUT, the producer drains its in-flight
+// copies (bounded again) and all warps exit.
 #include "launch.h"
 
 namespace fdtd {
@@ -31,18 +40,18 @@ namespace fdtd {
 namespace {
 
 constexpr int TX = kTileX;
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any healthy TMA latency
+constexpr int NTR = 8;                              // tile-record ring entries
+constexpr uint64_t kWaitLimitNs = 2000000000ull;    // 2 s: far beyond any healthy TMA latency
 
 template <typename T> struct FusedGeom {
-    static constexpr int HX = 16 / (int)sizeof(T);     // x halo rounded to a 16-byte TMA granule
-    static constexpr int BX = TX + 2 * HX;             // field box width (elements)
-    static constexpr int IDX_HALO = 16;                // id box starts 16 bytes left of x0
-    static constexpr int IBX = TX + IDX_HALO;          // id box width (bytes)
+    static constexpr int HX = 16 / (int)sizeof(T);  // x halo rounded to a 16-byte TMA granule
+    static constexpr int BX = TX + 2 * HX;          // field box width (elements)
+    static constexpr int IDX_HALO = 16;             // id box starts 16 bytes left of x0
+    static constexpr int IBX = TX + IDX_HALO;       // id box width (bytes)
 };
 
 struct FusedParams {
-    const CavityDesc *cav;
-    const TileDesc *tiles;
+    const TileRec *recs;
     int ntiles;
     int parity;
     int *status;
@@ -61,323 +70,370 @@ template <int TY>
 __host__ __device__ constexpr int id_box_bytes() {
     return FusedGeom<float>::IBX * (TY + 2);
 }
-// Each TMA destination box starts on a 128-byte boundary.
 template <typename T, int TY>
-__host__ __device__ constexpr int field_box_stride() {
+__host__ __device__ constexpr int field_box_stride() {   // each TMA destination on a 128-byte boundary
     return align_up(field_box_bytes<T, TY>(), 128);
 }
 template <typename T, int TY>
 __host__ __device__ constexpr int slot_bytes() {
     return align_up(6 * field_box_stride<T, TY>() + id_box_bytes<TY>(), 128);
 }
+constexpr int HP = TX + 2;   // shared H plane row pitch; column x + 2 holds x (x = -1 .. TX-1)
 template <int TY>
-__host__ __device__ constexpr int hplane_floats() {
-    return 3 * (TY + 1) * (TX + 1);
+__host__ __device__ constexpr int hbuf_floats() {
+    return 3 * (TY + 1) * HP;
 }
 template <typename T, int TY>
 __host__ __device__ constexpr int smem_bytes(int stages) {
-    return 128 /*barriers*/ + kMaxTable * 8 * 4 /*table*/ + align_up(hplane_floats<TY>() * 4, 128) +
+    return 128 /*barriers*/ + NTR * (int)sizeof(TileRec) + align_up(2 * hbuf_floats<TY>() * 4, 128) +
            stages * slot_bytes<T, TY>() + 128 /*alignment slack*/;
 }
+template <int TY>
+__host__ __device__ constexpr int block_threads() {
+    return (TY + 2) * 32;
+}
 
-// Producer-side view of one tile (kept in registers by the issuing thread).
-struct ProdTile {
-    const CUtensorMap *maps;
-    int src;
-    int has_id;
-    int x0, y0, k, kend;   // next plane to issue, last plane (inclusive)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Named barrier over `nthreads` threads that also ORs a predicate across them.
+__device__ __forceinline__ bool bar_sync_or(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "barrier.cta.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+// Two adjacent storage elements <-> two physical floats.
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+    __device__ __forceinline__ static float2 ld(const float *p, float) { return *reinterpret_cast<const float2 *>(p); }
+    __device__ __forceinline__ static float ld1(const float *p, float) { return *p; }
+    __device__ __forceinline__ static void st(float *p, float a, float b, float) {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
+};
+template <> struct Pair<__half> {
+    __device__ __forceinline__ static float2 ld(const __half *p, float is) {
+        float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        return make_float2(v.x * is, v.y * is);
+    }
+    __device__ __forceinline__ static float ld1(const __half *p, float is) { return __half2float(*p) * is; }
+    __device__ __forceinline__ static void st(__half *p, float a, float b, float s) {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a * s, b * s);
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    __device__ __forceinline__ static float2 ld(const __nv_bfloat16 *p, float is) {
+        float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+        return make_float2(v.x * is, v.y * is);
+    }
+    __device__ __forceinline__ static float ld1(const __nv_bfloat16 *p, float is) {
+        return __bfloat162float(*p) * is;
+    }
+    __device__ __forceinline__ static void st(__nv_bfloat16 *p, float a, float b, float s) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a * s, b * s);
+    }
 };
 
 template <typename T, int TY>
-__device__ __forceinline__ void load_prod_tile(const FusedParams &P, int t, ProdTile &pt) {
-    const TileDesc td = P.tiles[t];
-    const CavityDesc &cd = P.cav[td.cav];
-    pt.maps = cd.maps;
-    pt.src = P.parity ^ cd.parity_off;
-    pt.has_id = cd.coef_mode == COEF_ID8;
-    pt.x0 = td.x0;
-    pt.y0 = td.y0;
-    pt.k = td.kz0 > 0 ? td.kz0 - 1 : td.kz0;
-    pt.kend = td.kz1;
-}
-
-template <typename T, int TY, int NT>
-__global__ void __launch_bounds__(NT) fused_step_kernel(const FusedParams P) {
+__global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_step_kernel(const FusedParams P) {
     using G = FusedGeom<T>;
-    constexpr int HX = G::HX, BX = G::BX, BY = TY + 2, HP = TX + 1;
-    constexpr int FB = field_box_bytes<T, TY>();      // bytes the TMA writes per field box
-    constexpr int FS = field_box_stride<T, TY>();     // byte stride between boxes in a slot
-    constexpr int FE = FS / (int)sizeof(T);           // element stride between boxes
-    constexpr int R = TX * TY / NT;                   // interior cells per thread per plane
-    static_assert(TX * TY % NT == 0, "tile must split evenly over the block");
+    constexpr int HX = G::HX, BX = G::BX;
+    constexpr int FB = field_box_bytes<T, TY>();
+    constexpr int FS = field_box_stride<T, TY>();
+    constexpr int FE = FS / (int)sizeof(T);
+    constexpr int NCW = TY + 1;                 // consumer warps: TY row warps + halo warp
+    constexpr int NCT = NCW * 32;
+    constexpr int HB = hbuf_floats<TY>();       // floats per H plane buffer
+    constexpr int HC = (TY + 1) * HP;           // floats per component in a buffer
 
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    float *tab = reinterpret_cast<float *>(smem + 128);
-    float *hn = tab + kMaxTable * 8;
-    unsigned char *slots = reinterpret_cast<unsigned char *>(hn) + align_up(hplane_floats<TY>() * 4, 128);
+    uint64_t *empty = full + 8;
+    TileRec *recs = reinterpret_cast<TileRec *>(smem + 128);
+    float *hbuf = reinterpret_cast<float *>(smem + 128 + NTR * sizeof(TileRec));
+    unsigned char *slots = reinterpret_cast<unsigned char *>(hbuf) + align_up(2 * HB * 4, 128);
 
-    const int tid = threadIdx.x;
-    const int S = P.stages;
-    const int SB = P.slot_bytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = P.stages, SB = P.slot_bytes;
+    const bool inject = P.inject_timeout_us > 0 && blockIdx.x == 0;
+    const uint64_t lim = inject ? (uint64_t)P.inject_timeout_us * 1000ull : kWaitLimitNs;
 
-    if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
         fence_mbarrier_init();
         fence_proxy_async_smem();
     }
     __syncthreads();
 
-    // ---------------- producer state (thread 0 only)
-    int p_t = blockIdx.x;
-    int issued = 0, released = 0;
-    ProdTile pt{};
-    const bool inject = P.inject_timeout_us > 0 && blockIdx.x == 0;
-    const uint64_t wait_limit = inject ? (uint64_t)P.inject_timeout_us * 1000ull : kWaitLimitNs;
-
-    auto issue_more = [&]() {
-        while (issued - released < S && p_t < P.ntiles) {
-            const int slot = issued % S;
-            unsigned char *dst = slots + slot * SB;
-            uint64_t *bar = &full[slot];
-            if (inject && issued == 0) {
-                // fault injection: leave slot 0's barrier un-armed so its wait runs out
-            } else {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, 6 * FB + (pt.has_id ? id_box_bytes<TY>() : 0));
-                const CUtensorMap *m = pt.maps + pt.src * 6;
+    // =========================================================== producer warp
+    if (warp == TY + 1) {
+        int issued = 0, m = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x, ++m) {
+            TileRec *rec = &recs[m % NTR];
+            int kb = 0, kz1 = 0;
+            for (int k = 0;; ++k) {
+                const int s = issued % S;
+                if (issued >= S) {
+                    const bool w = mbar_wait_bounded(&empty[s], ((issued / S) - 1) & 1, lim);
+                    if (!__all_sync(0xffffffffu, w)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                if (k == 0) {   // first unit of the tile: publish the tile record (after the slot wait)
+                    const uint32_t *src = reinterpret_cast<const uint32_t *>(P.recs + t);
+                    uint32_t *dst = reinterpret_cast<uint32_t *>(rec);
+                    for (int q = lane; q < (int)(sizeof(TileRec) / 4); q += 32) dst[q] = __ldg(src + q);
+                    __syncwarp();
+                    kb = rec->kz0 > 0 ? rec->kz0 - 1 : rec->kz0;
+                    kz1 = rec->kz1;
+                }
+                const int kk = kb + k;
+                if (lane == 0 && !(inject && issued == 0)) {
+                    const int src_copy = P.parity ^ rec->parity_off;
+                    const bool has_id = rec->mode == COEF_ID8;
+                    unsigned char *dst = slots + s * SB;
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? id_box_bytes<TY>() : 0));
+                    const CUtensorMap *mp = rec->maps + src_copy * 6;
 #pragma unroll
-                for (int f = 0; f < 6; ++f) tma_load_3d(dst + f * FS, m + f, pt.x0 - HX, pt.y0 - 1, pt.k, bar);
-                if (pt.has_id)
-                    tma_load_3d(dst + 6 * FS, pt.maps + 12, pt.x0 - G::IDX_HALO, pt.y0 - 1, pt.k, bar);
-            }
-            ++issued;
-            if (++pt.k > pt.kend) {
-                p_t += gridDim.x;
-                if (p_t < P.ntiles) load_prod_tile<T, TY>(P, p_t, pt);
+                    for (int f = 0; f < 6; ++f)
+                        tma_load_3d(dst + f * FS, mp + f, rec->x0 - HX, rec->y0 - 1, kk, &full[s]);
+                    if (has_id)
+                        tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->x0 - G::IDX_HALO, rec->y0 - 1, kk, &full[s]);
+                }
+                __syncwarp();
+                ++issued;
+                if (kk >= kz1) break;
             }
         }
-    };
-    if (tid == 0 && p_t < P.ntiles) {
-        load_prod_tile<T, TY>(P, p_t, pt);
-        issue_more();
+        if (!ok && lane == 0) {
+            atomicOr(P.status, STATUS_TIMEOUT);
+            // drain this CTA's copies still in flight before its shared memory goes away
+            for (int u = issued > S ? issued - S : 0; u < issued; ++u) {
+                if (inject && u == 0) continue;
+                mbar_wait_bounded(&full[u % S], (u / S) & 1, kWaitLimitNs);
+            }
+        }
+        return;
     }
 
-    // ---------------- consumers (all threads, thread 0 included)
-    int u_base = 0;
-    int loaded_tab_cav = -1;
-    float hprev_x[R], hprev_y[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) hprev_x[r] = hprev_y[r] = 0.f;
+    // =========================================================== consumer warps
+    const bool halo = warp == TY;
+    const int y = halo ? -1 : warp;             // row of this warp (tile-local)
+    const int x = 2 * lane;                     // first of the lane's two cells
+    const int bx = x + HX, by = y + 1;          // position in a field box
+    int u = 0, m = 0, hb = 0;
+    float2 hpx = make_float2(0.f, 0.f), hpy = make_float2(0.f, 0.f);   // H^{n+1/2}(k-1) of own cells
 
-    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
-        const TileDesc td = P.tiles[t];
-        const CavityDesc &cd = P.cav[td.cav];
-        const int nx = cd.nx, ny = cd.ny;
-        const int pitch = cd.pitch;
-        const long long plane = cd.plane;
-        const int mode = cd.coef_mode;
-        const int dstc = (P.parity ^ cd.parity_off) ^ 1;
-        float inv_s[6], sc[6];
+    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x, ++m) {
+        bool ok = mbar_wait_bounded(&full[u % S], (u / S) & 1, lim);   // the tile record is valid from here
+        const TileRec *rec = &recs[m % NTR];
+        const int x0 = rec->x0, y0 = rec->y0, kz0 = rec->kz0, kz1 = rec->kz1;
+        const int nx = rec->nx, ny = rec->ny;
+        const long long pitch = rec->pitch, plane = rec->plane;
+        const bool id_mode = rec->mode == COEF_ID8;
+        const bool ch_uni = rec->ch_uniform != 0;
+        const float4 *table = rec->table;
+        const int dstc = (P.parity ^ rec->parity_off) ^ 1;
+        T *dst[6];
+        float sc[6], is[6];
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
-            inv_s[f] = cd.inv_scale[f];
-            sc[f] = cd.scale[f];
+            dst[f] = static_cast<T *>(rec->dst[dstc][f]);
+            sc[f] = rec->scale[f];
+            is[f] = rec->inv_scale[f];
         }
-        T *dstp[6];
-#pragma unroll
-        for (int f = 0; f < 6; ++f) dstp[f] = static_cast<T *>(cd.buf[dstc][f]);
-        float ce_s[3], ch_s[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ce_s[c] = cd.ce[c];
-            ch_s[c] = cd.ch[c];
-        }
-        if (mode == COEF_ID8 && loaded_tab_cav != td.cav) {
-            for (int e = tid; e < cd.ntab * 8; e += NT) tab[e] = cd.table[e];
-            loaded_tab_cav = td.cav;   // made visible by the barrier at the top of the first iteration
-        }
-        const int kb = td.kz0 > 0 ? td.kz0 - 1 : td.kz0;
+        const float ce_s0 = rec->ce[0], ce_s1 = rec->ce[1], ce_s2 = rec->ce[2];
+        const float ch_s0 = rec->ch[0], ch_s1 = rec->ch[1], ch_s2 = rec->ch[2];
+        const int gj = y0 + y;
+        const int gi = x0 + x;
+        const int kb = kz0 > 0 ? kz0 - 1 : kz0;
 
-        for (int k = kb; k < td.kz1; ++k) {
-            const int ua = u_base + (k - kb), ub = ua + 1;
-            bool ok = mbar_wait_bounded(&full[ua % S], (ua / S) & 1, wait_limit);
-            ok = ok && mbar_wait_bounded(&full[ub % S], (ub / S) & 1, wait_limit);
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) {
-                    atomicOr(P.status, STATUS_TIMEOUT);
-                    // drain this CTA's copies still in flight (bounded again) before shared memory goes away
-                    for (int u = released; u < issued; ++u) {
-                        if (inject && u == 0) continue;
-                        mbar_wait_bounded(&full[u % S], (u / S) & 1, kWaitLimitNs);
+        for (int k = kb; k < kz1; ++k) {
+            const int ua = u, ub = u + 1;
+            ok = ok && mbar_wait_bounded(&full[ua % S], (ua / S) & 1, lim);
+            ok = ok && mbar_wait_bounded(&full[ub % S], (ub / S) & 1, lim);
+            const bool prologue = k < kz0;
+            const T *A = reinterpret_cast<const T *>(slots + (ua % S) * SB);
+            const T *B = reinterpret_cast<const T *>(slots + (ub % S) * SB);
+            const uint8_t *ida = slots + (ua % S) * SB + 6 * FS;
+            float *hn = hbuf + hb * HB;
+            float2 ex = make_float2(0.f, 0.f), ey = ex, ez = ex, hx = ex, hy = ex, hz = ex;
+            uint32_t idpair = 0;
+            float4 ce_a = make_float4(ce_s0, ce_s1, ce_s2, 0.f), ce_b = ce_a;   // ce of the two cells
+
+            // ---------------- phase A: H^{n+1/2} on own cells (+ the halo column for the halo warp)
+            if (ok) {
+                auto at = [&](const T *base, int f, int xx, int yy) { return base + f * FE + yy * BX + xx; };
+                ex = Pair<T>::ld(at(A, 0, bx, by), is[0]);
+                ey = Pair<T>::ld(at(A, 1, bx, by), is[1]);
+                ez = Pair<T>::ld(at(A, 2, bx, by), is[2]);
+                const float2 ex_y1 = Pair<T>::ld(at(A, 0, bx, by + 1), is[0]);
+                const float2 ez_y1 = Pair<T>::ld(at(A, 2, bx, by + 1), is[2]);
+                const float ey_x2 = Pair<T>::ld1(at(A, 1, bx + 2, by), is[1]);
+                const float ez_x2 = Pair<T>::ld1(at(A, 2, bx + 2, by), is[2]);
+                const float2 exb = Pair<T>::ld(at(B, 0, bx, by), is[0]);
+                const float2 eyb = Pair<T>::ld(at(B, 1, bx, by), is[1]);
+                hx = Pair<T>::ld(at(A, 3, bx, by), is[3]);
+                hy = Pair<T>::ld(at(A, 4, bx, by), is[4]);
+                hz = Pair<T>::ld(at(A, 5, bx, by), is[5]);
+                float2 chx = make_float2(ch_s0, ch_s0), chy = make_float2(ch_s1, ch_s1),
+                       chz = make_float2(ch_s2, ch_s2);
+                if (id_mode) {
+                    idpair = *reinterpret_cast<const uint16_t *>(ida + by * G::IBX + x + G::IDX_HALO);
+                    if (!halo) {   // issued here, consumed in phase B: the L1 latency hides behind phase A
+                        ce_a = __ldg(&table[2 * (idpair & 0xff)]);
+                        ce_b = __ldg(&table[2 * (idpair >> 8)]);
+                    }
+                    if (!ch_uni) {
+                        const float4 a = __ldg(&table[2 * (idpair & 0xff) + 1]);
+                        const float4 b = __ldg(&table[2 * (idpair >> 8) + 1]);
+                        chx = make_float2(a.x, b.x);
+                        chy = make_float2(a.y, b.y);
+                        chz = make_float2(a.z, b.z);
                     }
                 }
-                __syncthreads();
+                hx.x -= chx.x * ((ez_y1.x - ez.x) - (eyb.x - ey.x));
+                hx.y -= chx.y * ((ez_y1.y - ez.y) - (eyb.y - ey.y));
+                hy.x -= chy.x * ((exb.x - ex.x) - (ez.y - ez.x));
+                hy.y -= chy.y * ((exb.y - ex.y) - (ez_x2 - ez.y));
+                hz.x -= chz.x * ((ey.y - ey.x) - (ex_y1.x - ex.x));
+                hz.y -= chz.y * ((ey_x2 - ey.y) - (ex_y1.y - ex.y));
+                const int o = by * HP + x + 2;
+                *reinterpret_cast<float2 *>(hn + o) = hx;
+                *reinterpret_cast<float2 *>(hn + HC + o) = hy;
+                *reinterpret_cast<float2 *>(hn + 2 * HC + o) = hz;
+                if (!halo && !prologue && gj < ny && gi < nx) {
+                    const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                    Pair<T>::st(dst[3] + g, hx.x, hx.y, sc[3]);
+                    Pair<T>::st(dst[4] + g, hy.x, hy.y, sc[4]);
+                    Pair<T>::st(dst[5] + g, hz.x, hz.y, sc[5]);
+                }
+                if (halo && lane < TY) {
+                    // column x = -1, row yy = lane: Hy and Hz (used by Ez and Ey at x = 0)
+                    const int yy = lane, cbx = HX - 1, cby = yy + 1;
+                    const float cex_ = Pair<T>::ld1(at(A, 0, cbx, cby), is[0]);
+                    const float cey_ = Pair<T>::ld1(at(A, 1, cbx, cby), is[1]);
+                    const float cez_ = Pair<T>::ld1(at(A, 2, cbx, cby), is[2]);
+                    const float cey_x1 = Pair<T>::ld1(at(A, 1, cbx + 1, cby), is[1]);
+                    const float cez_x1 = Pair<T>::ld1(at(A, 2, cbx + 1, cby), is[2]);
+                    const float cex_y1 = Pair<T>::ld1(at(A, 0, cbx, cby + 1), is[0]);
+                    const float cexb = Pair<T>::ld1(at(B, 0, cbx, cby), is[0]);
+                    float cchy = ch_s1, cchz = ch_s2;
+                    if (id_mode && !ch_uni) {
+                        const float4 a = __ldg(&table[2 * ida[cby * G::IBX + G::IDX_HALO - 1] + 1]);
+                        cchy = a.y;
+                        cchz = a.z;
+                    }
+                    const float chy_ = Pair<T>::ld1(at(A, 4, cbx, cby), is[4]) -
+                                       cchy * ((cexb - cex_) - (cez_x1 - cez_));
+                    const float chz_ = Pair<T>::ld1(at(A, 5, cbx, cby), is[5]) -
+                                       cchz * ((cey_x1 - cey_) - (cex_y1 - cex_));
+                    hn[HC + cby * HP + 1] = chy_;
+                    hn[2 * HC + cby * HP + 1] = chz_;
+                }
+            }
+            if (bar_sync_or(1, NCT, !ok)) {
+                if (threadIdx.x == 0) atomicOr(P.status, STATUS_TIMEOUT);
                 return;
             }
-            const unsigned char *sa = slots + (ua % S) * SB;
-            const unsigned char *sbb = slots + (ub % S) * SB;
-            const T *Ea = reinterpret_cast<const T *>(sa);             // fields 0..5 of plane k
-            const T *Eb = reinterpret_cast<const T *>(sbb);            // fields 0..2 of plane k+1
-            const uint8_t *ida = sa + 6 * FS;
-            const bool prologue = k < td.kz0;
-            const long long zoff = (long long)k * plane;
 
-            auto F = [&](const T *base, int f, int bx, int by) -> float {
-                float v = Storage<T>::load(base[f * FE + by * BX + bx]);
-                if (Storage<T>::scaled) v *= inv_s[f];
-                return v;
-            };
-            auto coef = [&](int x, int y, int c) -> float {   // c: 0..2 ce, 3..5 ch
-                if (mode == COEF_ID8) {
-                    const int id = ida[(y + 1) * G::IBX + (x + G::IDX_HALO)];
-                    return tab[id * 8 + (c < 3 ? c : c + 1)];
+            // ---------------- phase B: E^{n+1} on own cells (row warps)
+            if (!halo && !prologue) {
+                const int o = by * HP + x + 2;
+                const float2 hx_ym = *reinterpret_cast<const float2 *>(hn + o - HP);
+                const float2 hz_ym = *reinterpret_cast<const float2 *>(hn + 2 * HC + o - HP);
+                const float hy_xm = hn[HC + o - 1];
+                const float hz_xm = hn[2 * HC + o - 1];
+                const float2 cex = make_float2(ce_a.x, ce_b.x), cey = make_float2(ce_a.y, ce_b.y),
+                             cez = make_float2(ce_a.z, ce_b.z);
+                if (gj >= 1 && k >= 1) {
+                    ex.x += cex.x * ((hz.x - hz_ym.x) - (hy.x - hpy.x));
+                    ex.y += cex.y * ((hz.y - hz_ym.y) - (hy.y - hpy.y));
                 }
-                return c < 3 ? ce_s[c] : ch_s[c - 3];
-            };
-            // H^{n+1/2} at local (x, y) of plane k, from unit k (E, H) and unit k+1 (E).
-            auto h_update = [&](int x, int y, float &hx, float &hy, float &hz) {
-                const int bx = x + HX, by = y + 1;
-                const float ex = F(Ea, 0, bx, by), ey = F(Ea, 1, bx, by), ez = F(Ea, 2, bx, by);
-                const float ex_y1 = F(Ea, 0, bx, by + 1), ez_y1 = F(Ea, 2, bx, by + 1);
-                const float ey_x1 = F(Ea, 1, bx + 1, by), ez_x1 = F(Ea, 2, bx + 1, by);
-                const float ex_z1 = F(Eb, 0, bx, by), ey_z1 = F(Eb, 1, bx, by);
-                hx = F(Ea, 3, bx, by) - coef(x, y, 3) * ((ez_y1 - ez) - (ey_z1 - ey));
-                hy = F(Ea, 4, bx, by) - coef(x, y, 4) * ((ex_z1 - ex) - (ez_x1 - ez));
-                hz = F(Ea, 5, bx, by) - coef(x, y, 5) * ((ey_x1 - ey) - (ex_y1 - ex));
-            };
-
-            // ---- phase A: H on the interior (kept in registers and shared memory, stored) and the lower halo
-            float hxi[R], hyi[R], hzi[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int p = tid + r * NT;
-                const int x = p % TX, y = p / TX;
-                h_update(x, y, hxi[r], hyi[r], hzi[r]);
-            }
-            if (!prologue) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int p = tid + r * NT;
-                    const int x = p % TX, y = p / TX;
-                    const int o = (y + 1) * HP + (x + 1);
-                    hn[o] = hxi[r];
-                    hn[(TY + 1) * HP + o] = hyi[r];
-                    hn[2 * (TY + 1) * HP + o] = hzi[r];
-                    const int gi = td.x0 + x, gj = td.y0 + y;
-                    if (gi < nx && gj < ny) {
-                        const long long go = zoff + (long long)gj * pitch + gi;
-                        dstp[3][go] = Storage<T>::store(Storage<T>::scaled ? hxi[r] * sc[3] : hxi[r]);
-                        dstp[4][go] = Storage<T>::store(Storage<T>::scaled ? hyi[r] * sc[4] : hyi[r]);
-                        dstp[5][go] = Storage<T>::store(Storage<T>::scaled ? hzi[r] * sc[5] : hzi[r]);
-                    }
-                }
-                // halo: row y = -1 (Hx, Hz used by Ex/Ez) and column x = -1 (Hy, Hz used by Ey/Ez)
-                for (int h = tid; h < TX + TY; h += NT) {
-                    const int x = h < TX ? h : -1;
-                    const int y = h < TX ? -1 : h - TX;
-                    float a, b, c;
-                    h_update(x, y, a, b, c);
-                    const int o = (y + 1) * HP + (x + 1);
-                    hn[o] = a;
-                    hn[(TY + 1) * HP + o] = b;
-                    hn[2 * (TY + 1) * HP + o] = c;
+                if (gi >= 1 && k >= 1) ey.x += cey.x * ((hx.x - hpx.x) - (hz.x - hz_xm));
+                if (k >= 1) ey.y += cey.y * ((hx.y - hpx.y) - (hz.y - hz.x));
+                if (gi >= 1 && gj >= 1) ez.x += cez.x * ((hy.x - hy_xm) - (hx.x - hx_ym.x));
+                if (gj >= 1) ez.y += cez.y * ((hy.y - hy.x) - (hx.y - hx_ym.y));
+                if (gj < ny && gi < nx) {
+                    const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                    Pair<T>::st(dst[0] + g, ex.x, ex.y, sc[0]);
+                    Pair<T>::st(dst[1] + g, ey.x, ey.y, sc[1]);
+                    Pair<T>::st(dst[2] + g, ez.x, ez.y, sc[2]);
                 }
             }
-            __syncthreads();
-
-            // ---- phase B: E^{n+1} on the interior
-            if (!prologue) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int p = tid + r * NT;
-                    const int x = p % TX, y = p / TX;
-                    const int gi = td.x0 + x, gj = td.y0 + y;
-                    const int o = (y + 1) * HP + (x + 1);
-                    const float hx = hxi[r], hy = hyi[r], hz = hzi[r];
-                    const float hx_ym = hn[o - HP];
-                    const float hz_ym = hn[2 * (TY + 1) * HP + o - HP];
-                    const float hy_xm = hn[(TY + 1) * HP + o - 1];
-                    const float hz_xm = hn[2 * (TY + 1) * HP + o - 1];
-                    const int bx = x + HX, by = y + 1;
-                    float ex = F(Ea, 0, bx, by), ey = F(Ea, 1, bx, by), ez = F(Ea, 2, bx, by);
-                    if (gj >= 1 && k >= 1) ex += coef(x, y, 0) * ((hz - hz_ym) - (hy - hprev_y[r]));
-                    if (gi >= 1 && k >= 1) ey += coef(x, y, 1) * ((hx - hprev_x[r]) - (hz - hz_xm));
-                    if (gi >= 1 && gj >= 1) ez += coef(x, y, 2) * ((hy - hy_xm) - (hx - hx_ym));
-                    if (gi < nx && gj < ny) {
-                        const long long go = zoff + (long long)gj * pitch + gi;
-                        dstp[0][go] = Storage<T>::store(Storage<T>::scaled ? ex * sc[0] : ex);
-                        dstp[1][go] = Storage<T>::store(Storage<T>::scaled ? ey * sc[1] : ey);
-                        dstp[2][go] = Storage<T>::store(Storage<T>::scaled ? ez * sc[2] : ez);
-                    }
-                }
+            hpx = hx;
+            hpy = hy;
+            // ---------------- release the units this warp no longer reads
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[ua % S]);
+                if (k == kz1 - 1) mbar_arrive(&empty[ub % S]);
             }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                hprev_x[r] = hxi[r];
-                hprev_y[r] = hyi[r];
-            }
-            __syncthreads();
-            if (tid == 0) {
-                released += (k == td.kz1 - 1) ? 2 : 1;
-                issue_more();
-            }
+            u += (k == kz1 - 1) ? 2 : 1;
+            hb ^= 1;
         }
-        u_base += td.kz1 - kb + 1;
     }
-}
-
-template <typename T, int TY>
-constexpr int threads_for() {
-    return TX * TY / 2;
 }
 
 template <typename T, int TY>
 cudaError_t launch_typed(const FusedLaunch &L, cudaStream_t s) {
-    constexpr int NT = threads_for<T, TY>();
     const int smem = smem_bytes<T, TY>(L.stages);
-    auto kern = fused_step_kernel<T, TY, NT>;
+    auto kern = fused_step_kernel<T, TY>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     FusedParams P;
-    P.cav = L.cav;
-    P.tiles = L.tiles;
+    P.recs = L.recs;
     P.ntiles = L.ntiles;
     P.parity = L.parity;
     P.status = L.status;
     P.stages = L.stages;
     P.slot_bytes = slot_bytes<T, TY>();
     P.inject_timeout_us = L.inject_timeout_us;
-    kern<<<L.grid, NT, smem, s>>>(P);
+    kern<<<L.grid, block_threads<TY>(), smem, s>>>(P);
     return cudaGetLastError();
 }
 
 template <typename T, int TY>
 cudaError_t occupancy_typed(int stages, int *n) {
-    constexpr int NT = threads_for<T, TY>();
     const int smem = smem_bytes<T, TY>(stages);
-    auto kern = fused_step_kernel<T, TY, NT>;
+    auto kern = fused_step_kernel<T, TY>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, NT, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, block_threads<TY>(), smem);
 }
 
-#define FDTD_DISPATCH(storage, tile_y, ...)                                                         \
-    do {                                                                                             \
-        if (storage == 0) {                                                                          \
-            if (tile_y == 4) { using T = float; constexpr int TY = 4; __VA_ARGS__; }                        \
-            else if (tile_y == 8) { using T = float; constexpr int TY = 8; __VA_ARGS__; }                   \
-            else if (tile_y == 16) { using T = float; constexpr int TY = 16; __VA_ARGS__; }                 \
-        } else if (storage == 1) {                                                                   \
-            if (tile_y == 4) { using T = __half; constexpr int TY = 4; __VA_ARGS__; }                       \
-            else if (tile_y == 8) { using T = __half; constexpr int TY = 8; __VA_ARGS__; }                  \
-            else if (tile_y == 16) { using T = __half; constexpr int TY = 16; __VA_ARGS__; }                \
-        } else if (storage == 2) {                                                                   \
-            if (tile_y == 4) { using T = __nv_bfloat16; constexpr int TY = 4; __VA_ARGS__; }                \
-            else if (tile_y == 8) { using T = __nv_bfloat16; constexpr int TY = 8; __VA_ARGS__; }           \
-            else if (tile_y == 16) { using T = __nv_bfloat16; constexpr int TY = 16; __VA_ARGS__; }         \
-        }                                                                                            \
+#define FDTD_DISPATCH(storage, tile_y, ...)                                                       \
+    do {                                                                                          \
+        if (storage == 0) {                                                                       \
+            if (tile_y == 4) { using T = float; constexpr int TY = 4; __VA_ARGS__; }              \
+            else if (tile_y == 8) { using T = float; constexpr int TY = 8; __VA_ARGS__; }         \
+            else if (tile_y == 16) { using T = float; constexpr int TY = 16; __VA_ARGS__; }       \
+        } else if (storage == 1) {                                                                \
+            if (tile_y == 4) { using T = __half; constexpr int TY = 4; __VA_ARGS__; }             \
+            else if (tile_y == 8) { using T = __half; constexpr int TY = 8; __VA_ARGS__; }        \
+            else if (tile_y == 16) { using T = __half; constexpr int TY = 16; __VA_ARGS__; }      \
+        } else if (storage == 2) {                                                                \
+            if (tile_y == 4) { using T = __nv_bfloat16; constexpr int TY = 4; __VA_ARGS__; }      \
+            else if (tile_y == 8) { using T = __nv_bfloat16; constexpr int TY = 8; __VA_ARGS__; } \
+            else if (tile_y == 16) { using T = __nv_bfloat16; constexpr int TY = 16; __VA_ARGS__; } \
+        }                                                                                         \
     } while (0)
 
 }  // namespace
@@ -396,6 +452,7 @@ cudaError_t fused_occupancy(int storage, int tile_y, int stages, int *ctas_per_s
 
 cudaError_t launch_fused_step(int storage, const FusedLaunch &L, cudaStream_t s) {
     if (L.ntiles <= 0) return cudaSuccess;
+    if (L.stages < 3 || L.stages > 8) return cudaErrorInvalidValue;
     cudaError_t e = cudaErrorInvalidValue;
     FDTD_DISPATCH(storage, L.tile_y, e = launch_typed<T, TY>(L, s));
     return e;

@@ -22,8 +22,7 @@ cudaError_t launch_reductions(int storage, const CavityDesc &d, int copy, double
 int reduction_blocks();
 
 struct FusedLaunch {
-    const CavityDesc *cav;     // device array
-    const TileDesc *tiles;     // device array
+    const TileRec *recs;       // device array, one record per tile
     int ntiles;
     int parity;
     int *status;
