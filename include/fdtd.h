@@ -207,6 +207,32 @@ FDTD_API const char *fdtd_batch_last_error(const fdtd_batch *b);
  * Fault injection on the host side of a wait: no GPU fault is involved. */
 FDTD_API int fdtd_debug_inject_timeout(fdtd_ctx *ctx, int limit_us);
 
+/*
+ * fdtd_energy_static - the energy W of fdtd_energy, computed from caller-owned
+ * device arrays by a path that allocates no device memory.  (The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * where they need the energy, e.g. inside work they capture into a CUDA graph,
+ * under a fixed pre-reserved memory budget, or in a loop that cannot afford
+ * cudaMalloc's implicit synchronisation.)
+ *   nx, ny, nz, dt, dx  cavity size and steps as for fdtd_create; nz <= 8191.
+ *   f[6]                device pointers to canonical FP32 Ex..Hz (taken as given:
+ *                       tangential E is not zeroed here).
+ *   ce[3], ch[3]        device pointers to canonical FP32 coefficients, or NULL
+ *                       for vacuum (dt/dx).
+ *   W                   device pointer to one double that receives the energy.
+ *   cuda_stream         stream to run on (NULL = legacy default stream).
+ * Asynchronous: W is valid once the stream reaches this point.  Partial sums
+ * live in a fixed 64 KiB device array inside the library (one double per z
+ * plane), shared by every call: calls whose kernels overlap on the GPU race and
+ * must be serialised by the caller.  The first call on a device looks up that
+ * array's address (cudaGetSymbolAddress) and should come before any stream
+ * capture.  Returns FDTD_ERR_ARG (message via fdtd_last_error(NULL)) for NULL
+ * pointers, non-positive sizes or nz > 8191.
+ */
+FDTD_API int fdtd_energy_static(int nx, int ny, int nz, double dt, double dx, const float *const f[6],
+                                const float *const ce[3], const float *const ch[3], double *W,
+                                void *cuda_stream);
+
 /* fdtd_version - library version string. */
 FDTD_API const char *fdtd_version(void);
 

@@ -29,7 +29,7 @@ EXPORTS = (
     "fdtd_sync", "fdtd_set_tuning", "fdtd_steps_done", "fdtd_device_bytes", "fdtd_destroy", "fdtd_last_error",
     "fdtd_batch_create", "fdtd_batch_add", "fdtd_batch_remove", "fdtd_batch_step", "fdtd_batch_set_tuning",
     "fdtd_batch_size", "fdtd_batch_sync", "fdtd_batch_destroy", "fdtd_batch_last_error",
-    "fdtd_debug_inject_timeout", "fdtd_version",
+    "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static",
 )
 
 
@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
             L.fdtd_batch_last_error.restype = ctypes.c_char_p
             L.fdtd_debug_inject_timeout.argtypes = [vp, i]
             L.fdtd_version.restype = ctypes.c_char_p
+            L.fdtd_energy_static.argtypes = [i, i, i, d, d, vp, vp, vp, vp, vp]
             _LIB = L
         return _LIB
 
@@ -239,6 +240,34 @@ def fdtd_last_error(ctx=None) -> str:
 
 def fdtd_debug_inject_timeout(ctx, limit_us: int) -> None:
     _check(ctx, lib().fdtd_debug_inject_timeout(ctx, int(limit_us)))
+
+
+def fdtd_energy_static(nx: int, ny: int, nz: int, dt: float, dx: float, fields, W, ce=None, ch=None,
+                       stream=None) -> None:
+    """Energy of canonical FP32 device tensors into the float64 device tensor W, allocating nothing.
+
+    For callers that cannot allocate device memory where they need the energy.  The
+    library's fixed scratch is shared by all calls: do not overlap calls on the GPU.
+    """
+    shape = (nz + 1, ny + 1, nx + 1)
+    fptr, _ = _field_ptrs(fields, shape, True, False)
+    if str(W.dtype) != "torch.float64" or not W.is_cuda:
+        raise ValueError("W must be a float64 CUDA tensor")
+
+    def coef(c):
+        if c is None:
+            return None
+        if len(c) != 3:
+            raise ValueError("coefficients are three device tensors")
+        for t in c:
+            if str(t.dtype) != "torch.float32" or not t.is_contiguous() or t.numel() != int(np.prod(shape)):
+                raise ValueError("coefficients must be contiguous float32 tensors of the canonical size")
+        return ctypes.cast(_ptr_array([t.data_ptr() for t in c]), ctypes.c_void_p)
+
+    rc = lib().fdtd_energy_static(int(nx), int(ny), int(nz), float(dt), float(dx),
+                                  ctypes.cast(_ptr_array(fptr), ctypes.c_void_p), coef(ce), coef(ch),
+                                  W.data_ptr(), _stream_handle(stream))
+    _check(None, rc)
 
 
 def fdtd_version() -> str:

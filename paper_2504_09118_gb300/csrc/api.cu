@@ -385,6 +385,11 @@ struct TupleHash {
 
 }  // namespace
 
+namespace fdtd {
+// Message returned by fdtd_last_error(NULL) on this thread (used by context-free entry points).
+void set_last_error(const char *msg) { g_create_error = msg; }
+}  // namespace fdtd
+
 extern "C" {
 
 const char *fdtd_version(void) { return "fdtd-gb300 0.1 (sm_103a)"; }
