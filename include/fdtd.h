@@ -53,8 +53,9 @@ typedef struct fdtd_ctx fdtd_ctx;
 typedef struct fdtd_batch fdtd_batch;
 
 /* Storage precision of the fields in device memory.  Arithmetic is always FP32;
- * FP16/BF16 store each component scaled by a power of two s_c chosen at
- * fdtd_set_fields (s_c = 2^(8 - ceil(log2 max|F_c|))), rounded to nearest even. */
+ * FP16/BF16 store E scaled by a power of two s_E and H by s_H, chosen at
+ * fdtd_set_fields (s = 2^(8 - ceil(log2 max|F|)) over the three components of
+ * the field), rounded to nearest even. */
 enum fdtd_storage { FDTD_F32 = 0, FDTD_F16 = 1, FDTD_BF16 = 2 };
 
 enum fdtd_status {

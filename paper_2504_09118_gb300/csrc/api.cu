@@ -65,7 +65,9 @@ struct fdtd_ctx {
     int coef_mode = COEF_SCALAR;
     float ce_s[3] = {}, ch_s[3] = {};
     uint8_t *id = nullptr;
-    float *table = nullptr;
+    float *table = nullptr, *inv_table = nullptr;
+    float *table_fused = nullptr;     // table with the storage-scale ratios folded in (fused kernel)
+    std::vector<float> host_table;    // 8 floats per entry: ce xyz, pad, ch xyz, pad
     int ntab = 0;
     float *coef_full[6] = {};
     float scale[6] = {1, 1, 1, 1, 1, 1};
@@ -166,6 +168,11 @@ CavityDesc make_desc(const fdtd_ctx *c, int parity_off) {
     }
     d.id = c->id;
     d.table = c->table;
+    d.inv_table = c->inv_table;
+    for (int q = 0; q < 3; ++q) {
+        d.inv_ce[q] = 1.0f / c->ce_s[q];
+        d.inv_ch[q] = 1.0f / c->ch_s[q];
+    }
     d.maps = c->d_maps;
     return d;
 }
@@ -269,17 +276,16 @@ TileRec base_rec(const fdtd_ctx *c, int parity_off) {
     r.plane = (long long)c->pitch * c->ny;
     r.ch_uniform = c->ch_uniform;
     r.parity_off = parity_off;
+    const float re = c->scale[0] / c->scale[3];   // s_E / s_H (1 for FP32)
     for (int q = 0; q < 3; ++q) {
-        r.ce[q] = c->ce_s[q];
-        r.ch[q] = c->ch_s[q];
+        r.ce[q] = c->ce_s[q] * re;
+        r.ch[q] = c->ch_s[q] / re;
     }
-    r.table = reinterpret_cast<const float4 *>(c->table);
+    r.table = reinterpret_cast<const float4 *>(c->table_fused);
     r.maps = c->d_maps;
     for (int f = 0; f < 6; ++f) {
         r.dst[0][f] = c->fields[0][f];
         r.dst[1][f] = c->fields[1][f];
-        r.scale[f] = c->scale[f];
-        r.inv_scale[f] = 1.0f / c->scale[f];
     }
     return r;
 }
@@ -569,6 +575,20 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
             if ((e = dmalloc(c, (void **)&c->table, tab.size() * 4)) != cudaSuccess) return cfail("table alloc", e);
             if ((e = cudaMemcpy(c->table, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cfail("table copy", e);
+            if ((e = dmalloc(c, (void **)&c->table_fused, tab.size() * 4)) != cudaSuccess)
+                return cfail("table alloc", e);
+            if ((e = cudaMemcpy(c->table_fused, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cfail("table copy", e);
+            c->host_table = tab;
+            std::vector<float> inv(tab.size(), 0.f);
+            for (int n = 0; n < c->ntab; ++n)
+                for (int q = 0; q < 3; ++q) {
+                    inv[8 * n + q] = (float)(1.0 / (double)tab[8 * n + q]);
+                    inv[8 * n + 4 + q] = (float)(1.0 / (double)tab[8 * n + 4 + q]);
+                }
+            if ((e = dmalloc(c, (void **)&c->inv_table, inv.size() * 4)) != cudaSuccess) return cfail("table alloc", e);
+            if ((e = cudaMemcpy(c->inv_table, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cfail("table copy", e);
             if ((e = dmalloc(c, (void **)&c->id, c->arr_elems)) != cudaSuccess) return cfail("id alloc", e);
             if ((e = cudaMemset(c->id, 0, c->arr_elems)) != cudaSuccess) return cfail("memset", e);
             if ((e = cudaMemcpy2D(c->id, c->pitch, ids.data(), nx, nx, (size_t)ny * nz, cudaMemcpyHostToDevice)) !=
@@ -625,6 +645,8 @@ void fdtd_destroy(fdtd_ctx *c) {
     for (int a = 0; a < 6; ++a) cudaFree(c->coef_full[a]);
     cudaFree(c->id);
     cudaFree(c->table);
+    cudaFree(c->inv_table);
+    cudaFree(c->table_fused);
     cudaFree(c->d_status);
     cudaFree(c->d_partial);
     cudaFree(c->d_out);
@@ -676,12 +698,31 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
         unsigned hm[6];
         CK(c, cudaMemcpyAsync(hm, c->d_max, sizeof hm, cudaMemcpyDeviceToHost, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
-        for (int q = 0; q < 6; ++q) {
-            float m;
-            memcpy(&m, &hm[q], 4);
-            if (!std::isfinite(m)) return fail(c, FDTD_ERR_ARG, "field %d holds a non-finite value", q);
-            c->scale[q] = m > 0.f ? std::ldexp(1.0f, 8 - (int)std::ceil(std::log2((double)m))) : 1.0f;
+        // one power-of-two scale for the three E components and one for the three H components
+        for (int g = 0; g < 2; ++g) {
+            float mx = 0.f;
+            for (int q = 3 * g; q < 3 * g + 3; ++q) {
+                float m;
+                memcpy(&m, &hm[q], 4);
+                if (!std::isfinite(m)) return fail(c, FDTD_ERR_ARG, "field %d holds a non-finite value", q);
+                mx = std::max(mx, m);
+            }
+            const float sc = mx > 0.f ? std::ldexp(1.0f, 8 - (int)std::ceil(std::log2((double)mx))) : 1.0f;
+            for (int q = 3 * g; q < 3 * g + 3; ++q) c->scale[q] = sc;
         }
+        if (c->table_fused) {
+            const float re = c->scale[0] / c->scale[3];
+            std::vector<float> tf = c->host_table;
+            for (int n = 0; n < c->ntab; ++n)
+                for (int q = 0; q < 3; ++q) {
+                    tf[8 * n + q] = c->host_table[8 * n + q] * re;
+                    tf[8 * n + 4 + q] = c->host_table[8 * n + 4 + q] / re;
+                }
+            CK(c, cudaMemcpyAsync(c->table_fused, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, c->stream));
+            CK(c, cudaStreamSynchronize(c->stream));
+        }
+        c->tiles_ty = 0;   // tile records embed the folded coefficients: rebuild them
+        drop_graphs(c->graphs);
     }
     if (int rc = upload_desc(c)) return rc;
     CavityDesc d = make_desc(c, 0);
@@ -774,10 +815,10 @@ int fdtd_sync(fdtd_ctx *c) {
     return check_status(c, c->d_status, c->stream);
 }
 
-static int run_reductions(fdtd_ctx *c, double out[3]) {
+static int run_reductions(fdtd_ctx *c, int what, double out[3]) {
     if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
     if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
-    CK(c, launch_reductions(c->storage, make_desc(c, 0), c->cur, c->d_partial, reduction_blocks(), c->d_out,
+    CK(c, launch_reductions(c->storage, make_desc(c, 0), c->cur, what, c->d_partial, reduction_blocks(), c->d_out,
                             c->stream));
     CK(c, cudaMemcpyAsync(out, c->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -787,7 +828,7 @@ static int run_reductions(fdtd_ctx *c, double out[3]) {
 int fdtd_energy(fdtd_ctx *c, double *W) {
     if (!c || !W) return fail(c, FDTD_ERR_ARG, "NULL argument");
     double o[3];
-    if (int rc = run_reductions(c, o)) return rc;
+    if (int rc = run_reductions(c, 0, o)) return rc;
     *W = 0.5 * (c->dt / c->dx) * o[0];
     return FDTD_OK;
 }
@@ -795,7 +836,7 @@ int fdtd_energy(fdtd_ctx *c, double *W) {
 int fdtd_divergence(fdtd_ctx *c, double *de, double *dh) {
     if (!c || !de || !dh) return fail(c, FDTD_ERR_ARG, "NULL argument");
     double o[3];
-    if (int rc = run_reductions(c, o)) return rc;
+    if (int rc = run_reductions(c, 1, o)) return rc;
     *de = std::sqrt(o[1]);
     *dh = std::sqrt(o[2]);
     return FDTD_OK;

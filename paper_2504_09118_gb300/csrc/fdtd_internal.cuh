@@ -68,6 +68,8 @@ struct CavityDesc {
     const CUtensorMap *maps;// fused kernel: kMapsPerCavity tensor maps (global memory)
     const float *face[3];   // constant normal H on the far faces: Hx[k][j] at i=nx, Hy[k][i] at j=ny, Hz[j][i] at k=nz
     const float *face_ch[3];// ch at those positions (NULL in COEF_SCALAR mode)
+    const float *inv_table; // COEF_ID8: ntab x 8 floats of reciprocals (1/ce xyz, pad, 1/ch xyz, pad)
+    float inv_ce[3], inv_ch[3];  // COEF_SCALAR reciprocals
 };
 
 // Physical (unscaled) value of field f at linear offset off of copy `copy`.
@@ -83,6 +85,13 @@ template <typename T>
 __device__ __forceinline__ void st_field(const CavityDesc &d, int copy, int f, long long off, float x) {
     if (Storage<T>::scaled) x *= d.scale[f];
     static_cast<T *>(d.buf[copy][f])[off] = Storage<T>::store(x);
+}
+
+// 1/ce (c = 0..2) or 1/ch (c = 3..5) of the cell at active offset off.
+__device__ __forceinline__ float ld_inv_coef(const CavityDesc &d, int c, long long off) {
+    if (d.coef_mode == COEF_SCALAR) return c < 3 ? d.inv_ce[c] : d.inv_ch[c - 3];
+    if (d.coef_mode == COEF_ID8) return d.inv_table[8 * d.id[off] + (c < 3 ? c : c + 1)];
+    return 1.0f / d.coef[c][off];
 }
 
 // ce (c = 0..2) or ch (c = 3..5) of the cell at active offset off.
@@ -108,12 +117,13 @@ struct alignas(16) TileRec {
     long long plane;             // pitch * ny
     int ch_uniform;              // ch is the same in every cell (scalars in ch[])
     int parity_off;              // source copy = launch parity ^ parity_off
+    // Coefficients in storage units: with E stored as s_E*E and H as s_H*H, ce*s_E/s_H and
+    // ch*s_H/s_E (both 1 for FP32 storage), so the kernel never rescales a field value.
     float ce[3], ch[3];          // scalar coefficients (COEF_SCALAR; ch also when ch_uniform)
-    const float4 *table;         // COEF_ID8: per id two float4: (ce x,y,z,0), (ch x,y,z,0)
+    const float4 *table;         // COEF_ID8: per id two float4: (ce x,y,z,0), (ch x,y,z,0), folded
     const CUtensorMap *maps;     // kMapsPerCavity tensor maps in global memory
     void *dst[2][6];             // both copies of the six active arrays
-    float scale[6], inv_scale[6];
-    int pad[6];
+    int pad[18];
 };
 static_assert(sizeof(TileRec) == 256, "TileRec must be 256 bytes");
 

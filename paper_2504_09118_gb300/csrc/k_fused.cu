@@ -111,35 +111,33 @@ __device__ __forceinline__ bool bar_sync_or(int id, int nthreads, bool pred) {
     return r != 0;
 }
 
-// Two adjacent storage elements <-> two physical floats.
+// Two adjacent storage elements <-> two floats.  16-bit storage holds E scaled by s_E and
+// H scaled by s_H; the kernel computes in those scaled units (the ratio s_E/s_H is folded
+// into the coefficients of its tile records), so loads and stores are plain conversions.
 template <typename T> struct Pair;
 template <> struct Pair<float> {
-    __device__ __forceinline__ static float2 ld(const float *p, float) { return *reinterpret_cast<const float2 *>(p); }
-    __device__ __forceinline__ static float ld1(const float *p, float) { return *p; }
-    __device__ __forceinline__ static void st(float *p, float a, float b, float) {
+    __device__ __forceinline__ static float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    __device__ __forceinline__ static float ld1(const float *p) { return *p; }
+    __device__ __forceinline__ static void st(float *p, float a, float b) {
         *reinterpret_cast<float2 *>(p) = make_float2(a, b);
     }
 };
 template <> struct Pair<__half> {
-    __device__ __forceinline__ static float2 ld(const __half *p, float is) {
-        float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
-        return make_float2(v.x * is, v.y * is);
+    __device__ __forceinline__ static float2 ld(const __half *p) {
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
     }
-    __device__ __forceinline__ static float ld1(const __half *p, float is) { return __half2float(*p) * is; }
-    __device__ __forceinline__ static void st(__half *p, float a, float b, float s) {
-        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a * s, b * s);
+    __device__ __forceinline__ static float ld1(const __half *p) { return __half2float(*p); }
+    __device__ __forceinline__ static void st(__half *p, float a, float b) {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
     }
 };
 template <> struct Pair<__nv_bfloat16> {
-    __device__ __forceinline__ static float2 ld(const __nv_bfloat16 *p, float is) {
-        float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
-        return make_float2(v.x * is, v.y * is);
+    __device__ __forceinline__ static float2 ld(const __nv_bfloat16 *p) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
     }
-    __device__ __forceinline__ static float ld1(const __nv_bfloat16 *p, float is) {
-        return __bfloat162float(*p) * is;
-    }
-    __device__ __forceinline__ static void st(__nv_bfloat16 *p, float a, float b, float s) {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a * s, b * s);
+    __device__ __forceinline__ static float ld1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    __device__ __forceinline__ static void st(__nv_bfloat16 *p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
     }
 };
 
@@ -182,14 +180,15 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
     // =========================================================== producer warp
     if (warp == TY + 1) {
         int issued = 0, m = 0;
+        int s = 0;           // slot of the next unit
+        uint32_t rnd = 0;    // parity of the ring round of the next unit
         bool ok = true;
         for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x, ++m) {
             TileRec *rec = &recs[m % NTR];
             int kb = 0, kz1 = 0;
             for (int k = 0;; ++k) {
-                const int s = issued % S;
-                if (issued >= S) {
-                    const bool w = mbar_wait_bounded(&empty[s], ((issued / S) - 1) & 1, lim);
+                if (issued >= S) {   // wait until unit issued - S (same slot, previous round) is released
+                    const bool w = mbar_wait_bounded(&empty[s], rnd ^ 1u, lim);
                     if (!__all_sync(0xffffffffu, w)) {
                         ok = false;
                         break;
@@ -219,6 +218,10 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                 }
                 __syncwarp();
                 ++issued;
+                if (++s == S) {
+                    s = 0;
+                    rnd ^= 1u;
+                }
                 if (kk >= kz1) break;
             }
         }
@@ -238,11 +241,12 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
     const int y = halo ? -1 : warp;             // row of this warp (tile-local)
     const int x = 2 * lane;                     // first of the lane's two cells
     const int bx = x + HX, by = y + 1;          // position in a field box
-    int u = 0, m = 0, hb = 0;
+    int sa = 0, m = 0, hb = 0;   // slot of the current unit
+    uint32_t pa = 0;             // phase parity of that slot
     float2 hpx = make_float2(0.f, 0.f), hpy = make_float2(0.f, 0.f);   // H^{n+1/2}(k-1) of own cells
 
     for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x, ++m) {
-        bool ok = mbar_wait_bounded(&full[u % S], (u / S) & 1, lim);   // the tile record is valid from here
+        bool ok = mbar_wait_bounded(&full[sa], pa, lim);   // the tile record is valid from here
         const TileRec *rec = &recs[m % NTR];
         const int x0 = rec->x0, y0 = rec->y0, kz0 = rec->kz0, kz1 = rec->kz1;
         const int nx = rec->nx, ny = rec->ny;
@@ -252,13 +256,8 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
         const float4 *table = rec->table;
         const int dstc = (P.parity ^ rec->parity_off) ^ 1;
         T *dst[6];
-        float sc[6], is[6];
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            dst[f] = static_cast<T *>(rec->dst[dstc][f]);
-            sc[f] = rec->scale[f];
-            is[f] = rec->inv_scale[f];
-        }
+        for (int f = 0; f < 6; ++f) dst[f] = static_cast<T *>(rec->dst[dstc][f]);
         const float ce_s0 = rec->ce[0], ce_s1 = rec->ce[1], ce_s2 = rec->ce[2];
         const float ch_s0 = rec->ch[0], ch_s1 = rec->ch[1], ch_s2 = rec->ch[2];
         const int gj = y0 + y;
@@ -266,13 +265,18 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
         const int kb = kz0 > 0 ? kz0 - 1 : kz0;
 
         for (int k = kb; k < kz1; ++k) {
-            const int ua = u, ub = u + 1;
-            ok = ok && mbar_wait_bounded(&full[ua % S], (ua / S) & 1, lim);
-            ok = ok && mbar_wait_bounded(&full[ub % S], (ub / S) & 1, lim);
+            int sb = sa + 1;
+            uint32_t pb = pa;
+            if (sb == S) {
+                sb = 0;
+                pb ^= 1u;
+            }
+            ok = ok && mbar_wait_bounded(&full[sa], pa, lim);
+            ok = ok && mbar_wait_bounded(&full[sb], pb, lim);
             const bool prologue = k < kz0;
-            const T *A = reinterpret_cast<const T *>(slots + (ua % S) * SB);
-            const T *B = reinterpret_cast<const T *>(slots + (ub % S) * SB);
-            const uint8_t *ida = slots + (ua % S) * SB + 6 * FS;
+            const T *A = reinterpret_cast<const T *>(slots + sa * SB);
+            const T *B = reinterpret_cast<const T *>(slots + sb * SB);
+            const uint8_t *ida = slots + sa * SB + 6 * FS;
             float *hn = hbuf + hb * HB;
             float2 ex = make_float2(0.f, 0.f), ey = ex, ez = ex, hx = ex, hy = ex, hz = ex;
             uint32_t idpair = 0;
@@ -281,26 +285,22 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
             // ---------------- phase A: H^{n+1/2} on own cells (+ the halo column for the halo warp)
             if (ok) {
                 auto at = [&](const T *base, int f, int xx, int yy) { return base + f * FE + yy * BX + xx; };
-                ex = Pair<T>::ld(at(A, 0, bx, by), is[0]);
-                ey = Pair<T>::ld(at(A, 1, bx, by), is[1]);
-                ez = Pair<T>::ld(at(A, 2, bx, by), is[2]);
-                const float2 ex_y1 = Pair<T>::ld(at(A, 0, bx, by + 1), is[0]);
-                const float2 ez_y1 = Pair<T>::ld(at(A, 2, bx, by + 1), is[2]);
-                const float ey_x2 = Pair<T>::ld1(at(A, 1, bx + 2, by), is[1]);
-                const float ez_x2 = Pair<T>::ld1(at(A, 2, bx + 2, by), is[2]);
-                const float2 exb = Pair<T>::ld(at(B, 0, bx, by), is[0]);
-                const float2 eyb = Pair<T>::ld(at(B, 1, bx, by), is[1]);
-                hx = Pair<T>::ld(at(A, 3, bx, by), is[3]);
-                hy = Pair<T>::ld(at(A, 4, bx, by), is[4]);
-                hz = Pair<T>::ld(at(A, 5, bx, by), is[5]);
+                ex = Pair<T>::ld(at(A, 0, bx, by));
+                ey = Pair<T>::ld(at(A, 1, bx, by));
+                ez = Pair<T>::ld(at(A, 2, bx, by));
+                const float2 ex_y1 = Pair<T>::ld(at(A, 0, bx, by + 1));
+                const float2 ez_y1 = Pair<T>::ld(at(A, 2, bx, by + 1));
+                const float ey_x2 = Pair<T>::ld1(at(A, 1, bx + 2, by));
+                const float ez_x2 = Pair<T>::ld1(at(A, 2, bx + 2, by));
+                const float2 exb = Pair<T>::ld(at(B, 0, bx, by));
+                const float2 eyb = Pair<T>::ld(at(B, 1, bx, by));
+                hx = Pair<T>::ld(at(A, 3, bx, by));
+                hy = Pair<T>::ld(at(A, 4, bx, by));
+                hz = Pair<T>::ld(at(A, 5, bx, by));
                 float2 chx = make_float2(ch_s0, ch_s0), chy = make_float2(ch_s1, ch_s1),
                        chz = make_float2(ch_s2, ch_s2);
                 if (id_mode) {
                     idpair = *reinterpret_cast<const uint16_t *>(ida + by * G::IBX + x + G::IDX_HALO);
-                    if (!halo) {   // issued here, consumed in phase B: the L1 latency hides behind phase A
-                        ce_a = __ldg(&table[2 * (idpair & 0xff)]);
-                        ce_b = __ldg(&table[2 * (idpair >> 8)]);
-                    }
                     if (!ch_uni) {
                         const float4 a = __ldg(&table[2 * (idpair & 0xff) + 1]);
                         const float4 b = __ldg(&table[2 * (idpair >> 8) + 1]);
@@ -321,29 +321,29 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                 *reinterpret_cast<float2 *>(hn + 2 * HC + o) = hz;
                 if (!halo && !prologue && gj < ny && gi < nx) {
                     const long long g = (long long)k * plane + (long long)gj * pitch + gi;
-                    Pair<T>::st(dst[3] + g, hx.x, hx.y, sc[3]);
-                    Pair<T>::st(dst[4] + g, hy.x, hy.y, sc[4]);
-                    Pair<T>::st(dst[5] + g, hz.x, hz.y, sc[5]);
+                    Pair<T>::st(dst[3] + g, hx.x, hx.y);
+                    Pair<T>::st(dst[4] + g, hy.x, hy.y);
+                    Pair<T>::st(dst[5] + g, hz.x, hz.y);
                 }
                 if (halo && lane < TY) {
                     // column x = -1, row yy = lane: Hy and Hz (used by Ez and Ey at x = 0)
                     const int yy = lane, cbx = HX - 1, cby = yy + 1;
-                    const float cex_ = Pair<T>::ld1(at(A, 0, cbx, cby), is[0]);
-                    const float cey_ = Pair<T>::ld1(at(A, 1, cbx, cby), is[1]);
-                    const float cez_ = Pair<T>::ld1(at(A, 2, cbx, cby), is[2]);
-                    const float cey_x1 = Pair<T>::ld1(at(A, 1, cbx + 1, cby), is[1]);
-                    const float cez_x1 = Pair<T>::ld1(at(A, 2, cbx + 1, cby), is[2]);
-                    const float cex_y1 = Pair<T>::ld1(at(A, 0, cbx, cby + 1), is[0]);
-                    const float cexb = Pair<T>::ld1(at(B, 0, cbx, cby), is[0]);
+                    const float cex_ = Pair<T>::ld1(at(A, 0, cbx, cby));
+                    const float cey_ = Pair<T>::ld1(at(A, 1, cbx, cby));
+                    const float cez_ = Pair<T>::ld1(at(A, 2, cbx, cby));
+                    const float cey_x1 = Pair<T>::ld1(at(A, 1, cbx + 1, cby));
+                    const float cez_x1 = Pair<T>::ld1(at(A, 2, cbx + 1, cby));
+                    const float cex_y1 = Pair<T>::ld1(at(A, 0, cbx, cby + 1));
+                    const float cexb = Pair<T>::ld1(at(B, 0, cbx, cby));
                     float cchy = ch_s1, cchz = ch_s2;
                     if (id_mode && !ch_uni) {
                         const float4 a = __ldg(&table[2 * ida[cby * G::IBX + G::IDX_HALO - 1] + 1]);
                         cchy = a.y;
                         cchz = a.z;
                     }
-                    const float chy_ = Pair<T>::ld1(at(A, 4, cbx, cby), is[4]) -
+                    const float chy_ = Pair<T>::ld1(at(A, 4, cbx, cby)) -
                                        cchy * ((cexb - cex_) - (cez_x1 - cez_));
-                    const float chz_ = Pair<T>::ld1(at(A, 5, cbx, cby), is[5]) -
+                    const float chz_ = Pair<T>::ld1(at(A, 5, cbx, cby)) -
                                        cchz * ((cey_x1 - cey_) - (cex_y1 - cex_));
                     hn[HC + cby * HP + 1] = chy_;
                     hn[2 * HC + cby * HP + 1] = chz_;
@@ -361,6 +361,10 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                 const float2 hz_ym = *reinterpret_cast<const float2 *>(hn + 2 * HC + o - HP);
                 const float hy_xm = hn[HC + o - 1];
                 const float hz_xm = hn[2 * HC + o - 1];
+                if (id_mode) {
+                    ce_a = __ldg(&table[2 * (idpair & 0xff)]);
+                    ce_b = __ldg(&table[2 * (idpair >> 8)]);
+                }
                 const float2 cex = make_float2(ce_a.x, ce_b.x), cey = make_float2(ce_a.y, ce_b.y),
                              cez = make_float2(ce_a.z, ce_b.z);
                 if (gj >= 1 && k >= 1) {
@@ -373,20 +377,26 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                 if (gj >= 1) ez.y += cez.y * ((hy.y - hy.x) - (hx.y - hx_ym.y));
                 if (gj < ny && gi < nx) {
                     const long long g = (long long)k * plane + (long long)gj * pitch + gi;
-                    Pair<T>::st(dst[0] + g, ex.x, ex.y, sc[0]);
-                    Pair<T>::st(dst[1] + g, ey.x, ey.y, sc[1]);
-                    Pair<T>::st(dst[2] + g, ez.x, ez.y, sc[2]);
+                    Pair<T>::st(dst[0] + g, ex.x, ex.y);
+                    Pair<T>::st(dst[1] + g, ey.x, ey.y);
+                    Pair<T>::st(dst[2] + g, ez.x, ez.y);
                 }
             }
             hpx = hx;
             hpy = hy;
             // ---------------- release the units this warp no longer reads
             __syncwarp();
+            const bool last = k == kz1 - 1;
             if (lane == 0) {
-                mbar_arrive(&empty[ua % S]);
-                if (k == kz1 - 1) mbar_arrive(&empty[ub % S]);
+                mbar_arrive(&empty[sa]);
+                if (last) mbar_arrive(&empty[sb]);
             }
-            u += (k == kz1 - 1) ? 2 : 1;
+            sa = sb;
+            pa = pb;
+            if (last && ++sa == S) {   // the tile's final unit (sb) is released too: move past it
+                sa = 0;
+                pa ^= 1u;
+            }
             hb ^= 1;
         }
     }

@@ -136,21 +136,22 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
-// Per block: sum E^2/ce + sum H (H - ch curl E)/ch (energy without the 1/2 dt/dx factor),
-// sum divE^2 over interior nodes, sum divH^2 over cells.  Cells are visited in a fixed
-// grid-stride order; far-face H terms are appended after the cells.
-template <typename T>
+// Per block, in a fixed grid-stride order over the cells (far-face H appended):
+//   WHAT == 0: energy sum  E^2/ce + H^2/ch - H curl E   (W without the 1/2 dt/dx factor)
+//   WHAT == 1: sum of divE^2 over interior nodes and of divH^2 over cells.
+// Each cell's terms are formed in FP32 with precomputed reciprocal coefficients (relative
+// error of order 2^-23 per term, unbiased) and accumulated in FP64.
+template <typename T, int WHAT>
 __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const CavityDesc d, int copy, double *partial) {
     __shared__ double sh[kRedThreads / 32];
     const int nx = d.nx, ny = d.ny, nz = d.nz;
     const long long P = d.pitch, Z = d.plane;
     const long long ncell = (long long)nx * ny * nz;
-    double se = 0.0, sde = 0.0, sdh = 0.0;
-    auto F = [&](int f, long long o) -> double { return (double)ld_field<T>(d, copy, f, o); };
-    auto C = [&](int c, long long o) -> double { return (double)ld_coef(d, c, o); };
-    auto faceB = [&](int c, long long fi) -> double {
-        const double ch = d.coef_mode == COEF_SCALAR ? (double)d.ch[c] : (double)d.face_ch[c][fi];
-        return (double)d.face[c][fi] / ch;
+    double s0 = 0.0, s1 = 0.0;
+    auto F = [&](int f, long long o) -> float { return ld_field<T>(d, copy, f, o); };
+    auto IC = [&](int c, long long o) -> float { return ld_inv_coef(d, c, o); };
+    auto face_inv_ch = [&](int c, long long fi) -> float {
+        return d.coef_mode == COEF_SCALAR ? d.inv_ch[c] : 1.0f / d.face_ch[c][fi];
     };
     for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < ncell;
          n += (long long)gridDim.x * kRedThreads) {
@@ -158,47 +159,55 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const CavityDesc d,
         const long long t = n / nx;
         const int j = (int)(t % ny), k = (int)(t / ny);
         const long long o = (long long)k * Z + (long long)j * P + i;
-        const double ex = F(0, o), ey = F(1, o), ez = F(2, o);
-        const double cex = C(0, o), cey = C(1, o), cez = C(2, o);
-        se += ex * ex / cex + ey * ey / cey + ez * ez / cez;
-        const double ex_j1 = j + 1 < ny ? F(0, o + P) : 0.0, ex_k1 = k + 1 < nz ? F(0, o + Z) : 0.0;
-        const double ey_i1 = i + 1 < nx ? F(1, o + 1) : 0.0, ey_k1 = k + 1 < nz ? F(1, o + Z) : 0.0;
-        const double ez_i1 = i + 1 < nx ? F(2, o + 1) : 0.0, ez_j1 = j + 1 < ny ? F(2, o + P) : 0.0;
-        const double hx = F(3, o), hy = F(4, o), hz = F(5, o);
-        const double chx = C(3, o), chy = C(4, o), chz = C(5, o);
-        se += hx * (hx - chx * ((ez_j1 - ez) - (ey_k1 - ey))) / chx;
-        se += hy * (hy - chy * ((ex_k1 - ex) - (ez_i1 - ez))) / chy;
-        se += hz * (hz - chz * ((ey_i1 - ey) - (ex_j1 - ex))) / chz;
-        if (i >= 1 && j >= 1 && k >= 1) {
-            const double de = ex / cex - F(0, o - 1) / C(0, o - 1) + ey / cey - F(1, o - P) / C(1, o - P) +
-                              ez / cez - F(2, o - Z) / C(2, o - Z);
-            sde += de * de;
+        const float ex = F(0, o), ey = F(1, o), ez = F(2, o), hx = F(3, o), hy = F(4, o), hz = F(5, o);
+        if (WHAT == 0) {
+            const float ex_j1 = j + 1 < ny ? F(0, o + P) : 0.f, ex_k1 = k + 1 < nz ? F(0, o + Z) : 0.f;
+            const float ey_i1 = i + 1 < nx ? F(1, o + 1) : 0.f, ey_k1 = k + 1 < nz ? F(1, o + Z) : 0.f;
+            const float ez_i1 = i + 1 < nx ? F(2, o + 1) : 0.f, ez_j1 = j + 1 < ny ? F(2, o + P) : 0.f;
+            const float cx = (ez_j1 - ez) - (ey_k1 - ey);
+            const float cy = (ex_k1 - ex) - (ez_i1 - ez);
+            const float cz = (ey_i1 - ey) - (ex_j1 - ex);
+            const float e = ex * ex * IC(0, o) + ey * ey * IC(1, o) + ez * ez * IC(2, o);
+            const float h = (hx * hx * IC(3, o) - hx * cx) + (hy * hy * IC(4, o) - hy * cy) +
+                            (hz * hz * IC(5, o) - hz * cz);
+            s0 += (double)e + (double)h;
+        } else {
+            if (i >= 1 && j >= 1 && k >= 1) {
+                const float de = (ex * IC(0, o) - F(0, o - 1) * IC(0, o - 1)) +
+                                 (ey * IC(1, o) - F(1, o - P) * IC(1, o - P)) +
+                                 (ez * IC(2, o) - F(2, o - Z) * IC(2, o - Z));
+                s0 += (double)de * de;
+            }
+            const float bx1 = i + 1 < nx ? F(3, o + 1) * IC(3, o + 1)
+                                         : d.face[0][(long long)k * ny + j] * face_inv_ch(0, (long long)k * ny + j);
+            const float by1 = j + 1 < ny ? F(4, o + P) * IC(4, o + P)
+                                         : d.face[1][(long long)k * nx + i] * face_inv_ch(1, (long long)k * nx + i);
+            const float bz1 = k + 1 < nz ? F(5, o + Z) * IC(5, o + Z)
+                                         : d.face[2][(long long)j * nx + i] * face_inv_ch(2, (long long)j * nx + i);
+            const float dh = (bx1 - hx * IC(3, o)) + (by1 - hy * IC(4, o)) + (bz1 - hz * IC(5, o));
+            s1 += (double)dh * dh;
         }
-        const double bx1 = i + 1 < nx ? F(3, o + 1) / C(3, o + 1) : faceB(0, (long long)k * ny + j);
-        const double by1 = j + 1 < ny ? F(4, o + P) / C(4, o + P) : faceB(1, (long long)k * nx + i);
-        const double bz1 = k + 1 < nz ? F(5, o + Z) / C(5, o + Z) : faceB(2, (long long)j * nx + i);
-        const double dh = bx1 - hx / chx + by1 - hy / chy + bz1 - hz / chz;
-        sdh += dh * dh;
     }
-    // constant far-face normal H: curl E vanishes there, so its energy term is H^2/ch
-    const long long nfx = (long long)ny * nz, nfy = (long long)nx * nz, nfz = (long long)nx * ny;
-    for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < nfx + nfy + nfz;
-         n += (long long)gridDim.x * kRedThreads) {
-        int c;
-        long long fi;
-        if (n < nfx) { c = 0; fi = n; }
-        else if (n < nfx + nfy) { c = 1; fi = n - nfx; }
-        else { c = 2; fi = n - nfx - nfy; }
-        const double h = d.face[c][fi];
-        se += h * faceB(c, fi);
+    if (WHAT == 0) {
+        // constant far-face normal H: curl E vanishes there, so its energy term is H^2/ch
+        const long long nfx = (long long)ny * nz, nfy = (long long)nx * nz, nfz = (long long)nx * ny;
+        for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < nfx + nfy + nfz;
+             n += (long long)gridDim.x * kRedThreads) {
+            int c;
+            long long fi;
+            if (n < nfx) { c = 0; fi = n; }
+            else if (n < nfx + nfy) { c = 1; fi = n - nfx; }
+            else { c = 2; fi = n - nfx - nfy; }
+            const float h = d.face[c][fi];
+            s0 += (double)(h * h * face_inv_ch(c, fi));
+        }
     }
-    const double a = block_sum(se, sh);
-    const double b = block_sum(sde, sh);
-    const double e = block_sum(sdh, sh);
+    const double a = block_sum(s0, sh);
+    const double b = block_sum(s1, sh);
     if (threadIdx.x == 0) {
-        partial[3 * blockIdx.x + 0] = a;
-        partial[3 * blockIdx.x + 1] = b;
-        partial[3 * blockIdx.x + 2] = e;
+        partial[3 * blockIdx.x + 0] = WHAT == 0 ? a : 0.0;
+        partial[3 * blockIdx.x + 1] = WHAT == 1 ? a : 0.0;
+        partial[3 * blockIdx.x + 2] = b;
     }
 }
 
@@ -256,9 +265,12 @@ cudaError_t launch_simple_step(int storage, const CavityDesc &d, int copy, cudaS
 
 int reduction_blocks() { return kRedBlocks; }
 
-cudaError_t launch_reductions(int storage, const CavityDesc &d, int copy, double *partial, int nblocks, double *out,
-                              cudaStream_t s) {
-    FDTD_STORAGE_DISPATCH(storage, reduce_kernel<T><<<nblocks, kRedThreads, 0, s>>>(d, copy, partial));
+cudaError_t launch_reductions(int storage, const CavityDesc &d, int copy, int what, double *partial, int nblocks,
+                              double *out, cudaStream_t s) {
+    if (what == 0)
+        FDTD_STORAGE_DISPATCH(storage, reduce_kernel<T, 0><<<nblocks, kRedThreads, 0, s>>>(d, copy, partial));
+    else
+        FDTD_STORAGE_DISPATCH(storage, reduce_kernel<T, 1><<<nblocks, kRedThreads, 0, s>>>(d, copy, partial));
     reduce_final_kernel<<<1, kRedThreads, 0, s>>>(partial, nblocks, out);
     return cudaGetLastError();
 }

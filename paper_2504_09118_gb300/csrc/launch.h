@@ -15,10 +15,10 @@ cudaError_t launch_unpack(int storage, const CavityDesc &d, int copy, int comp, 
 cudaError_t launch_maxabs(const float *canon, int comp, int nx, int ny, int nz, unsigned *out, cudaStream_t s);
 // One unfused step in place on copy `copy`: H kernel then E kernel.
 cudaError_t launch_simple_step(int storage, const CavityDesc &d, int copy, cudaStream_t s);
-// FP64 reductions: energy terms (sum E^2/ce + sum H.(H - ch curl E)/ch) and the two divergence sums of squares.
-// partial must hold nblocks*3 doubles; out receives 3 doubles {energy_sum, divE2, divH2}.
-cudaError_t launch_reductions(int storage, const CavityDesc &d, int copy, double *partial, int nblocks, double *out,
-                              cudaStream_t s);
+// Reductions accumulated in FP64: what == 0 gives out[0] = sum E^2/ce + H.(H - ch curl E)/ch;
+// what == 1 gives out[1] = sum divE^2, out[2] = sum divH^2.  partial holds nblocks*3 doubles.
+cudaError_t launch_reductions(int storage, const CavityDesc &d, int copy, int what, double *partial, int nblocks,
+                              double *out, cudaStream_t s);
 int reduction_blocks();
 
 struct FusedLaunch {

@@ -1,0 +1,100 @@
+"""Full-size workloads in the launch configuration the bench times.
+
+512^3 FP32 with 32 dielectric spheres: after 3 steps, sampled sub-boxes are
+checked element by element against the FP64 oracle run on the sub-box alone
+(a value after s steps depends only on inputs within s+1 cells, so the core of
+a sub-box with its own PEC walls matches; the oracle pins check that property),
+then after 200 steps the invariants that hold at any size: energy drift,
+divergence, PEC bits.  384^3 with FP16/BF16 storage, 1000 steps: error against
+the FP32 GPU run of the same input and energy drift.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import bench
+import cavity_inputs as ci
+from tests.gpu_util import DT, ENERGY_DRIFT_F32, REL_L2_F32
+
+pytestmark = pytest.mark.gpu
+
+
+def _sub(arr, a, b):
+    return np.ascontiguousarray(arr[a[2]:b[2] + 1, a[1]:b[1] + 1, a[0]:b[0] + 1])
+
+
+def test_512_spheres_sampled_parity_and_invariants():
+    import oracle
+    from paper_2504_09118_gb300 import Cavity
+    w = bench.WORKLOADS["single512"]
+    n = w["n"]
+    ce, ch = bench.sphere_coefs(w)
+    f = ci.random_fields(w["field_seed"], *n)
+    s = 3
+    with Cavity(*n, DT, 1.0, ce, ch) as cav:
+        cav.tune(**bench.BENCH_TUNING)
+        cav.set_fields(f)
+        w0 = cav.energy()
+        d0 = cav.divergence()
+        cav.step(s)
+        g = cav.get_fields()
+        N = n[0]
+        R = 14
+        centres = [(0, 0, 0), (N, N, N), (N // 2, N // 2, N // 2), (63, 200, 17), (300, 5, 511), (128, 447, 260),
+                   (511, 64, 130), (7, 300, 400)]
+        for (cx, cy, cz) in centres:
+            a = [max(0, c - R) for c in (cx, cy, cz)]
+            b = [min(N, c + R) for c in (cx, cy, cz)]
+            sub = oracle.as_f64([_sub(x, a, b) for x in f])
+            sce = [_sub(x, a, b).astype(np.float64) for x in ce]
+            oracle.pec_e(sub)
+            oracle.step(sub, sce, ch, s)
+            # compare away from cut faces (real faces are exact)
+            m = s + 2
+            sl = tuple(slice(m if lo > 0 else 0, (hi - lo + 1) - m if hi < N else hi - lo + 1)
+                       for lo, hi in ((a[2], b[2]), (a[1], b[1]), (a[0], b[0])))
+            for c, name in enumerate(ci.COMPONENTS):
+                got = _sub(g[c], a, b)[sl].astype(np.float64)
+                ref = sub[c][sl]
+                mask = ci.extent_mask(name, b[0] - a[0], b[1] - a[1], b[2] - a[2])[sl]
+                err = np.linalg.norm(got[mask] - ref[mask]) / max(np.linalg.norm(ref[mask]), 1e-30)
+                assert err <= REL_L2_F32, (name, (cx, cy, cz), err)
+        del g
+        cav.step(200 - s)
+        w1 = cav.energy()
+        d1 = cav.divergence()
+        assert abs(w1 - w0) / w0 <= ENERGY_DRIFT_F32, (w0, w1)
+        assert abs(d1[0] - d0[0]) / d0[0] <= 1e-5 and abs(d1[1] - d0[1]) / d0[1] <= 1e-5
+        g = cav.get_fields()
+        for c, name in enumerate(("Ex", "Ey", "Ez")):
+            assert np.all(g[c][ci.tangential_e_mask(name, *n)] == 0.0)
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_384_precision_1000_steps(storage):
+    from paper_2504_09118_gb300 import Cavity
+    w = bench.WORKLOADS["precision384_f16" if storage == 1 else "precision384_bf16"]
+    n, steps = w["n"], w["steps"]
+    ce, ch = bench.sphere_coefs(w)
+    f = ci.random_fields(w["field_seed"], *n)
+    with Cavity(*n, DT, 1.0, ce, ch, 0) as ref_cav:
+        ref_cav.tune(**bench.BENCH_TUNING)
+        ref_cav.set_fields(f)
+        ref_cav.step(steps)
+        ref = ref_cav.get_fields()
+    with Cavity(*n, DT, 1.0, ce, ch, storage) as cav:
+        cav.tune(**bench.BENCH_TUNING)
+        cav.set_fields(f)
+        w0 = cav.energy()
+        cav.step(steps)
+        w1 = cav.energy()
+        got = cav.get_fields()
+    num = sum(float(np.sum((a.astype(np.float64) - b) ** 2)) for a, b in zip(got, ref))
+    den = sum(float(np.sum(b.astype(np.float64) ** 2)) for b in ref)
+    err = math.sqrt(num / den)
+    u = 2.0 ** -11 if storage == 1 else 2.0 ** -8
+    est = u / math.sqrt(3.0) * math.sqrt(steps + 1)
+    print(f"storage {storage}: rel-L2 vs FP32 GPU {err:.3e} (estimate {est:.3e}); energy drift {(w1 - w0) / w0:.3e}")
+    assert err <= 3 * est
+    assert abs(w1 - w0) / w0 <= 3 * est
