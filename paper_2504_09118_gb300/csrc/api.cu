@@ -282,6 +282,7 @@ TileRec base_rec(const fdtd_ctx *c, int parity_off) {
         r.ch[q] = c->ch_s[q] / re;
     }
     r.table = reinterpret_cast<const float4 *>(c->table_fused);
+    r.ntab = c->ntab;
     r.maps = c->d_maps;
     for (int f = 0; f < 6; ++f) {
         r.dst[0][f] = c->fields[0][f];

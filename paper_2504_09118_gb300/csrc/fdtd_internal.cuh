@@ -123,7 +123,8 @@ struct alignas(16) TileRec {
     const float4 *table;         // COEF_ID8: per id two float4: (ce x,y,z,0), (ch x,y,z,0), folded
     const CUtensorMap *maps;     // kMapsPerCavity tensor maps in global memory
     void *dst[2][6];             // both copies of the six active arrays
-    int pad[18];
+    int ntab;                    // COEF_ID8: table entries
+    int pad[17];
 };
 static_assert(sizeof(TileRec) == 256, "TileRec must be 256 bytes");
 
@@ -186,6 +187,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     for (;;) {
         for (int r = 0; r < 4; ++r)
             if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// As mbar_wait_bounded, but sleeps sleep_ns between polls (for a thread whose wait is not on the
+// critical path, so that it does not take issue slots from the warps doing the arithmetic).
+__device__ __forceinline__ bool mbar_wait_bounded_sleep(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                                        unsigned sleep_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        __nanosleep(sleep_ns);
+        if (mbar_try_wait(bar, parity)) return true;
         if (global_timer_ns() - t0 > limit_ns) return false;
     }
 }

@@ -39,6 +39,10 @@ namespace fdtd {
 
 namespace {
 
+#ifndef FDTD_PRODUCER_SLEEP_NS
+#define FDTD_PRODUCER_SLEEP_NS 0   // back-off of the producer warp between polls of a full ring slot
+#endif
+
 constexpr int TX = kTileX;
 constexpr int NTR = 8;                              // tile-record ring entries
 constexpr uint64_t kWaitLimitNs = 2000000000ull;    // 2 s: far beyond any healthy TMA latency
@@ -83,9 +87,10 @@ template <int TY>
 __host__ __device__ constexpr int hbuf_floats() {
     return 3 * (TY + 1) * HP;
 }
+constexpr int TAB_BYTES = kMaxTable * 2 * 16;   // shared copy of a cavity's material table (ce, ch float4)
 template <typename T, int TY>
 __host__ __device__ constexpr int smem_bytes(int stages) {
-    return 128 /*barriers*/ + NTR * (int)sizeof(TileRec) + align_up(2 * hbuf_floats<TY>() * 4, 128) +
+    return 128 /*barriers*/ + NTR * (int)sizeof(TileRec) + TAB_BYTES + align_up(2 * hbuf_floats<TY>() * 4, 128) +
            stages * slot_bytes<T, TY>() + 128 /*alignment slack*/;
 }
 template <int TY>
@@ -159,7 +164,8 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + 8;
     TileRec *recs = reinterpret_cast<TileRec *>(smem + 128);
-    float *hbuf = reinterpret_cast<float *>(smem + 128 + NTR * sizeof(TileRec));
+    float4 *stab = reinterpret_cast<float4 *>(smem + 128 + NTR * sizeof(TileRec));
+    float *hbuf = reinterpret_cast<float *>(smem + 128 + NTR * sizeof(TileRec) + TAB_BYTES);
     unsigned char *slots = reinterpret_cast<unsigned char *>(hbuf) + align_up(2 * HB * 4, 128);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -188,7 +194,9 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
             int kb = 0, kz1 = 0;
             for (int k = 0;; ++k) {
                 if (issued >= S) {   // wait until unit issued - S (same slot, previous round) is released
-                    const bool w = mbar_wait_bounded(&empty[s], rnd ^ 1u, lim);
+                    const bool w = FDTD_PRODUCER_SLEEP_NS > 0
+                                       ? mbar_wait_bounded_sleep(&empty[s], rnd ^ 1u, lim, FDTD_PRODUCER_SLEEP_NS)
+                                       : mbar_wait_bounded(&empty[s], rnd ^ 1u, lim);
                     if (!__all_sync(0xffffffffu, w)) {
                         ok = false;
                         break;
@@ -243,17 +251,30 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
     const int bx = x + HX, by = y + 1;          // position in a field box
     int sa = 0, m = 0, hb = 0;   // slot of the current unit
     uint32_t pa = 0;             // phase parity of that slot
+    const float4 *tab_cached = nullptr;
     float2 hpx = make_float2(0.f, 0.f), hpy = make_float2(0.f, 0.f);   // H^{n+1/2}(k-1) of own cells
 
     for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x, ++m) {
         bool ok = mbar_wait_bounded(&full[sa], pa, lim);   // the tile record is valid from here
+        // every consumer warp is past the previous tile's E phase here; a timeout anywhere ends the CTA
+        if (bar_sync_or(2, NCT, !ok)) {
+            if (threadIdx.x == 0) atomicOr(P.status, STATUS_TIMEOUT);
+            return;
+        }
         const TileRec *rec = &recs[m % NTR];
         const int x0 = rec->x0, y0 = rec->y0, kz0 = rec->kz0, kz1 = rec->kz1;
         const int nx = rec->nx, ny = rec->ny;
         const long long pitch = rec->pitch, plane = rec->plane;
         const bool id_mode = rec->mode == COEF_ID8;
         const bool ch_uni = rec->ch_uniform != 0;
-        const float4 *table = rec->table;
+        if (id_mode && rec->table != tab_cached) {   // new cavity: copy its material table to shared memory
+            const float4 *src = rec->table;
+            const int n = 2 * rec->ntab;
+            for (int e = threadIdx.x; e < n; e += NCT) stab[e] = __ldg(src + e);
+            bar_sync_or(2, NCT, false);
+            tab_cached = src;
+        }
+        const float4 *table = stab;
         const int dstc = (P.parity ^ rec->parity_off) ^ 1;
         T *dst[6];
 #pragma unroll
@@ -302,8 +323,8 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                 if (id_mode) {
                     idpair = *reinterpret_cast<const uint16_t *>(ida + by * G::IBX + x + G::IDX_HALO);
                     if (!ch_uni) {
-                        const float4 a = __ldg(&table[2 * (idpair & 0xff) + 1]);
-                        const float4 b = __ldg(&table[2 * (idpair >> 8) + 1]);
+                        const float4 a = (table[2 * (idpair & 0xff) + 1]);
+                        const float4 b = (table[2 * (idpair >> 8) + 1]);
                         chx = make_float2(a.x, b.x);
                         chy = make_float2(a.y, b.y);
                         chz = make_float2(a.z, b.z);
@@ -337,7 +358,7 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     const float cexb = Pair<T>::ld1(at(B, 0, cbx, cby));
                     float cchy = ch_s1, cchz = ch_s2;
                     if (id_mode && !ch_uni) {
-                        const float4 a = __ldg(&table[2 * ida[cby * G::IBX + G::IDX_HALO - 1] + 1]);
+                        const float4 a = (table[2 * ida[cby * G::IBX + G::IDX_HALO - 1] + 1]);
                         cchy = a.y;
                         cchz = a.z;
                     }
@@ -362,8 +383,8 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                 const float hy_xm = hn[HC + o - 1];
                 const float hz_xm = hn[2 * HC + o - 1];
                 if (id_mode) {
-                    ce_a = __ldg(&table[2 * (idpair & 0xff)]);
-                    ce_b = __ldg(&table[2 * (idpair >> 8)]);
+                    ce_a = (table[2 * (idpair & 0xff)]);
+                    ce_b = (table[2 * (idpair >> 8)]);
                 }
                 const float2 cex = make_float2(ce_a.x, ce_b.x), cey = make_float2(ce_a.y, ce_b.y),
                              cez = make_float2(ce_a.z, ce_b.z);
