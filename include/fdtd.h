@@ -173,11 +173,22 @@ FDTD_API const char *fdtd_last_error(const fdtd_ctx *ctx);
 /* fdtd_batch_create - empty batch for members of the given storage, on cuda_stream. */
 FDTD_API int fdtd_batch_create(fdtd_batch **out, int storage, void *cuda_stream);
 
-/* fdtd_batch_add - add a cavity (after its fdtd_set_fields); it keeps its state and step count. */
+/* fdtd_batch_add - add a cavity (after its fdtd_set_fields); it keeps its state.  The cavity may
+ * use its own stream: fdtd_batch_remove orders that stream after the batch's work. */
 FDTD_API int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *ctx);
 
-/* fdtd_batch_remove - remove a member; it can be stepped or read on its own afterwards. */
+/* fdtd_batch_remove - remove a member; it can be stepped or read on its own afterwards.  Does not
+ * wait for the GPU: the member's stream is made to wait for the batch work enqueued so far.
+ * The member's fdtd_steps_done is brought up to date here. */
 FDTD_API int fdtd_batch_remove(fdtd_batch *b, fdtd_ctx *ctx);
+
+/* fdtd_batch_set_steps - the member takes exactly nsteps more steps of this batch and is then
+ * skipped by every later launch (its state frozen) until it is removed.  Lets members with
+ * different step counts share launches without stopping the batch for each of them. */
+FDTD_API int fdtd_batch_set_steps(fdtd_batch *b, fdtd_ctx *ctx, long long nsteps);
+
+/* fdtd_batch_steps_done - batch launches enqueued since the batch was created (-1 for NULL). */
+FDTD_API long long fdtd_batch_steps_done(const fdtd_batch *b);
 
 /* fdtd_batch_step - advance every member nsteps steps, asynchronously on the batch stream. */
 FDTD_API int fdtd_batch_step(fdtd_batch *b, int nsteps);

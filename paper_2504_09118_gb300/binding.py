@@ -29,7 +29,8 @@ EXPORTS = (
     "fdtd_sync", "fdtd_set_tuning", "fdtd_steps_done", "fdtd_device_bytes", "fdtd_destroy", "fdtd_last_error",
     "fdtd_batch_create", "fdtd_batch_add", "fdtd_batch_remove", "fdtd_batch_step", "fdtd_batch_set_tuning",
     "fdtd_batch_size", "fdtd_batch_sync", "fdtd_batch_destroy", "fdtd_batch_last_error",
-    "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static",
+    "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static", "fdtd_batch_set_steps",
+    "fdtd_batch_steps_done",
 )
 
 
@@ -93,6 +94,9 @@ def lib() -> ctypes.CDLL:
             L.fdtd_batch_last_error.argtypes = [vp]
             L.fdtd_batch_last_error.restype = ctypes.c_char_p
             L.fdtd_debug_inject_timeout.argtypes = [vp, i]
+            L.fdtd_batch_set_steps.argtypes = [vp, vp, ll]
+            L.fdtd_batch_steps_done.argtypes = [vp]
+            L.fdtd_batch_steps_done.restype = ll
             L.fdtd_version.restype = ctypes.c_char_p
             L.fdtd_energy_static.argtypes = [i, i, i, d, d, vp, vp, vp, vp, vp]
             _LIB = L
@@ -304,6 +308,14 @@ def fdtd_batch_step(b, nsteps: int) -> None:
 def fdtd_batch_set_tuning(b, kernel=0, tile_y=0, zchunk=0, ctas_per_sm=0, stages=0, use_graph=0) -> None:
     t = fdtd_tuning(kernel, tile_y, zchunk, ctas_per_sm, stages, use_graph)
     _bcheck(b, lib().fdtd_batch_set_tuning(b, ctypes.byref(t)))
+
+
+def fdtd_batch_set_steps(b, ctx, nsteps: int) -> None:
+    _bcheck(b, lib().fdtd_batch_set_steps(b, ctx, int(nsteps)))
+
+
+def fdtd_batch_steps_done(b) -> int:
+    return int(lib().fdtd_batch_steps_done(b))
 
 
 def fdtd_batch_size(b) -> int:

@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -92,19 +93,26 @@ struct fdtd_ctx {
 };
 
 struct fdtd_batch {
+    struct Member {
+        fdtd_ctx *c;
+        int cur0;               // member's current copy when it joined
+        long long join;         // batch launch index at which it joined
+        long long stop;         // launch index from which it is skipped (LLONG_MAX: no limit)
+        long long steps0;       // its step count when it joined
+    };
     int storage = 0;
     cudaStream_t stream = nullptr;
-    std::vector<fdtd_ctx *> members;
-    std::vector<int> off;            // parity offset of each member
-    int parity = 0;                  // launch parity of the next step
+    std::vector<Member> members;
+    long long step = 0;              // launches enqueued so far; the next launch has parity step & 1
+    long long *d_step = nullptr;     // device copy of the launch counter (advanced by a kernel per launch)
     fdtd_tuning tuning{};
-    CavityDesc *d_desc = nullptr;
-    int desc_cap = 0;
     TileRec *d_tiles = nullptr;
     int tiles_cap = 0, ntiles = 0, grid = 0;
     bool dirty = true;
     int *d_status = nullptr;
+    cudaEvent_t done_ev = nullptr;   // recorded at member removal; the member's stream waits on it
     std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::vector<cudaGraphExec_t> retired_graphs;   // destroyed at the next synchronisation point
     std::string err;
 };
 
@@ -137,8 +145,41 @@ int bfail(fdtd_batch *b, int code, const char *fmt, ...) {
                         cudaGetErrorString(e_));                                                        \
     } while (0)
 
+// Device memory comes from a library-owned stream-ordered pool per device that keeps freed
+// memory for reuse (release threshold: never), so creating and destroying contexts at a
+// serving rate neither returns memory to the driver nor synchronises the device.
+cudaMemPool_t lib_pool() {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    pools[dev] = pool;
+    return pool;
+}
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = lib_pool();
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void pool_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
 cudaError_t dmalloc(fdtd_ctx *c, void **p, size_t bytes) {
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = pool_alloc(p, bytes, c->stream);
     if (e == cudaSuccess) c->bytes += (long long)bytes;
     return e;
 }
@@ -283,6 +324,7 @@ TileRec base_rec(const fdtd_ctx *c, int parity_off) {
     }
     r.table = reinterpret_cast<const float4 *>(c->table_fused);
     r.ntab = c->ntab;
+    r.stop = LLONG_MAX;
     r.maps = c->d_maps;
     for (int f = 0; f < 6; ++f) {
         r.dst[0][f] = c->fields[0][f];
@@ -315,9 +357,9 @@ int build_tiles(fdtd_ctx *c) {
     const int zlen = choose_zlen(cols, c->nz, G, c->tuning.zchunk);
     std::vector<TileRec> v;
     append_tiles(v, c, 0, s.tile_y, zlen);
-    if (c->d_tiles) cudaFree(c->d_tiles);
+    pool_free(c->d_tiles, c->stream);
     c->d_tiles = nullptr;
-    CK(c, cudaMalloc(&c->d_tiles, sizeof(TileRec) * v.size()));
+    CK(c, pool_alloc((void **)&c->d_tiles, sizeof(TileRec) * v.size(), c->stream));
     CK(c, cudaMemcpyAsync(c->d_tiles, v.data(), sizeof(TileRec) * v.size(), cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     c->ntiles = (int)v.size();
@@ -553,6 +595,7 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
                 fc[n] = have_ch ? ch[q][src] : vac;
             }
             if ((e = dmalloc(c, (void **)&c->face_ch[q], nface[q] * 4)) != cudaSuccess) return cfail("face alloc", e);
+            if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cfail("sync", e);
             if ((e = cudaMemcpy(c->face_ch[q], fc.data(), nface[q] * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cfail("face copy", e);
         }
@@ -574,10 +617,12 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
                 }
             }
             if ((e = dmalloc(c, (void **)&c->table, tab.size() * 4)) != cudaSuccess) return cfail("table alloc", e);
+            if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cfail("sync", e);
             if ((e = cudaMemcpy(c->table, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cfail("table copy", e);
             if ((e = dmalloc(c, (void **)&c->table_fused, tab.size() * 4)) != cudaSuccess)
                 return cfail("table alloc", e);
+            if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cfail("sync", e);
             if ((e = cudaMemcpy(c->table_fused, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cfail("table copy", e);
             c->host_table = tab;
@@ -588,9 +633,11 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
                     inv[8 * n + 4 + q] = (float)(1.0 / (double)tab[8 * n + 4 + q]);
                 }
             if ((e = dmalloc(c, (void **)&c->inv_table, inv.size() * 4)) != cudaSuccess) return cfail("table alloc", e);
+            if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cfail("sync", e);
             if ((e = cudaMemcpy(c->inv_table, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cfail("table copy", e);
             if ((e = dmalloc(c, (void **)&c->id, c->arr_elems)) != cudaSuccess) return cfail("id alloc", e);
+            if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cfail("sync", e);
             if ((e = cudaMemset(c->id, 0, c->arr_elems)) != cudaSuccess) return cfail("memset", e);
             if ((e = cudaMemcpy2D(c->id, c->pitch, ids.data(), nx, nx, (size_t)ny * nz, cudaMemcpyHostToDevice)) !=
                 cudaSuccess)
@@ -608,6 +655,7 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
                         }
                 if ((e = dmalloc(c, (void **)&c->coef_full[a], row.size() * 4)) != cudaSuccess)
                     return cfail("coef alloc", e);
+                if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cfail("sync", e);
                 if ((e = cudaMemcpy(c->coef_full[a], row.data(), row.size() * 4, cudaMemcpyHostToDevice)) !=
                     cudaSuccess)
                     return cfail("coef copy", e);
@@ -615,7 +663,7 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
         }
     }
     if ((e = dmalloc(c, (void **)&c->d_status, sizeof(int))) != cudaSuccess) return cfail("status alloc", e);
-    if ((e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess) return cfail("memset", e);
+    if ((e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream)) != cudaSuccess) return cfail("memset", e);
     const int nb = reduction_blocks();
     if ((e = dmalloc(c, (void **)&c->d_partial, sizeof(double) * 3 * nb)) != cudaSuccess) return cfail("alloc", e);
     if ((e = dmalloc(c, (void **)&c->d_out, sizeof(double) * 3)) != cudaSuccess) return cfail("alloc", e);
@@ -637,25 +685,19 @@ void fdtd_destroy(fdtd_ctx *c) {
     if (c->batch) fdtd_batch_remove(c->batch, c);
     cudaStreamSynchronize(c->stream);
     drop_graphs(c->graphs);
+    cudaStream_t st = c->stream;
     for (int cp = 0; cp < 2; ++cp)
-        for (int f = 0; f < 6; ++f) cudaFree(c->fields[cp][f]);
+        for (int f = 0; f < 6; ++f) pool_free(c->fields[cp][f], st);
     for (int q = 0; q < 3; ++q) {
-        cudaFree(c->face[q]);
-        cudaFree(c->face_ch[q]);
+        pool_free(c->face[q], st);
+        pool_free(c->face_ch[q], st);
     }
-    for (int a = 0; a < 6; ++a) cudaFree(c->coef_full[a]);
-    cudaFree(c->id);
-    cudaFree(c->table);
-    cudaFree(c->inv_table);
-    cudaFree(c->table_fused);
-    cudaFree(c->d_status);
-    cudaFree(c->d_partial);
-    cudaFree(c->d_out);
-    cudaFree(c->d_stage);
-    cudaFree(c->d_max);
-    cudaFree(c->d_maps);
-    cudaFree(c->d_desc);
-    cudaFree(c->d_tiles);
+    for (int a = 0; a < 6; ++a) pool_free(c->coef_full[a], st);
+    for (void *p : {(void *)c->id, (void *)c->table, (void *)c->inv_table, (void *)c->table_fused,
+                    (void *)c->d_status, (void *)c->d_partial, (void *)c->d_out, (void *)c->d_stage,
+                    (void *)c->d_max, (void *)c->d_maps, (void *)c->d_desc, (void *)c->d_tiles})
+        pool_free(p, st);
+    cudaStreamSynchronize(st);
     delete c;
 }
 
@@ -673,6 +715,7 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
     if (n.zchunk < 0 || n.ctas_per_sm < 0) return fail(c, FDTD_ERR_ARG, "negative tuning value");
     c->tuning = n;
     c->tiles_ty = 0;   // force a tile rebuild
+    cudaStreamSynchronize(c->stream);   // no graph of this context may still be running
     drop_graphs(c->graphs);
     return FDTD_OK;
 }
@@ -723,6 +766,7 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
             CK(c, cudaStreamSynchronize(c->stream));
         }
         c->tiles_ty = 0;   // tile records embed the folded coefficients: rebuild them
+        cudaStreamSynchronize(c->stream);
         drop_graphs(c->graphs);
     }
     if (int rc = upload_desc(c)) return rc;
@@ -860,8 +904,16 @@ int fdtd_batch_create(fdtd_batch **out, int storage, void *cuda_stream) {
     fdtd_batch *b = new fdtd_batch();
     b->storage = storage;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
-    if (cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess || cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) {
-        cudaFree(b->d_status);
+    bool ok = pool_alloc((void **)&b->d_status, sizeof(int), b->stream) == cudaSuccess &&
+              pool_alloc((void **)&b->d_step, sizeof(long long), b->stream) == cudaSuccess &&
+              cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream) == cudaSuccess &&
+              cudaMemsetAsync(b->d_step, 0, sizeof(long long), b->stream) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->done_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamSynchronize(b->stream) == cudaSuccess;
+    if (!ok) {
+        pool_free(b->d_status, b->stream);
+        pool_free(b->d_step, b->stream);
+        if (b->done_ev) cudaEventDestroy(b->done_ev);
         delete b;
         return FDTD_ERR_OOM;
     }
@@ -871,35 +923,55 @@ int fdtd_batch_create(fdtd_batch **out, int storage, void *cuda_stream) {
 
 int fdtd_batch_size(const fdtd_batch *b) { return b ? (int)b->members.size() : -1; }
 const char *fdtd_batch_last_error(const fdtd_batch *b) { return b ? b->err.c_str() : ""; }
+long long fdtd_batch_steps_done(const fdtd_batch *b) { return b ? b->step : -1; }
+
+static fdtd_batch::Member *find_member(fdtd_batch *b, fdtd_ctx *c, size_t *idx = nullptr) {
+    for (size_t n = 0; n < b->members.size(); ++n)
+        if (b->members[n].c == c) {
+            if (idx) *idx = n;
+            return &b->members[n];
+        }
+    return nullptr;
+}
 
 int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *c) {
     if (!b || !c) return bfail(b, FDTD_ERR_ARG, "NULL argument");
     if (c->batch) return bfail(b, FDTD_ERR_STATE, "context already belongs to a batch");
     if (!c->has_fields) return bfail(b, FDTD_ERR_STATE, "context has no fields yet");
     if (c->storage != b->storage) return bfail(b, FDTD_ERR_ARG, "storage mismatch");
-    if (c->stream != b->stream) return bfail(b, FDTD_ERR_ARG, "stream mismatch");
     if (c->coef_mode == COEF_FULL) return bfail(b, FDTD_ERR_ARG, "per-position coefficient arrays are not batched");
-    // the member's current copy must be the one the batch's next launch reads
-    b->members.push_back(c);
-    b->off.push_back(b->parity ^ c->cur);
+    // the member's pending work (set_fields) happened-before: its stream was synchronised by that call
+    b->members.push_back({c, c->cur, b->step, LLONG_MAX, c->steps});
     c->batch = b;
+    b->dirty = true;
+    return FDTD_OK;
+}
+
+int fdtd_batch_set_steps(fdtd_batch *b, fdtd_ctx *c, long long nsteps) {
+    if (!b || !c || nsteps < 0) return bfail(b, FDTD_ERR_ARG, "bad argument");
+    fdtd_batch::Member *mb = find_member(b, c);
+    if (!mb) return bfail(b, FDTD_ERR_ARG, "context is not a member");
+    mb->stop = b->step + nsteps;
     b->dirty = true;
     return FDTD_OK;
 }
 
 int fdtd_batch_remove(fdtd_batch *b, fdtd_ctx *c) {
     if (!b || !c) return bfail(b, FDTD_ERR_ARG, "NULL argument");
-    for (size_t n = 0; n < b->members.size(); ++n)
-        if (b->members[n] == c) {
-            cudaStreamSynchronize(b->stream);
-            c->cur = b->parity ^ b->off[n];
-            c->batch = nullptr;
-            b->members.erase(b->members.begin() + n);
-            b->off.erase(b->off.begin() + n);
-            b->dirty = true;
-            return FDTD_OK;
-        }
-    return bfail(b, FDTD_ERR_ARG, "context is not a member");
+    size_t n = 0;
+    fdtd_batch::Member *mb = find_member(b, c, &n);
+    if (!mb) return bfail(b, FDTD_ERR_ARG, "context is not a member");
+    const long long taken = std::min(b->step, mb->stop) - mb->join;
+    c->cur = mb->cur0 ^ (int)(taken & 1);
+    c->steps = mb->steps0 + taken;
+    c->batch = nullptr;
+    // later work on the member's own stream (read-back, destroy) waits for the batch work enqueued so far
+    if (cudaEventRecord(b->done_ev, b->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(c->stream, b->done_ev, 0) != cudaSuccess)
+        return bfail(b, FDTD_ERR_CUDA, "ordering the member's stream after the batch failed");
+    b->members.erase(b->members.begin() + n);
+    b->dirty = true;
+    return FDTD_OK;
 }
 
 int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t) {
@@ -914,51 +986,58 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t) {
     return FDTD_OK;
 }
 
+static void batch_retire_graphs(fdtd_batch *b) {
+    for (auto &kv : b->graphs) b->retired_graphs.push_back(kv.second);
+    b->graphs.clear();
+}
+
+static void batch_free_retired_graphs(fdtd_batch *b) {   // call only when the batch stream is idle
+    for (cudaGraphExec_t g : b->retired_graphs) cudaGraphExecDestroy(g);
+    b->retired_graphs.clear();
+}
+
+// Rebuild the packed tile list (asynchronously on the batch stream: the upload runs after the
+// launches already enqueued, and the old buffer is released in stream order).
 static int batch_rebuild(fdtd_batch *b) {
     if (!b->dirty) return FDTD_OK;
-    drop_graphs(b->graphs);
+    batch_retire_graphs(b);
     Shape s = resolve_shape(b->storage, b->tuning);
     const int G = num_sms() * s.ctas_per_sm;
-    std::vector<CavityDesc> descs;
     std::vector<TileRec> tiles;
     long long total_cols_planes = 0;
-    for (size_t n = 0; n < b->members.size(); ++n) {
-        fdtd_ctx *c = b->members[n];
-        if (int rc = encode_maps(c, s.tile_y)) return bfail(b, rc, "member %zu: %s", n, c->err.c_str());
-        descs.push_back(make_desc(c, b->off[n]));
+    for (auto &mb : b->members)
+        if (mb.stop > b->step && mb.c->maps_ty != 0 && mb.c->maps_ty != s.tile_y) {
+            cudaStreamSynchronize(b->stream);   // launches in flight may still read the old maps
+            break;
+        }
+    for (auto &mb : b->members) {
+        if (mb.stop <= b->step) continue;   // finished members carry no tiles
+        fdtd_ctx *c = mb.c;
+        if (int rc = encode_maps(c, s.tile_y)) return bfail(b, rc, "member: %s", c->err.c_str());
         total_cols_planes += (long long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + s.tile_y - 1) / s.tile_y) * c->nz;
     }
     // one z-length for all members so tiles carry similar work; about 8 tiles per CTA
-    int zlen = b->tuning.zchunk > 0 ? b->tuning.zchunk
-                                    : (int)std::max<long long>(8, total_cols_planes / std::max(1, 8 * G));
-    for (size_t n = 0; n < b->members.size(); ++n) {
-        fdtd_ctx *c = b->members[n];
-        append_tiles(tiles, c, b->off[n], s.tile_y, std::min(zlen, c->nz));
+    const int zlen = b->tuning.zchunk > 0 ? b->tuning.zchunk
+                                          : (int)std::max<long long>(8, total_cols_planes / std::max(1, 8 * G));
+    for (auto &mb : b->members) {
+        if (mb.stop <= b->step) continue;
+        const size_t first = tiles.size();
+        append_tiles(tiles, mb.c, mb.cur0 ^ (int)(mb.join & 1), s.tile_y, std::min(zlen, mb.c->nz));
+        for (size_t q = first; q < tiles.size(); ++q) tiles[q].stop = mb.stop;
     }
     // longest tiles first, then round-robin over the persistent CTAs
     std::stable_sort(tiles.begin(), tiles.end(),
                      [](const TileRec &a, const TileRec &c) { return (a.kz1 - a.kz0) > (c.kz1 - c.kz0); });
-    if ((int)descs.size() > b->desc_cap) {
-        cudaFree(b->d_desc);
-        b->desc_cap = std::max<int>((int)descs.size(), 2 * b->desc_cap);
-        if (cudaMalloc(&b->d_desc, sizeof(CavityDesc) * b->desc_cap) != cudaSuccess)
-            return bfail(b, FDTD_ERR_OOM, "descriptor alloc");
-    }
     if ((int)tiles.size() > b->tiles_cap) {
-        cudaFree(b->d_tiles);
+        pool_free(b->d_tiles, b->stream);
+        b->d_tiles = nullptr;
         b->tiles_cap = std::max<int>((int)tiles.size(), 2 * b->tiles_cap);
-        if (cudaMalloc(&b->d_tiles, sizeof(TileRec) * b->tiles_cap) != cudaSuccess)
-            return bfail(b, FDTD_ERR_OOM, "tile alloc");
+        if (pool_alloc((void **)&b->d_tiles, sizeof(TileRec) * b->tiles_cap, b->stream) != cudaSuccess)
+            return bfail(b, FDTD_ERR_OOM, "tile list alloc");
     }
-    if (!descs.empty())
-        if (cudaMemcpyAsync(b->d_desc, descs.data(), sizeof(CavityDesc) * descs.size(), cudaMemcpyHostToDevice,
-                            b->stream) != cudaSuccess)
-            return bfail(b, FDTD_ERR_CUDA, "descriptor upload");
-    if (!tiles.empty())
-        if (cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(TileRec) * tiles.size(), cudaMemcpyHostToDevice,
-                            b->stream) != cudaSuccess)
-            return bfail(b, FDTD_ERR_CUDA, "tile upload");
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "sync");
+    if (!tiles.empty() && cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(TileRec) * tiles.size(),
+                                          cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        return bfail(b, FDTD_ERR_CUDA, "tile list upload");
     b->ntiles = (int)tiles.size();
     b->grid = std::min(b->ntiles, G);
     b->dirty = false;
@@ -969,6 +1048,7 @@ static int batch_launch(fdtd_batch *b, int parity) {
     Shape s = resolve_shape(b->storage, b->tuning);
     FusedLaunch L{};
     L.recs = b->d_tiles;
+    L.step = b->d_step;
     L.ntiles = b->ntiles;
     L.parity = parity;
     L.status = b->d_status;
@@ -976,6 +1056,7 @@ static int batch_launch(fdtd_batch *b, int parity) {
     L.stages = s.stages;
     L.grid = b->grid;
     cudaError_t e = launch_fused_step(b->storage, L, b->stream);
+    if (e == cudaSuccess) e = launch_step_counter(b->d_step, b->stream);
     if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
     return FDTD_OK;
 }
@@ -987,14 +1068,15 @@ int fdtd_batch_step(fdtd_batch *b, int nsteps) {
     int left = nsteps;
     const int K = 16;
     if (b->tuning.use_graph && b->stream != nullptr && left >= K) {
-        GraphKey key{K, b->parity};
+        const int par = (int)(b->step & 1);
+        GraphKey key{K, par};
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
             cudaGraph_t g;
             if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return bfail(b, FDTD_ERR_CUDA, "capture");
             int rc = FDTD_OK;
-            for (int s = 0; s < K && !rc; ++s) rc = batch_launch(b, b->parity ^ (s & 1));
+            for (int s = 0; s < K && !rc; ++s) rc = batch_launch(b, par ^ (s & 1));
             cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
             if (rc) return rc;
             if (ee != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "end capture: %s", cudaGetErrorString(ee));
@@ -1009,13 +1091,12 @@ int fdtd_batch_step(fdtd_batch *b, int nsteps) {
         while (left >= K) {
             if (cudaGraphLaunch(it->second, b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "graph launch");
             left -= K;
+            b->step += K;
         }
-        for (fdtd_ctx *c : b->members) c->steps += nsteps - left;
     }
     for (; left > 0; --left) {
-        if (int rc = batch_launch(b, b->parity)) return rc;
-        b->parity ^= 1;
-        for (fdtd_ctx *c : b->members) ++c->steps;
+        if (int rc = batch_launch(b, (int)(b->step & 1))) return rc;
+        ++b->step;
     }
     return FDTD_OK;
 }
@@ -1023,6 +1104,7 @@ int fdtd_batch_step(fdtd_batch *b, int nsteps) {
 int fdtd_batch_sync(fdtd_batch *b) {
     if (!b) return FDTD_ERR_ARG;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "sync");
+    batch_free_retired_graphs(b);
     int h = 0;
     if (cudaMemcpy(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return bfail(b, FDTD_ERR_CUDA, "status read");
@@ -1036,11 +1118,15 @@ int fdtd_batch_sync(fdtd_batch *b) {
 void fdtd_batch_destroy(fdtd_batch *b) {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
-    while (!b->members.empty()) fdtd_batch_remove(b, b->members.back());
-    drop_graphs(b->graphs);
-    cudaFree(b->d_desc);
-    cudaFree(b->d_tiles);
-    cudaFree(b->d_status);
+    while (!b->members.empty()) fdtd_batch_remove(b, b->members.back().c);
+    cudaStreamSynchronize(b->stream);
+    batch_retire_graphs(b);
+    batch_free_retired_graphs(b);
+    pool_free(b->d_tiles, b->stream);
+    pool_free(b->d_status, b->stream);
+    pool_free(b->d_step, b->stream);
+    cudaStreamSynchronize(b->stream);
+    cudaEventDestroy(b->done_ev);
     delete b;
 }
 

@@ -123,8 +123,9 @@ struct alignas(16) TileRec {
     const float4 *table;         // COEF_ID8: per id two float4: (ce x,y,z,0), (ch x,y,z,0), folded
     const CUtensorMap *maps;     // kMapsPerCavity tensor maps in global memory
     void *dst[2][6];             // both copies of the six active arrays
+    long long stop;              // batch launch index from which this tile is skipped (member finished)
     int ntab;                    // COEF_ID8: table entries
-    int pad[17];
+    int pad[15];
 };
 static_assert(sizeof(TileRec) == 256, "TileRec must be 256 bytes");
 
@@ -188,6 +189,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         for (int r = 0; r < 4; ++r)
             if (mbar_try_wait(bar, parity)) return true;
         if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// Bounded wait that also gives up when another warp of the CTA has raised *abort; a wait that
+// runs out raises it.  sleep_ns > 0 sleeps between polls (for waits off the critical path).
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                                    volatile int *abort, unsigned sleep_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        if (sleep_ns) __nanosleep(sleep_ns);
+        for (int r = 0; r < 4; ++r)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (global_timer_ns() - t0 > limit_ns) {
+            *abort = 1;
+            return false;
+        }
     }
 }
 

@@ -23,16 +23,19 @@
 //     H to a double-buffered shared plane, and after one named barrier updates
 //     E on the same cells; H^{n+1/2}(k-1) of its cells stays in registers for
 //     the z derivative of the next plane;
-//   * halo warp: H on the row y = -1 and the column x = -1 (needed by the E
-//     update of the first row/column), phase A only.
-// One named barrier per plane; a consumer warp releases a unit (arrive on
-// empty[s]) once it no longer reads it.
+//   * halo warp: H on the row y = -1 (Hx, Hz) and the column x = -1 (Hy, Hz),
+//     needed by the E update of the tile's first row and column; phase A only.
+// One plain named barrier per plane; a consumer warp releases a unit (arrive
+// on empty[s]) once it no longer reads it.  Arithmetic uses the packed FP32x2
+// instructions of sm_100+ over each lane's two cells.
 //
 // Bytes per cell and plane: 6 loads + 6 stores of the storage type + one
 // material-id byte (49 B in FP32, 25 B in 16-bit storage); halo rows are
 // re-read from L2.  Every mbarrier wait is bounded in wall time (globaltimer):
-// on expiry the CTA latches STATUS_TIMEOUT, the producer drains its in-flight
-// copies (bounded again) and all warps exit.
+// the first wait that runs out raises a shared abort flag, after which every
+// wait returns at once; the consumers leave together at the next tile start
+// (an OR-reducing barrier) after latching STATUS_TIMEOUT, and the producer
+// stops issuing, drains its in-flight copies (bounded again) and exits.
 #include "launch.h"
 
 namespace fdtd {
@@ -56,6 +59,7 @@ template <typename T> struct FusedGeom {
 
 struct FusedParams {
     const TileRec *recs;
+    const long long *step;
     int ntiles;
     int parity;
     int *status;
@@ -90,13 +94,16 @@ __host__ __device__ constexpr int hbuf_floats() {
 constexpr int TAB_BYTES = kMaxTable * 2 * 16;   // shared copy of a cavity's material table (ce, ch float4)
 template <typename T, int TY>
 __host__ __device__ constexpr int smem_bytes(int stages) {
-    return 128 /*barriers*/ + NTR * (int)sizeof(TileRec) + TAB_BYTES + align_up(2 * hbuf_floats<TY>() * 4, 128) +
+    return 256 /*barriers, abort flag*/ + NTR * (int)sizeof(TileRec) + TAB_BYTES + align_up(2 * hbuf_floats<TY>() * 4, 128) +
            stages * slot_bytes<T, TY>() + 128 /*alignment slack*/;
 }
 template <int TY>
 __host__ __device__ constexpr int block_threads() {
     return (TY + 2) * 32;
 }
+
+// a - b for two packed floats in one instruction: fma(b, -1, a) rounds exactly like a - b.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -163,17 +170,20 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + 8;
-    TileRec *recs = reinterpret_cast<TileRec *>(smem + 128);
-    float4 *stab = reinterpret_cast<float4 *>(smem + 128 + NTR * sizeof(TileRec));
-    float *hbuf = reinterpret_cast<float *>(smem + 128 + NTR * sizeof(TileRec) + TAB_BYTES);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 128);   // set by the first wait that runs out
+    TileRec *recs = reinterpret_cast<TileRec *>(smem + 256);
+    float4 *stab = reinterpret_cast<float4 *>(smem + 256 + NTR * sizeof(TileRec));
+    float *hbuf = reinterpret_cast<float *>(smem + 256 + NTR * sizeof(TileRec) + TAB_BYTES);
     unsigned char *slots = reinterpret_cast<unsigned char *>(hbuf) + align_up(2 * HB * 4, 128);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = P.stages, SB = P.slot_bytes;
+    const long long step = P.step ? *P.step : 0;   // launch index within a batch
     const bool inject = P.inject_timeout_us > 0 && blockIdx.x == 0;
     const uint64_t lim = inject ? (uint64_t)P.inject_timeout_us * 1000ull : kWaitLimitNs;
 
     if (threadIdx.x == 0) {
+        *abort_flag = 0;
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], NCW);
@@ -189,18 +199,21 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
         int s = 0;           // slot of the next unit
         uint32_t rnd = 0;    // parity of the ring round of the next unit
         bool ok = true;
-        for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x, ++m) {
-            TileRec *rec = &recs[m % NTR];
+        for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+            if (__ldg(&P.recs[t].stop) <= step) continue;   // member already took its last step
+            TileRec *rec = &recs[m++ % NTR];
             int kb = 0, kz1 = 0;
             for (int k = 0;; ++k) {
                 if (issued >= S) {   // wait until unit issued - S (same slot, previous round) is released
-                    const bool w = FDTD_PRODUCER_SLEEP_NS > 0
-                                       ? mbar_wait_bounded_sleep(&empty[s], rnd ^ 1u, lim, FDTD_PRODUCER_SLEEP_NS)
-                                       : mbar_wait_bounded(&empty[s], rnd ^ 1u, lim);
+                    const bool w = mbar_wait_abortable(&empty[s], rnd ^ 1u, lim, abort_flag, FDTD_PRODUCER_SLEEP_NS);
                     if (!__all_sync(0xffffffffu, w)) {
                         ok = false;
                         break;
                     }
+                }
+                if (__any_sync(0xffffffffu, *abort_flag != 0)) {
+                    ok = false;
+                    break;
                 }
                 if (k == 0) {   // first unit of the tile: publish the tile record (after the slot wait)
                     const uint32_t *src = reinterpret_cast<const uint32_t *>(P.recs + t);
@@ -249,19 +262,21 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
     const int y = halo ? -1 : warp;             // row of this warp (tile-local)
     const int x = 2 * lane;                     // first of the lane's two cells
     const int bx = x + HX, by = y + 1;          // position in a field box
-    int sa = 0, m = 0, hb = 0;   // slot of the current unit
-    uint32_t pa = 0;             // phase parity of that slot
+    int sa = 0, m = 0, hb = 0;                  // slot of the current unit, tile count, H buffer
+    uint32_t pa = 0;                            // phase parity of that slot
     const float4 *tab_cached = nullptr;
     float2 hpx = make_float2(0.f, 0.f), hpy = make_float2(0.f, 0.f);   // H^{n+1/2}(k-1) of own cells
+    auto wait_full = [&](int slot, uint32_t par) { return mbar_wait_abortable(&full[slot], par, lim, abort_flag, 0); };
 
-    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x, ++m) {
-        bool ok = mbar_wait_bounded(&full[sa], pa, lim);   // the tile record is valid from here
-        // every consumer warp is past the previous tile's E phase here; a timeout anywhere ends the CTA
-        if (bar_sync_or(2, NCT, !ok)) {
+    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+        if (__ldg(&P.recs[t].stop) <= step) continue;   // same skip rule as the producer
+        bool ok = wait_full(sa, pa);   // the tile record is valid once its first unit has landed
+        // every consumer warp is past the previous tile's E phase here; an abort anywhere ends the CTA
+        if (bar_sync_or(2, NCT, !ok || *abort_flag != 0)) {
             if (threadIdx.x == 0) atomicOr(P.status, STATUS_TIMEOUT);
             return;
         }
-        const TileRec *rec = &recs[m % NTR];
+        const TileRec *rec = &recs[m++ % NTR];
         const int x0 = rec->x0, y0 = rec->y0, kz0 = rec->kz0, kz1 = rec->kz1;
         const int nx = rec->nx, ny = rec->ny;
         const long long pitch = rec->pitch, plane = rec->plane;
@@ -285,6 +300,37 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
         const int gi = x0 + x;
         const int kb = kz0 > 0 ? kz0 - 1 : kz0;
 
+        auto at = [&](const T *base, int f, int xx, int yy) { return base + f * FE + yy * BX + xx; };
+        auto ch_pair = [&](const uint8_t *ida_, int yy, float2 &cx, float2 &cy, float2 &cz) {
+            cx = make_float2(ch_s0, ch_s0);
+            cy = make_float2(ch_s1, ch_s1);
+            cz = make_float2(ch_s2, ch_s2);
+            if (id_mode && !ch_uni) {
+                const uint32_t ip = *reinterpret_cast<const uint16_t *>(ida_ + (yy + 1) * G::IBX + x + G::IDX_HALO);
+                const float4 a = table[2 * (ip & 0xff) + 1], b = table[2 * (ip >> 8) + 1];
+                cx = make_float2(a.x, b.x);
+                cy = make_float2(a.y, b.y);
+                cz = make_float2(a.z, b.z);
+            }
+        };
+        // halo row y = -1 of the plane held by units U (plane) and V (plane + 1): Hx and Hz only
+        auto halo_row = [&](const T *U, const T *V, const uint8_t *idu, float *hbuf_) {
+            const int ry = 0;   // box row of y = -1
+            const float2 ey_ = Pair<T>::ld(at(U, 1, bx, ry)), ez_ = Pair<T>::ld(at(U, 2, bx, ry));
+            const float2 ex_ = Pair<T>::ld(at(U, 0, bx, ry));
+            const float2 ex_y1 = Pair<T>::ld(at(U, 0, bx, ry + 1)), ez_y1 = Pair<T>::ld(at(U, 2, bx, ry + 1));
+            const float ey_x2 = Pair<T>::ld1(at(U, 1, bx + 2, ry));
+            const float2 eyb = Pair<T>::ld(at(V, 1, bx, ry));
+            float2 hx_ = Pair<T>::ld(at(U, 3, bx, ry)), hz_ = Pair<T>::ld(at(U, 5, bx, ry));
+            float2 cx, cy, cz;
+            ch_pair(idu, -1, cx, cy, cz);
+            const float2 ey_x1 = make_float2(ey_.y, ey_x2);
+            hx_ = __ffma2_rn(cx, sub2(sub2(eyb, ey_), sub2(ez_y1, ez_)), hx_);
+            hz_ = __ffma2_rn(cz, sub2(sub2(ex_y1, ex_), sub2(ey_x1, ey_)), hz_);
+            *reinterpret_cast<float2 *>(hbuf_ + x + 2) = hx_;
+            *reinterpret_cast<float2 *>(hbuf_ + 2 * HC + x + 2) = hz_;
+        };
+
         for (int k = kb; k < kz1; ++k) {
             int sb = sa + 1;
             uint32_t pb = pa;
@@ -292,8 +338,7 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                 sb = 0;
                 pb ^= 1u;
             }
-            ok = ok && mbar_wait_bounded(&full[sa], pa, lim);
-            ok = ok && mbar_wait_bounded(&full[sb], pb, lim);
+            ok = wait_full(sa, pa) && wait_full(sb, pb);
             const bool prologue = k < kz0;
             const T *A = reinterpret_cast<const T *>(slots + sa * SB);
             const T *B = reinterpret_cast<const T *>(slots + sb * SB);
@@ -301,53 +346,46 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
             float *hn = hbuf + hb * HB;
             float2 ex = make_float2(0.f, 0.f), ey = ex, ez = ex, hx = ex, hy = ex, hz = ex;
             uint32_t idpair = 0;
-            float4 ce_a = make_float4(ce_s0, ce_s1, ce_s2, 0.f), ce_b = ce_a;   // ce of the two cells
 
-            // ---------------- phase A: H^{n+1/2} on own cells (+ the halo column for the halo warp)
-            if (ok) {
-                auto at = [&](const T *base, int f, int xx, int yy) { return base + f * FE + yy * BX + xx; };
-                ex = Pair<T>::ld(at(A, 0, bx, by));
-                ey = Pair<T>::ld(at(A, 1, bx, by));
-                ez = Pair<T>::ld(at(A, 2, bx, by));
-                const float2 ex_y1 = Pair<T>::ld(at(A, 0, bx, by + 1));
-                const float2 ez_y1 = Pair<T>::ld(at(A, 2, bx, by + 1));
-                const float ey_x2 = Pair<T>::ld1(at(A, 1, bx + 2, by));
-                const float ez_x2 = Pair<T>::ld1(at(A, 2, bx + 2, by));
-                const float2 exb = Pair<T>::ld(at(B, 0, bx, by));
-                const float2 eyb = Pair<T>::ld(at(B, 1, bx, by));
-                hx = Pair<T>::ld(at(A, 3, bx, by));
-                hy = Pair<T>::ld(at(A, 4, bx, by));
-                hz = Pair<T>::ld(at(A, 5, bx, by));
-                float2 chx = make_float2(ch_s0, ch_s0), chy = make_float2(ch_s1, ch_s1),
-                       chz = make_float2(ch_s2, ch_s2);
-                if (id_mode) {
-                    idpair = *reinterpret_cast<const uint16_t *>(ida + by * G::IBX + x + G::IDX_HALO);
-                    if (!ch_uni) {
-                        const float4 a = (table[2 * (idpair & 0xff) + 1]);
-                        const float4 b = (table[2 * (idpair >> 8) + 1]);
-                        chx = make_float2(a.x, b.x);
-                        chy = make_float2(a.y, b.y);
-                        chz = make_float2(a.z, b.z);
+            // ---------------- phase A: H^{n+1/2} on own cells; the halo warp: row y = -1 and column x = -1
+            if (!halo) {
+                if (ok) {
+                    ex = Pair<T>::ld(at(A, 0, bx, by));
+                    ey = Pair<T>::ld(at(A, 1, bx, by));
+                    ez = Pair<T>::ld(at(A, 2, bx, by));
+                    const float2 ex_y1 = Pair<T>::ld(at(A, 0, bx, by + 1));
+                    const float2 ez_y1 = Pair<T>::ld(at(A, 2, bx, by + 1));
+                    const float ey_x2 = Pair<T>::ld1(at(A, 1, bx + 2, by));
+                    const float ez_x2 = Pair<T>::ld1(at(A, 2, bx + 2, by));
+                    const float2 exb = Pair<T>::ld(at(B, 0, bx, by));
+                    const float2 eyb = Pair<T>::ld(at(B, 1, bx, by));
+                    hx = Pair<T>::ld(at(A, 3, bx, by));
+                    hy = Pair<T>::ld(at(A, 4, bx, by));
+                    hz = Pair<T>::ld(at(A, 5, bx, by));
+                    if (id_mode) idpair = *reinterpret_cast<const uint16_t *>(ida + by * G::IBX + x + G::IDX_HALO);
+                    float2 chx, chy, chz;
+                    ch_pair(ida, y, chx, chy, chz);
+                    // packed over the lane's two cells; operand order makes each bracket -(curl E), so
+                    // H + ch * bracket rounds exactly like H - ch * curl E
+                    const float2 ez_x1 = make_float2(ez.y, ez_x2), ey_x1 = make_float2(ey.y, ey_x2);
+                    hx = __ffma2_rn(chx, sub2(sub2(eyb, ey), sub2(ez_y1, ez)), hx);
+                    hy = __ffma2_rn(chy, sub2(sub2(ez_x1, ez), sub2(exb, ex)), hy);
+                    hz = __ffma2_rn(chz, sub2(sub2(ex_y1, ex), sub2(ey_x1, ey)), hz);
+                    const int o = by * HP + x + 2;
+                    *reinterpret_cast<float2 *>(hn + o) = hx;
+                    *reinterpret_cast<float2 *>(hn + HC + o) = hy;
+                    *reinterpret_cast<float2 *>(hn + 2 * HC + o) = hz;
+                    if (!prologue && gj < ny && gi < nx) {
+                        const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                        Pair<T>::st(dst[3] + g, hx.x, hx.y);
+                        Pair<T>::st(dst[4] + g, hy.x, hy.y);
+                        Pair<T>::st(dst[5] + g, hz.x, hz.y);
                     }
                 }
-                hx.x -= chx.x * ((ez_y1.x - ez.x) - (eyb.x - ey.x));
-                hx.y -= chx.y * ((ez_y1.y - ez.y) - (eyb.y - ey.y));
-                hy.x -= chy.x * ((exb.x - ex.x) - (ez.y - ez.x));
-                hy.y -= chy.y * ((exb.y - ex.y) - (ez_x2 - ez.y));
-                hz.x -= chz.x * ((ey.y - ey.x) - (ex_y1.x - ex.x));
-                hz.y -= chz.y * ((ey_x2 - ey.y) - (ex_y1.y - ex.y));
-                const int o = by * HP + x + 2;
-                *reinterpret_cast<float2 *>(hn + o) = hx;
-                *reinterpret_cast<float2 *>(hn + HC + o) = hy;
-                *reinterpret_cast<float2 *>(hn + 2 * HC + o) = hz;
-                if (!halo && !prologue && gj < ny && gi < nx) {
-                    const long long g = (long long)k * plane + (long long)gj * pitch + gi;
-                    Pair<T>::st(dst[3] + g, hx.x, hx.y);
-                    Pair<T>::st(dst[4] + g, hy.x, hy.y);
-                    Pair<T>::st(dst[5] + g, hz.x, hz.y);
-                }
-                if (halo && lane < TY) {
-                    // column x = -1, row yy = lane: Hy and Hz (used by Ez and Ey at x = 0)
+            } else if (ok && !prologue) {
+                halo_row(A, B, ida, hn);
+                if (lane < TY) {
+                    // column x = -1 of row yy: Hy and Hz (used by Ez and Ey at x = 0)
                     const int yy = lane, cbx = HX - 1, cby = yy + 1;
                     const float cex_ = Pair<T>::ld1(at(A, 0, cbx, cby));
                     const float cey_ = Pair<T>::ld1(at(A, 1, cbx, cby));
@@ -358,7 +396,7 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     const float cexb = Pair<T>::ld1(at(B, 0, cbx, cby));
                     float cchy = ch_s1, cchz = ch_s2;
                     if (id_mode && !ch_uni) {
-                        const float4 a = (table[2 * ida[cby * G::IBX + G::IDX_HALO - 1] + 1]);
+                        const float4 a = table[2 * ida[cby * G::IBX + G::IDX_HALO - 1] + 1];
                         cchy = a.y;
                         cchz = a.z;
                     }
@@ -370,44 +408,44 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     hn[2 * HC + cby * HP + 1] = chz_;
                 }
             }
-            if (bar_sync_or(1, NCT, !ok)) {
-                if (threadIdx.x == 0) atomicOr(P.status, STATUS_TIMEOUT);
-                return;
-            }
+            // all of plane k's H (own rows, halo row and column) is in hn from here on
+            asm volatile("bar.sync 1, %0;" ::"r"(NCT) : "memory");
 
             // ---------------- phase B: E^{n+1} on own cells (row warps)
-            if (!halo && !prologue) {
-                const int o = by * HP + x + 2;
-                const float2 hx_ym = *reinterpret_cast<const float2 *>(hn + o - HP);
-                const float2 hz_ym = *reinterpret_cast<const float2 *>(hn + 2 * HC + o - HP);
-                const float hy_xm = hn[HC + o - 1];
-                const float hz_xm = hn[2 * HC + o - 1];
-                if (id_mode) {
-                    ce_a = (table[2 * (idpair & 0xff)]);
-                    ce_b = (table[2 * (idpair >> 8)]);
+            if (!halo) {
+                if (ok && !prologue) {
+                    const int o = by * HP + x + 2;
+                    const float2 hx_ym = *reinterpret_cast<const float2 *>(hn + o - HP);
+                    const float2 hz_ym = *reinterpret_cast<const float2 *>(hn + 2 * HC + o - HP);
+                    const float hy_xm = hn[HC + o - 1];
+                    const float hz_xm = hn[2 * HC + o - 1];
+                    float4 ce_a = make_float4(ce_s0, ce_s1, ce_s2, 0.f), ce_b = ce_a;
+                    if (id_mode) {
+                        ce_a = table[2 * (idpair & 0xff)];
+                        ce_b = table[2 * (idpair >> 8)];
+                    }
+                    // PEC: a zero coefficient leaves a tangential E exactly unchanged (e + 0 * c == e)
+                    const bool k1 = k >= 1, j1 = gj >= 1, i1 = gi >= 1;
+                    const float2 cex = (j1 && k1) ? make_float2(ce_a.x, ce_b.x) : make_float2(0.f, 0.f);
+                    const float2 cey = make_float2((i1 && k1) ? ce_a.y : 0.f, k1 ? ce_b.y : 0.f);
+                    const float2 cez = make_float2((i1 && j1) ? ce_a.z : 0.f, j1 ? ce_b.z : 0.f);
+                    const float2 hz_xm2 = make_float2(hz_xm, hz.x), hy_xm2 = make_float2(hy_xm, hy.x);
+                    ex = __ffma2_rn(cex, sub2(sub2(hz, hz_ym), sub2(hy, hpy)), ex);
+                    ey = __ffma2_rn(cey, sub2(sub2(hx, hpx), sub2(hz, hz_xm2)), ey);
+                    ez = __ffma2_rn(cez, sub2(sub2(hy, hy_xm2), sub2(hx, hx_ym)), ez);
+                    if (gj < ny && gi < nx) {
+                        const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                        Pair<T>::st(dst[0] + g, ex.x, ex.y);
+                        Pair<T>::st(dst[1] + g, ey.x, ey.y);
+                        Pair<T>::st(dst[2] + g, ez.x, ez.y);
+                    }
                 }
-                const float2 cex = make_float2(ce_a.x, ce_b.x), cey = make_float2(ce_a.y, ce_b.y),
-                             cez = make_float2(ce_a.z, ce_b.z);
-                if (gj >= 1 && k >= 1) {
-                    ex.x += cex.x * ((hz.x - hz_ym.x) - (hy.x - hpy.x));
-                    ex.y += cex.y * ((hz.y - hz_ym.y) - (hy.y - hpy.y));
-                }
-                if (gi >= 1 && k >= 1) ey.x += cey.x * ((hx.x - hpx.x) - (hz.x - hz_xm));
-                if (k >= 1) ey.y += cey.y * ((hx.y - hpx.y) - (hz.y - hz.x));
-                if (gi >= 1 && gj >= 1) ez.x += cez.x * ((hy.x - hy_xm) - (hx.x - hx_ym.x));
-                if (gj >= 1) ez.y += cez.y * ((hy.y - hy.x) - (hx.y - hx_ym.y));
-                if (gj < ny && gi < nx) {
-                    const long long g = (long long)k * plane + (long long)gj * pitch + gi;
-                    Pair<T>::st(dst[0] + g, ex.x, ex.y);
-                    Pair<T>::st(dst[1] + g, ey.x, ey.y);
-                    Pair<T>::st(dst[2] + g, ez.x, ez.y);
-                }
+                hpx = hx;
+                hpy = hy;
             }
-            hpx = hx;
-            hpy = hy;
             // ---------------- release the units this warp no longer reads
-            __syncwarp();
             const bool last = k == kz1 - 1;
+            __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&empty[sa]);
                 if (last) mbar_arrive(&empty[sb]);
@@ -431,6 +469,7 @@ cudaError_t launch_typed(const FusedLaunch &L, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     FusedParams P;
     P.recs = L.recs;
+    P.step = L.step;
     P.ntiles = L.ntiles;
     P.parity = L.parity;
     P.status = L.status;
@@ -487,6 +526,13 @@ cudaError_t launch_fused_step(int storage, const FusedLaunch &L, cudaStream_t s)
     cudaError_t e = cudaErrorInvalidValue;
     FDTD_DISPATCH(storage, L.tile_y, e = launch_typed<T, TY>(L, s));
     return e;
+}
+
+__global__ void step_counter_kernel(long long *c) { *c += 1; }
+
+cudaError_t launch_step_counter(long long *counter, cudaStream_t s) {
+    step_counter_kernel<<<1, 1, 0, s>>>(counter);
+    return cudaGetLastError();
 }
 
 void fused_box(int storage, int tile_y, int *box_x, int *box_y, int *halo_x) {

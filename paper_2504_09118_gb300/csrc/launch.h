@@ -23,6 +23,7 @@ int reduction_blocks();
 
 struct FusedLaunch {
     const TileRec *recs;       // device array, one record per tile
+    const long long *step;     // device launch counter compared with TileRec::stop (NULL: no tile skipped)
     int ntiles;
     int parity;
     int *status;
@@ -35,6 +36,8 @@ struct FusedLaunch {
 int fused_smem_bytes(int storage, int tile_y, int stages);
 cudaError_t fused_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
 cudaError_t launch_fused_step(int storage, const FusedLaunch &L, cudaStream_t s);
+// *counter += 1 on the stream (advances a batch's device launch counter after each step).
+cudaError_t launch_step_counter(long long *counter, cudaStream_t s);
 // Box sizes used to encode the tensor maps of the fused kernel.
 void fused_box(int storage, int tile_y, int *box_x, int *box_y, int *halo_x);
 

@@ -156,3 +156,34 @@ def test_batch_rejects_mismatches():
         c.close()
     finally:
         binding.fdtd_batch_destroy(b)
+
+
+def test_members_stop_at_their_own_step_counts():
+    """fdtd_batch_set_steps freezes each member after its own count, inside graph-replayed chunks."""
+    import torch
+    from paper_2504_09118_gb300 import binding
+    s = torch.cuda.Stream()
+    counts = [7, 16, 23, 40, 41, 0]
+    solo = make_members(0, s, seed=11)[:len(counts)]
+    for (c, *_), n in zip(solo, counts):
+        c.tune(kernel=2, tile_y=8)
+        c.step(n)
+    ref = [c.get_fields() for c, *_ in solo]
+    load = torch.cuda.Stream()   # members on their own stream: removal orders it after the batch
+    mem = make_members(0, load, seed=11)[:len(counts)]
+    b = binding.fdtd_batch_create(0, s)
+    binding.fdtd_batch_set_tuning(b, kernel=2, tile_y=8, use_graph=1)
+    for (c, *_), n in zip(mem, counts):
+        binding.fdtd_batch_add(b, c.handle)
+        binding.fdtd_batch_set_steps(b, c.handle, n)
+    binding.fdtd_batch_step(b, 48)          # three 16-step graph chunks: everyone is done by then
+    assert binding.fdtd_batch_steps_done(b) == 48
+    for c, *_ in mem:
+        binding.fdtd_batch_remove(b, c.handle)
+    binding.fdtd_batch_destroy(b)
+    for (c, *_), n, r in zip(mem, counts, ref):
+        assert c.steps_done == n
+        for x, y in zip(c.get_fields(), r):
+            assert np.array_equal(x, y)
+    for c, *_ in solo + mem:
+        c.close()
