@@ -165,9 +165,14 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
     constexpr int HB = hbuf_floats<TY>();       // floats per H plane buffer
     constexpr int HC = (TY + 1) * HP;           // floats per component in a buffer
 
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // Indexed directly (no pointer round trip through an integer) so that every access keeps the
+    // shared-memory address space.  The dynamic region starts on a 1 KiB boundary when the kernel
+    // declares no static shared memory; the check below turns any other layout into an error.
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (smem_u32(smem) & 127u) {
+        if (threadIdx.x == 0) atomicOr(P.status, STATUS_BADINDEX);
+        return;
+    }
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + 8;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 128);   // set by the first wait that runs out
