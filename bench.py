@@ -46,6 +46,8 @@ WORKLOADS = {
     "batch256": dict(kind="batch", count=256, lo=16, hi=96, steps=500, seed=5, storage=0),
     # Poisson stream: 200 req/s, sides log-uniform 16-256, steps U{100..2000}, BF16 flag Bernoulli(1/2)
     "serve": dict(kind="serve", rate=200.0, seed=6, budget_gb=120),
+    # error study: 384^3 spheres, 1000 steps, FP32 / FP16 / BF16 storage against the FP64 oracle
+    "precision": dict(kind="precision", n=(384, 384, 384), steps=1000, sphere_seed=3, field_seed=4, spheres=32),
 }
 # Launch configuration of the fused kernel that the bench times (the full-size parity test uses the same).
 BENCH_TUNING = dict(kernel=2, tile_y=8, stages=4, zchunk=0, ctas_per_sm=0, use_graph=1)
@@ -164,7 +166,7 @@ def run_reference(args, w, wname):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    if "n" not in w:
+    if "n" not in w or w.get("kind"):
         print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm is timed on the single-cavity "
                                                               f"workloads only, not on '{wname}'"}), flush=True)
         return
@@ -295,6 +297,54 @@ def run_serve(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args, w):
+    """Storage precision study: rel-L2 per field and energy drift of FP32/FP16/BF16 GPU runs against
+    the FP64 oracle (OpenMP build on the host cores) and the FP32 GPU run, same seeded input."""
+    import torch
+    import oracle
+    from paper_2504_09118_gb300 import Cavity
+    torch.cuda.set_device(0)
+    nx, ny, nz = w["n"]
+    steps = args.precision_steps or w["steps"]
+    ce, ch = sphere_coefs(w)
+    f = ci.random_fields(w["field_seed"], nx, ny, nz)
+    runs = {}
+    for st, name in ((0, "f32"), (1, "f16"), (2, "bf16")):
+        with Cavity(nx, ny, nz, ci.COURANT_HALF_DT, 1.0, ce, ch, st) as cav:
+            cav.tune(**BENCH_TUNING)
+            cav.set_fields(f)
+            w0 = cav.energy()
+            cav.step(steps)
+            w1 = cav.energy()
+            runs[name] = (cav.get_fields(), w0, w1)
+    t0 = time.perf_counter()
+    ref = oracle.as_f64(f)
+    ce64 = [c.astype(np.float64) for c in ce]
+    W0 = oracle.energy(ref, ce64, ch, ci.COURANT_HALF_DT)
+    oracle.step(ref, ce64, ch, steps, omp=True)
+    W1 = oracle.energy(ref, ce64, ch, ci.COURANT_HALF_DT)
+    t_or = time.perf_counter() - t0
+
+    def rel(a, b):
+        out = {}
+        for c, name in enumerate(ci.COMPONENTS):
+            m = ci.extent_mask(name, nx, ny, nz)
+            d = np.asarray(a[c], np.float64)[m] - np.asarray(b[c], np.float64)[m]
+            out[name] = float(np.linalg.norm(d) / np.linalg.norm(np.asarray(b[c], np.float64)[m]))
+        return out
+
+    res = {}
+    for name, (g, w0, w1) in runs.items():
+        res[name] = {"rel_l2_vs_oracle": rel(g, ref), "energy_drift": (w1 - w0) / w0,
+                     "energy_vs_oracle_final": (w1 - W1) / W1}
+        if name != "f32":
+            res[name]["rel_l2_vs_f32_gpu"] = rel(g, runs["f32"][0])
+    line = {"metric": "rel-L2 and energy drift", "workload": "precision", "cells": [nx, ny, nz], "steps": steps,
+            "oracle": {"energy_drift": (W1 - W0) / W0, "seconds": round(t_or, 1), "threads": oracle.threads(True)},
+            "storage": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -307,6 +357,7 @@ def main():
     ap.add_argument("--clocks-csv", default=None)
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-seq-requests", type=int, default=150)
+    ap.add_argument("--precision-steps", type=int, default=0)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "ours" and w.get("kind") == "batch":
@@ -314,6 +365,9 @@ def main():
         return
     if args.impl == "ours" and w.get("kind") == "serve":
         run_serve(args, w)
+        return
+    if args.impl == "ours" and w.get("kind") == "precision":
+        run_precision(args, w)
         return
     if args.impl == "reference":
         run_reference(args, w, args.workload)

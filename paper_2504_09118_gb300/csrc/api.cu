@@ -48,8 +48,11 @@ int num_sms() {
 size_t esize(int storage) { return storage == FDTD_F32 ? 4 : 2; }
 
 struct GraphKey {
-    int steps, parity;
-    bool operator<(const GraphKey &o) const { return steps != o.steps ? steps < o.steps : parity < o.parity; }
+    int steps, parity, kind = 0;
+    bool operator<(const GraphKey &o) const {
+        if (kind != o.kind) return kind < o.kind;
+        return steps != o.steps ? steps < o.steps : parity < o.parity;
+    }
 };
 
 }  // namespace
@@ -79,10 +82,14 @@ struct fdtd_ctx {
     double *d_partial = nullptr, *d_out = nullptr;
     float *d_stage = nullptr;    // canonical staging buffer for host transfers (lazy)
     unsigned *d_max = nullptr;
-    CUtensorMap *d_maps = nullptr;
+    CUtensorMap *d_maps = nullptr;          // kMapSets x kMapsPerCavity
+    std::vector<CUtensorMap> host_maps[kMapSets];
+    int maps_by[kMapSets] = {0, 0};         // box height each map set was encoded for (0: not yet)
     CavityDesc *d_desc = nullptr;
-    TileRec *d_tiles = nullptr;
-    int ntiles = 0, grid = 0, tiles_ty = 0, maps_ty = 0;
+    struct TileList {
+        TileRec *d = nullptr;
+        int n = 0, grid = 0, key = 0;
+    } tl[2];                                // [0] one-step kernel, [1] two-step kernel
     int ch_uniform = 1;
     fdtd_tuning tuning{};
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -224,14 +231,16 @@ int upload_desc(fdtd_ctx *c) {
     return FDTD_OK;
 }
 
-// Encode the 13 tensor maps of a cavity for a given tile height.
-int encode_maps(fdtd_ctx *c, int tile_y) {
-    if (c->maps_ty == tile_y) return FDTD_OK;
+// Encode the 13 tensor maps of map set `set` (0: one-step kernel, 1: two-step kernel) for
+// boxes box_y rows high.  Set 1 sits right after set 0 in the context's map array.
+int encode_maps(fdtd_ctx *c, int set, int box_y) {
+    if (c->maps_by[set] == box_y) return FDTD_OK;
     auto enc = get_encode();
     if (!enc) return fail(c, FDTD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    int bx, by, hx;
-    fused_box(c->storage, tile_y, &bx, &by, &hx);
-    std::vector<CUtensorMap> maps(kMapsPerCavity);
+    const int hx = 16 / (int)esize(c->storage);
+    const int bx = kTileX + 2 * hx;
+    std::vector<CUtensorMap> &maps = c->host_maps[set];
+    maps.assign(kMapsPerCavity, CUtensorMap{});
     const size_t es = esize(c->storage);
     const CUtensorMapDataType dt = c->storage == FDTD_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : c->storage == FDTD_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -241,7 +250,7 @@ int encode_maps(fdtd_ctx *c, int tile_y) {
     for (int cp = 0; cp < 2; ++cp)
         for (int f = 0; f < 6; ++f) {
             cuuint64_t gstr[2] = {(cuuint64_t)c->pitch * es, (cuuint64_t)c->pitch * c->ny * es};
-            cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+            cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)box_y, 1};
             CUresult r = enc(&maps[cp * 6 + f], dt, 3, c->fields[cp][f], gdim, gstr, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -249,33 +258,40 @@ int encode_maps(fdtd_ctx *c, int tile_y) {
         }
     if (c->id) {
         cuuint64_t gstr[2] = {(cuuint64_t)c->pitch, (cuuint64_t)c->pitch * c->ny};
-        cuuint32_t box[3] = {(cuuint32_t)(kTileX + 16), (cuuint32_t)by, 1};
+        cuuint32_t box[3] = {(cuuint32_t)(kTileX + 16), (cuuint32_t)box_y, 1};
         CUresult r = enc(&maps[12], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->id, gdim, gstr, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(c, FDTD_ERR_CUDA, "id tensor map encode failed (%d)", (int)r);
-    } else {
-        memset(&maps[12], 0, sizeof(CUtensorMap));
     }
-    CK(c, cudaMemcpyAsync(c->d_maps, maps.data(), sizeof(CUtensorMap) * kMapsPerCavity, cudaMemcpyHostToDevice,
-                          c->stream));
+    CK(c, cudaMemcpyAsync(c->d_maps + set * kMapsPerCavity, maps.data(), sizeof(CUtensorMap) * kMapsPerCavity,
+                          cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    c->maps_ty = tile_y;
+    c->maps_by[set] = box_y;
     return FDTD_OK;
 }
 
 struct Shape {
+    int kind;   // 0: one step per launch, 1: two steps per launch
     int tile_y, stages, ctas_per_sm;
 };
 
-Shape resolve_shape(int storage, const fdtd_tuning &t) {
+// Launch shape of kernel kind 0 (one step) or 1 (two steps) from the tuning (invalid fields -> defaults).
+Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0) {
     static std::mutex mu;
-    static std::map<int, int> occ_cache;   // (storage, tile_y, stages) -> max CTAs per SM
+    static std::map<int, int> occ_cache;   // (kind, storage, tile_y, stages) -> max CTAs per SM
     Shape s;
-    s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 16) ? t.tile_y : 8;
+    s.kind = kind;
+    if (kind == 0)
+        s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 16) ? t.tile_y : 8;
+    else
+        s.tile_y = (t.tile_y == 8 || t.tile_y == 12) ? t.tile_y : 8;
     s.stages = (t.stages >= 3 && t.stages <= 8) ? t.stages : 4;
-    while (s.stages > 3 && fused_smem_bytes(storage, s.tile_y, s.stages) > 227 * 1024) --s.stages;
-    const int key = (storage * 64 + s.tile_y) * 16 + s.stages;
+    auto smem = [&](int st) {
+        return kind == 0 ? fused_smem_bytes(storage, s.tile_y, st) : fused2_smem_bytes(storage, s.tile_y, st);
+    };
+    while (s.stages > 3 && smem(s.stages) > 227 * 1024) --s.stages;
+    const int key = ((kind * 4 + storage) * 64 + s.tile_y) * 16 + s.stages;
     int occ = 0;
     {
         std::lock_guard<std::mutex> g(mu);
@@ -283,7 +299,9 @@ Shape resolve_shape(int storage, const fdtd_tuning &t) {
         if (it != occ_cache.end()) {
             occ = it->second;
         } else {
-            if (fused_occupancy(storage, s.tile_y, s.stages, &occ) != cudaSuccess || occ < 1) occ = 1;
+            cudaError_t e = kind == 0 ? fused_occupancy(storage, s.tile_y, s.stages, &occ)
+                                      : fused2_occupancy(storage, s.tile_y, s.stages, &occ);
+            if (e != cudaSuccess || occ < 1) occ = 1;
             occ_cache[key] = occ;
         }
     }
@@ -292,14 +310,14 @@ Shape resolve_shape(int storage, const fdtd_tuning &t) {
 }
 
 // Planes per tile for a cavity given the column count and grid size (load balance vs prologue overhead).
-int choose_zlen(long long cols, int nz, int grid, int zchunk) {
+int choose_zlen(long long cols, int nz, int grid, int zchunk, int prologue_planes) {
     if (zchunk > 0) return std::min(zchunk, nz);
     long long best = -1;
     int bestL = nz;
     for (int L = nz; L >= 1; --L) {
         const long long nch = (nz + L - 1) / L;
         const long long waves = (cols * nch + grid - 1) / grid;
-        const long long cost = waves * (L + 1);
+        const long long cost = waves * (L + prologue_planes);
         if (best < 0 || cost < best) {
             best = cost;
             bestL = L;
@@ -308,10 +326,11 @@ int choose_zlen(long long cols, int nz, int grid, int zchunk) {
     return bestL;
 }
 
-TileRec base_rec(const fdtd_ctx *c, int parity_off) {
+TileRec base_rec(const fdtd_ctx *c, int parity_off, int set = 0) {
     TileRec r{};
     r.nx = c->nx;
     r.ny = c->ny;
+    r.nz = c->nz;
     r.pitch = c->pitch;
     r.mode = c->coef_mode;
     r.plane = (long long)c->pitch * c->ny;
@@ -325,7 +344,7 @@ TileRec base_rec(const fdtd_ctx *c, int parity_off) {
     r.table = reinterpret_cast<const float4 *>(c->table_fused);
     r.ntab = c->ntab;
     r.stop = LLONG_MAX;
-    r.maps = c->d_maps;
+    r.maps = c->d_maps + set * kMapsPerCavity;
     for (int f = 0; f < 6; ++f) {
         r.dst[0][f] = c->fields[0][f];
         r.dst[1][f] = c->fields[1][f];
@@ -333,38 +352,43 @@ TileRec base_rec(const fdtd_ctx *c, int parity_off) {
     return r;
 }
 
-void append_tiles(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y, int zlen) {
-    const TileRec b = base_rec(c, parity_off);
+// Tiles of the one-step kernel (kind 0: 64 cells wide) or the two-step kernel (kind 1: W wide).
+void append_tiles(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y, int zlen, int kind = 0) {
+    const TileRec b = base_rec(c, parity_off, kind);
+    const int tw = kind == 0 ? kTileX : fused2_tile_w(c->storage);
     for (int z0 = 0; z0 < c->nz; z0 += zlen)
         for (int y0 = 0; y0 < c->ny; y0 += tile_y)
-            for (int x0 = 0; x0 < c->nx; x0 += kTileX) {
+            for (int x0 = 0; x0 < c->nx; x0 += tw) {
                 TileRec t = b;
                 t.x0 = x0;
                 t.y0 = y0;
                 t.kz0 = z0;
                 t.kz1 = std::min(c->nz, z0 + zlen);
+                t.id_x0 = (x0 - 2) & ~15;   // two-step kernel: 16-byte aligned origin of the id box
                 v.push_back(t);
             }
 }
 
-int build_tiles(fdtd_ctx *c) {
-    Shape s = resolve_shape(c->storage, c->tuning);
-    if (c->tiles_ty == s.tile_y && c->d_tiles && c->grid) return FDTD_OK;
-    int rc = encode_maps(c, s.tile_y);
+int build_tiles(fdtd_ctx *c, int kind) {
+    Shape s = resolve_shape(c->storage, c->tuning, kind);
+    fdtd_ctx::TileList &tl = c->tl[kind];
+    if (tl.key == s.tile_y && tl.d && tl.grid) return FDTD_OK;
+    int rc = encode_maps(c, kind, s.tile_y + (kind == 0 ? 2 : 4));
     if (rc) return rc;
     const int G = num_sms() * s.ctas_per_sm;
-    const long long cols = (long long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + s.tile_y - 1) / s.tile_y);
-    const int zlen = choose_zlen(cols, c->nz, G, c->tuning.zchunk);
+    const int tw = kind == 0 ? kTileX : fused2_tile_w(c->storage);
+    const long long cols = (long long)((c->nx + tw - 1) / tw) * ((c->ny + s.tile_y - 1) / s.tile_y);
+    const int zlen = choose_zlen(cols, c->nz, G, c->tuning.zchunk, kind == 0 ? 1 : 3);
     std::vector<TileRec> v;
-    append_tiles(v, c, 0, s.tile_y, zlen);
-    pool_free(c->d_tiles, c->stream);
-    c->d_tiles = nullptr;
-    CK(c, pool_alloc((void **)&c->d_tiles, sizeof(TileRec) * v.size(), c->stream));
-    CK(c, cudaMemcpyAsync(c->d_tiles, v.data(), sizeof(TileRec) * v.size(), cudaMemcpyHostToDevice, c->stream));
+    append_tiles(v, c, 0, s.tile_y, zlen, kind);
+    pool_free(tl.d, c->stream);
+    tl.d = nullptr;
+    CK(c, pool_alloc((void **)&tl.d, sizeof(TileRec) * v.size(), c->stream));
+    CK(c, cudaMemcpyAsync(tl.d, v.data(), sizeof(TileRec) * v.size(), cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    c->ntiles = (int)v.size();
-    c->grid = std::min<int>(c->ntiles, G);
-    c->tiles_ty = s.tile_y;
+    tl.n = (int)v.size();
+    tl.grid = std::min<int>(tl.n, G);
+    tl.key = s.tile_y;
     return FDTD_OK;
 }
 
@@ -377,23 +401,29 @@ bool use_fused(const fdtd_ctx *c) {
     return c->coef_mode != COEF_FULL && c->tuning.kernel != FDTD_KERNEL_SIMPLE;
 }
 
-// One step of a single context (no graph).
-int launch_one(fdtd_ctx *c, int parity, int inject_us) {
+bool use_temporal(const fdtd_ctx *c) { return use_fused(c) && c->tuning.kernel == FDTD_KERNEL_TEMPORAL; }
+
+// One launch of a single context (no graph): kind 0 advances one step, kind 1 two steps.
+int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind = 0) {
     if (!use_fused(c)) {
         CK(c, launch_simple_step(c->storage, make_desc(c, 0), c->cur, c->stream));
         return FDTD_OK;
     }
-    Shape s = resolve_shape(c->storage, c->tuning);
+    Shape s = resolve_shape(c->storage, c->tuning, kind);
+    const fdtd_ctx::TileList &tl = c->tl[kind];
     FusedLaunch L{};
-    L.recs = c->d_tiles;
-    L.ntiles = c->ntiles;
+    L.recs = tl.d;
+    L.ntiles = tl.n;
     L.parity = parity;
     L.status = c->d_status;
     L.tile_y = s.tile_y;
     L.stages = s.stages;
-    L.grid = c->grid;
+    L.grid = tl.grid;
     L.inject_timeout_us = inject_us;
-    CK(c, launch_fused_step(c->storage, L, c->stream));
+    if (kind == 0)
+        CK(c, launch_fused_step(c->storage, L, c->stream));
+    else
+        CK(c, launch_fused2_step(c->storage, L, c->stream));
     return FDTD_OK;
 }
 
@@ -668,7 +698,7 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
     if ((e = dmalloc(c, (void **)&c->d_partial, sizeof(double) * 3 * nb)) != cudaSuccess) return cfail("alloc", e);
     if ((e = dmalloc(c, (void **)&c->d_out, sizeof(double) * 3)) != cudaSuccess) return cfail("alloc", e);
     if ((e = dmalloc(c, (void **)&c->d_max, sizeof(unsigned) * 6)) != cudaSuccess) return cfail("alloc", e);
-    if ((e = dmalloc(c, (void **)&c->d_maps, sizeof(CUtensorMap) * kMapsPerCavity)) != cudaSuccess)
+    if ((e = dmalloc(c, (void **)&c->d_maps, sizeof(CUtensorMap) * kMapsPerCavity * kMapSets)) != cudaSuccess)
         return cfail("alloc", e);
     if ((e = dmalloc(c, (void **)&c->d_desc, sizeof(CavityDesc))) != cudaSuccess) return cfail("alloc", e);
     if (int rc = upload_desc(c)) {
@@ -695,7 +725,8 @@ void fdtd_destroy(fdtd_ctx *c) {
     for (int a = 0; a < 6; ++a) pool_free(c->coef_full[a], st);
     for (void *p : {(void *)c->id, (void *)c->table, (void *)c->inv_table, (void *)c->table_fused,
                     (void *)c->d_status, (void *)c->d_partial, (void *)c->d_out, (void *)c->d_stage,
-                    (void *)c->d_max, (void *)c->d_maps, (void *)c->d_desc, (void *)c->d_tiles})
+                    (void *)c->d_max, (void *)c->d_maps, (void *)c->d_desc, (void *)c->tl[0].d,
+                    (void *)c->tl[1].d})
         pool_free(p, st);
     cudaStreamSynchronize(st);
     delete c;
@@ -708,13 +739,14 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
     if (!c) return FDTD_ERR_ARG;
     fdtd_tuning n{};
     if (t) n = *t;
-    if (n.kernel < 0 || n.kernel > FDTD_KERNEL_FUSED) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
-    if (n.tile_y && n.tile_y != 4 && n.tile_y != 8 && n.tile_y != 16)
-        return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16");
+    if (n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
+    if (n.kernel == FDTD_KERNEL_TEMPORAL ? (n.tile_y && n.tile_y != 8 && n.tile_y != 12)
+                                         : (n.tile_y && n.tile_y != 4 && n.tile_y != 8 && n.tile_y != 16))
+        return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (8 or 12 for the two-step kernel)");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return fail(c, FDTD_ERR_ARG, "stages must be in [3, 8]");
     if (n.zchunk < 0 || n.ctas_per_sm < 0) return fail(c, FDTD_ERR_ARG, "negative tuning value");
     c->tuning = n;
-    c->tiles_ty = 0;   // force a tile rebuild
+    c->tl[0].key = c->tl[1].key = 0;   // force tile rebuilds
     cudaStreamSynchronize(c->stream);   // no graph of this context may still be running
     drop_graphs(c->graphs);
     return FDTD_OK;
@@ -765,7 +797,7 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
             CK(c, cudaMemcpyAsync(c->table_fused, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, c->stream));
             CK(c, cudaStreamSynchronize(c->stream));
         }
-        c->tiles_ty = 0;   // tile records embed the folded coefficients: rebuild them
+        c->tl[0].key = c->tl[1].key = 0;   // tile records embed the folded coefficients: rebuild them
         cudaStreamSynchronize(c->stream);
         drop_graphs(c->graphs);
     }
@@ -810,11 +842,14 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
     if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
     if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; step the batch");
     if (nsteps == 0) return FDTD_OK;
-    if (use_fused(c)) {
-        if (int rc = build_tiles(c)) return rc;
-    }
+    const bool fused = use_fused(c);
+    const bool temporal = use_temporal(c);
+    if (fused)
+        if (int rc = build_tiles(c, 0)) return rc;
+    if (temporal)
+        if (int rc = build_tiles(c, 1)) return rc;
     int left = nsteps;
-    if (c->inject_us > 0 && use_fused(c)) {
+    if (c->inject_us > 0 && fused) {
         const int inj = c->inject_us;
         c->inject_us = 0;
         if (int rc = launch_one(c, c->cur, inj)) return rc;
@@ -822,16 +857,19 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
         ++c->steps;
         --left;
     }
-    const bool fused = use_fused(c);
-    const int K = 16;
+    // kind 1 advances two steps per launch; either kind reads copy cur and writes copy 1 - cur.
+    // An odd remainder takes one launch of the one-step kernel at the end.
+    const int kind = temporal ? 1 : 0;
+    const int per = temporal ? 2 : 1;
+    const int K = 16;   // steps per graph
     if (c->tuning.use_graph && fused && c->stream != nullptr && left >= K) {
-        GraphKey key{K, c->cur};
+        GraphKey key{K, c->cur, kind};
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             cudaGraph_t g;
             CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             int rc = FDTD_OK;
-            for (int s = 0; s < K && !rc; ++s) rc = launch_one(c, c->cur ^ (s & 1), 0);
+            for (int s = 0; s < K / per && !rc; ++s) rc = launch_one(c, c->cur ^ (s & 1), 0, kind);
             cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
             if (rc) return rc;
             CK(c, ee);
@@ -843,9 +881,15 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
         while (left >= K) {
             CK(c, cudaGraphLaunch(it->second, c->stream));
             left -= K;
-            c->steps += K;   // K even: parity unchanged
+            c->steps += K;   // an even number of launches: parity unchanged
         }
     }
+    if (temporal)
+        for (; left >= 2; left -= 2) {
+            if (int rc = launch_one(c, c->cur, 0, 1)) return rc;
+            c->cur ^= 1;
+            c->steps += 2;
+        }
     for (; left > 0; --left) {
         if (int rc = launch_one(c, c->cur, 0)) return rc;
         if (fused) c->cur ^= 1;
@@ -978,7 +1022,8 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t) {
     if (!b) return FDTD_ERR_ARG;
     fdtd_tuning n{};
     if (t) n = *t;
-    if (n.kernel == FDTD_KERNEL_SIMPLE) return bfail(b, FDTD_ERR_ARG, "batches use the fused kernel");
+    if (n.kernel != FDTD_KERNEL_AUTO && n.kernel != FDTD_KERNEL_FUSED)
+        return bfail(b, FDTD_ERR_ARG, "batches use the one-step fused kernel");
     if (n.tile_y && n.tile_y != 4 && n.tile_y != 8 && n.tile_y != 16) return bfail(b, FDTD_ERR_ARG, "bad tile_y");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return bfail(b, FDTD_ERR_ARG, "bad stages");
     b->tuning = n;
@@ -1006,14 +1051,14 @@ static int batch_rebuild(fdtd_batch *b) {
     std::vector<TileRec> tiles;
     long long total_cols_planes = 0;
     for (auto &mb : b->members)
-        if (mb.stop > b->step && mb.c->maps_ty != 0 && mb.c->maps_ty != s.tile_y) {
+        if (mb.stop > b->step && mb.c->maps_by[0] != 0 && mb.c->maps_by[0] != s.tile_y + 2) {
             cudaStreamSynchronize(b->stream);   // launches in flight may still read the old maps
             break;
         }
     for (auto &mb : b->members) {
         if (mb.stop <= b->step) continue;   // finished members carry no tiles
         fdtd_ctx *c = mb.c;
-        if (int rc = encode_maps(c, s.tile_y)) return bfail(b, rc, "member: %s", c->err.c_str());
+        if (int rc = encode_maps(c, 0, s.tile_y + 2)) return bfail(b, rc, "member: %s", c->err.c_str());
         total_cols_planes += (long long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + s.tile_y - 1) / s.tile_y) * c->nz;
     }
     // one z-length for all members so tiles carry similar work; about 8 tiles per CTA

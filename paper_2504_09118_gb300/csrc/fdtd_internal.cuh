@@ -28,6 +28,7 @@ constexpr int kNumFields = 6;      // Ex, Ey, Ez, Hx, Hy, Hz
 constexpr int kMaxTable = 256;
 constexpr int kTileX = 64;         // fused kernel tile width along x (cells)
 constexpr int kMapsPerCavity = 13; // [parity 0: 6 fields][parity 1: 6 fields][id]
+constexpr int kMapSets = 2;        // one set for the one-step kernel's boxes, one for the two-step kernel's
 
 template <typename T> struct Storage;
 template <> struct Storage<float> {
@@ -125,7 +126,9 @@ struct alignas(16) TileRec {
     void *dst[2][6];             // both copies of the six active arrays
     long long stop;              // batch launch index from which this tile is skipped (member finished)
     int ntab;                    // COEF_ID8: table entries
-    int pad[15];
+    int nz;
+    int id_x0;                   // two-step kernel: x origin of the id box (a multiple of 16)
+    int pad[13];
 };
 static_assert(sizeof(TileRec) == 256, "TileRec must be 256 bytes");
 

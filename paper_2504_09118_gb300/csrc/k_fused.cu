@@ -36,11 +36,14 @@
 // wait returns at once; the consumers leave together at the next tile start
 // (an OR-reducing barrier) after latching STATUS_TIMEOUT, and the producer
 // stops issuing, drains its in-flight copies (bounded again) and exits.
+#include "fused_common.cuh"
 #include "launch.h"
 
 namespace fdtd {
 
 namespace {
+
+using namespace fused;
 
 #ifndef FDTD_PRODUCER_SLEEP_NS
 #define FDTD_PRODUCER_SLEEP_NS 0   // back-off of the producer warp between polls of a full ring slot
@@ -101,57 +104,6 @@ template <int TY>
 __host__ __device__ constexpr int block_threads() {
     return (TY + 2) * 32;
 }
-
-// a - b for two packed floats in one instruction: fma(b, -1, a) rounds exactly like a - b.
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Named barrier over `nthreads` threads that also ORs a predicate across them.
-__device__ __forceinline__ bool bar_sync_or(int id, int nthreads, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "barrier.cta.red.or.pred p, %2, %3, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
-        : "memory");
-    return r != 0;
-}
-
-// Two adjacent storage elements <-> two floats.  16-bit storage holds E scaled by s_E and
-// H scaled by s_H; the kernel computes in those scaled units (the ratio s_E/s_H is folded
-// into the coefficients of its tile records), so loads and stores are plain conversions.
-template <typename T> struct Pair;
-template <> struct Pair<float> {
-    __device__ __forceinline__ static float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
-    __device__ __forceinline__ static float ld1(const float *p) { return *p; }
-    __device__ __forceinline__ static void st(float *p, float a, float b) {
-        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
-    }
-};
-template <> struct Pair<__half> {
-    __device__ __forceinline__ static float2 ld(const __half *p) {
-        return __half22float2(*reinterpret_cast<const __half2 *>(p));
-    }
-    __device__ __forceinline__ static float ld1(const __half *p) { return __half2float(*p); }
-    __device__ __forceinline__ static void st(__half *p, float a, float b) {
-        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
-    }
-};
-template <> struct Pair<__nv_bfloat16> {
-    __device__ __forceinline__ static float2 ld(const __nv_bfloat16 *p) {
-        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
-    }
-    __device__ __forceinline__ static float ld1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-    __device__ __forceinline__ static void st(__nv_bfloat16 *p, float a, float b) {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
-    }
-};
 
 template <typename T, int TY>
 __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_step_kernel(const FusedParams P) {

@@ -1,0 +1,437 @@
+// Two Yee leapfrog steps per pass over HBM (temporal blocking, T = 2) for sm_103a.
+//
+// Same update as k_fused.cu (Eq. 2 of the paper in the order of Listing 1, PEC by
+// index predicates), applied twice per launch: level 1 takes (H^{n-1/2}, E^n) to
+// (H^{n+1/2}, E^{n+1}) and level 2 takes that to (H^{n+3/2}, E^{n+2}); only level 2
+// is written to HBM (copy 1-s), so a step costs half the DRAM bytes of the one-step
+// kernel at the price of recomputing a wider halo.
+//
+// Tile: W = 64 - HX output columns (60 FP32, 56 16-bit: keeps the TMA x origin x0 - HX
+// on a 16-byte boundary) x TY output rows, over planes [kz0, kz1).  Consumer warps
+// r = 0..TY+2 own rows y = y0 - 2 + r; each lane owns the two cells x0 - 2 + 2 lane,
+// +1, so the lanes cover [x0 - 2, x0 + 62) at both levels:
+//   level 1  H1 rows y0-2 .. y0+TY,   E1 rows y0-1 .. y0+TY    (from units k, k+1)
+//   level 2  H2 rows y0-1 .. y0+TY-1, E2 rows y0 .. y0+TY-1    (one plane behind)
+// which is exactly what the outputs need (a stored value never depends on a lane's
+// unused edge cells).  E1 outside the cavity is forced to 0: at i = nx, j = ny or k = nz
+// it is tangential to a PEC face.  x neighbours come from lane shuffles, y neighbours
+// from small shared planes (H1 and H2: Hx, Hz of the row above; E1: Ex, Ez of the row
+// below, double-buffered in z); z neighbours stay in registers.
+//
+// Per z-plane iteration j: [H1(j)] bar [E1(j)] bar [H2(j-1)] bar [E2(j-1) + stores], the
+// last phase running into the next plane's H1 (they share no data).  A producer warp
+// streams plane units (six field boxes with a 2-cell halo in y, id box) through an
+// S-slot TMA ring exactly as the one-step kernel does; waits are bounded and a shared
+// abort flag ends the CTA together (see k_fused.cu).
+#include "fused_common.cuh"
+#include "launch.h"
+
+namespace fdtd {
+
+namespace {
+
+using namespace fused;
+
+constexpr int NTR2 = 8;
+constexpr uint64_t kWaitLimitNs2 = 2000000000ull;
+
+template <typename T> struct Geom2 {
+    static constexpr int HX = 16 / (int)sizeof(T);   // 4 (FP32) or 8 (16-bit)
+    static constexpr int W = 64 - HX;                 // output columns per tile
+    static constexpr int BX = 64 + 2 * HX;            // field box width
+    static constexpr int IBX = 80;                    // id box width (bytes)
+};
+
+struct Fused2Params {
+    const TileRec *recs;
+    int ntiles;
+    int parity;
+    int *status;
+    int stages;
+    int slot_bytes;
+};
+
+__host__ __device__ constexpr int al(int v, int a) { return (v + a - 1) / a * a; }
+
+template <typename T, int TY> __host__ __device__ constexpr int box_bytes() {
+    return Geom2<T>::BX * (TY + 4) * (int)sizeof(T);
+}
+template <typename T, int TY> __host__ __device__ constexpr int box_stride() { return al(box_bytes<T, TY>(), 128); }
+template <int TY> __host__ __device__ constexpr int idbox_bytes() { return Geom2<float>::IBX * (TY + 4); }
+template <typename T, int TY> __host__ __device__ constexpr int slot2_bytes() {
+    return al(6 * box_stride<T, TY>() + idbox_bytes<TY>(), 128);
+}
+constexpr int PW = 68;   // shared plane row pitch: column x - x0 + 4 (lane cells at 2 lane + 2, + 3)
+template <int TY> __host__ __device__ constexpr int PR() { return TY + 5; }   // rows: r + 1 for r in -1 .. TY+3
+template <int TY> __host__ __device__ constexpr int plane_floats() { return PR<TY>() * PW; }
+constexpr int TAB2_BYTES = kMaxTable * 2 * 16;
+template <typename T, int TY> __host__ __device__ constexpr int smem2_bytes(int stages) {
+    // barriers/abort | records | table | H1 (Hx,Hz) | H2 (Hx,Hz) | E1 (Ex,Ez) x 2 | ring
+    return 256 + NTR2 * (int)sizeof(TileRec) + TAB2_BYTES + al(8 * plane_floats<TY>() * 4, 128) +
+           stages * slot2_bytes<T, TY>();
+}
+template <int TY> __host__ __device__ constexpr int threads2() { return (TY + 4) * 32; }
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fused2Params P) {
+    using G = Geom2<T>;
+    constexpr int HX = G::HX, BX = G::BX, W = G::W;
+    constexpr int FB = box_bytes<T, TY>(), FS = box_stride<T, TY>(), FE = FS / (int)sizeof(T);
+    constexpr int NCW = TY + 3, NCT = NCW * 32;
+    constexpr int PF = plane_floats<TY>();
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (smem_u32(smem) & 127u) {
+        if (threadIdx.x == 0) atomicOr(P.status, STATUS_BADINDEX);
+        return;
+    }
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + 8;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 128);
+    TileRec *recs = reinterpret_cast<TileRec *>(smem + 256);
+    float4 *stab = reinterpret_cast<float4 *>(smem + 256 + NTR2 * sizeof(TileRec));
+    float *planes = reinterpret_cast<float *>(smem + 256 + NTR2 * sizeof(TileRec) + TAB2_BYTES);
+    float *sh1x = planes, *sh1z = planes + PF, *sh2x = planes + 2 * PF, *sh2z = planes + 3 * PF;
+    float *e1b = planes + 4 * PF;   // [buffer][Ex, Ez][PF]
+    unsigned char *slots = smem + 256 + NTR2 * sizeof(TileRec) + TAB2_BYTES + al(8 * PF * 4, 128);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = P.stages, SB = P.slot_bytes;
+
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        fence_mbarrier_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+
+    // =========================================================== producer warp
+    if (warp == NCW) {
+        int issued = 0, m = 0, s = 0;
+        uint32_t rnd = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+            TileRec *rec = &recs[m++ % NTR2];
+            int kb = 0, klast = 0;
+            for (int k = 0;; ++k) {
+                if (issued >= S) {
+                    const bool w = mbar_wait_abortable(&empty[s], rnd ^ 1u, kWaitLimitNs2, abort_flag, 0);
+                    if (!__all_sync(0xffffffffu, w)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                if (__any_sync(0xffffffffu, *abort_flag != 0)) {
+                    ok = false;
+                    break;
+                }
+                if (k == 0) {
+                    const uint32_t *src = reinterpret_cast<const uint32_t *>(P.recs + t);
+                    uint32_t *dst = reinterpret_cast<uint32_t *>(rec);
+                    for (int q = lane; q < (int)(sizeof(TileRec) / 4); q += 32) dst[q] = __ldg(src + q);
+                    __syncwarp();
+                    kb = rec->kz0 > 2 ? rec->kz0 - 2 : 0;
+                    klast = rec->kz1 + 1;
+                }
+                const int kk = kb + k;
+                if (lane == 0) {
+                    const int src_copy = P.parity ^ rec->parity_off;
+                    const bool has_id = rec->mode == COEF_ID8;
+                    unsigned char *dst = slots + s * SB;
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? idbox_bytes<TY>() : 0));
+                    const CUtensorMap *mp = rec->maps + src_copy * 6;
+#pragma unroll
+                    for (int f = 0; f < 6; ++f)
+                        tma_load_3d(dst + f * FS, mp + f, rec->x0 - HX, rec->y0 - 2, kk, &full[s]);
+                    if (has_id) tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
+                }
+                __syncwarp();
+                ++issued;
+                if (++s == S) {
+                    s = 0;
+                    rnd ^= 1u;
+                }
+                if (kk >= klast) break;
+            }
+        }
+        if (!ok && lane == 0) {
+            atomicOr(P.status, STATUS_TIMEOUT);
+            for (int u = issued > S ? issued - S : 0; u < issued; ++u)
+                mbar_wait_bounded(&full[u % S], (u / S) & 1, kWaitLimitNs2);
+        }
+        return;
+    }
+
+    // =========================================================== consumer warps
+    const int r = warp;                      // row warp: y = y0 - 2 + r
+    const int bx = HX - 2 + 2 * lane;        // box column of the lane's first cell
+    const int by = r;                        // box row
+    const int pc = 2 * lane + 2;             // shared plane column of the first cell
+    const int pr = r + 1;                    // shared plane row
+    int sa = 0, m = 0;
+    uint32_t pa = 0;
+    const float4 *tab_cached = nullptr;
+    auto wait_full = [&](int slot, uint32_t par) {
+        return mbar_wait_abortable(&full[slot], par, kWaitLimitNs2, abort_flag, 0);
+    };
+    const float2 zero2 = make_float2(0.f, 0.f);
+
+    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+        bool ok = wait_full(sa, pa);
+        if (bar_sync_or(2, NCT, !ok || *abort_flag != 0)) {
+            if (threadIdx.x == 0) atomicOr(P.status, STATUS_TIMEOUT);
+            return;
+        }
+        const TileRec *rec = &recs[m++ % NTR2];
+        const int x0 = rec->x0, y0 = rec->y0, kz0 = rec->kz0, kz1 = rec->kz1;
+        const int nx = rec->nx, ny = rec->ny, nz = rec->nz;
+        const long long pitch = rec->pitch, plane = rec->plane;
+        const bool id_mode = rec->mode == COEF_ID8;
+        const bool ch_uni = rec->ch_uniform != 0;
+        const int idoff = x0 - 2 - rec->id_x0;   // lane cells start this many bytes into the id box
+        if (id_mode && rec->table != tab_cached) {
+            const float4 *src = rec->table;
+            const int n = 2 * rec->ntab;
+            for (int e = threadIdx.x; e < n; e += NCT) stab[e] = __ldg(src + e);
+            bar_sync_or(2, NCT, false);
+            tab_cached = src;
+        }
+        const int dstc = (P.parity ^ rec->parity_off) ^ 1;
+        T *dst[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) dst[f] = static_cast<T *>(rec->dst[dstc][f]);
+        const float4 ce_s = make_float4(rec->ce[0], rec->ce[1], rec->ce[2], 0.f);
+        const float4 ch_s = make_float4(rec->ch[0], rec->ch[1], rec->ch[2], 0.f);
+        const int gj = y0 - 2 + r;
+        const int gi = x0 - 2 + 2 * lane;       // first cell; second is gi + 1
+        const bool rowin = gj >= 0 && gj < ny;
+        const bool ina = gi >= 0 && gi < nx, inb = gi + 1 < nx;   // gi + 1 >= 0 always for gi >= -2
+        const bool out_row = r >= 2 && r < TY + 2 && gj < ny;      // level-2 outputs of this row are stored
+        const bool out_a = lane >= 1 && 2 * lane - 2 < W && gi < nx; // both cells share the column window
+        const int kb = kz0 > 2 ? kz0 - 2 : 0;
+
+        auto at = [&](const T *base, int f, int xx, int yy) { return base + f * FE + yy * BX + xx; };
+        auto coef = [&](uint32_t ip, int which, float4 &a, float4 &b) {   // which: 0 ce, 1 ch
+            if (id_mode && !(which && ch_uni)) {
+                a = stab[2 * (ip & 0xff) + which];
+                b = stab[2 * (ip >> 8) + which];
+            } else {
+                a = b = which ? ch_s : ce_s;
+            }
+        };
+        float2 h1px = zero2, h1py = zero2, h1pz = zero2;   // H1(j-1) of own cells
+        float2 e1px = zero2, e1py = zero2, e1pz = zero2;   // E1(j-1)
+        float2 h2px = zero2, h2py = zero2;                 // H2(j-2) (Hx, Hy)
+        uint32_t idprev = 0;                               // material ids of plane j-1
+
+        for (int k = kb; k <= kz1; ++k) {
+            int sb = sa + 1;
+            uint32_t pb = pa;
+            if (sb == S) {
+                sb = 0;
+                pb ^= 1u;
+            }
+            ok = wait_full(sa, pa) && wait_full(sb, pb);
+            ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the phases below shuffle across lanes
+            const T *A = reinterpret_cast<const T *>(slots + sa * SB);
+            const T *B = reinterpret_cast<const T *>(slots + sb * SB);
+            const uint8_t *ida = slots + sa * SB + 6 * FS;
+            // H2(k-1) needs plane k-1 >= 0 (its inputs at plane -1 were never written)
+            const bool do_e1 = k >= kz0 - 1, do_h2 = k >= kz0 && k >= 1, do_e2 = k >= kz0 + 1;
+            float *e1cur = e1b + (k & 1) * 2 * PF, *e1prv = e1b + ((k + 1) & 1) * 2 * PF;
+
+            // ---------------- phase 1: H1(k) on the lane's two cells
+            float2 e0x = zero2, e0y = zero2, e0z = zero2, h1x_ = zero2, h1y_ = zero2, h1z_ = zero2;
+            uint32_t idpair = 0;
+            if (ok) {
+                e0x = Pair<T>::ld(at(A, 0, bx, by));
+                e0y = Pair<T>::ld(at(A, 1, bx, by));
+                e0z = Pair<T>::ld(at(A, 2, bx, by));
+                const float2 ex_y1 = Pair<T>::ld(at(A, 0, bx, by + 1));
+                const float2 ez_y1 = Pair<T>::ld(at(A, 2, bx, by + 1));
+                const float ey_x2 = Pair<T>::ld1(at(A, 1, bx + 2, by));
+                const float ez_x2 = Pair<T>::ld1(at(A, 2, bx + 2, by));
+                const float2 exb = Pair<T>::ld(at(B, 0, bx, by));
+                const float2 eyb = Pair<T>::ld(at(B, 1, bx, by));
+                h1x_ = Pair<T>::ld(at(A, 3, bx, by));
+                h1y_ = Pair<T>::ld(at(A, 4, bx, by));
+                h1z_ = Pair<T>::ld(at(A, 5, bx, by));
+                if (id_mode) idpair = ida[by * G::IBX + idoff + 2 * lane] | (ida[by * G::IBX + idoff + 2 * lane + 1] << 8);
+                float4 ca, cb;
+                coef(idpair, 1, ca, cb);
+                const float2 ez_x1 = make_float2(e0z.y, ez_x2), ey_x1 = make_float2(e0y.y, ey_x2);
+                h1x_ = __ffma2_rn(make_float2(ca.x, cb.x), sub2(sub2(eyb, e0y), sub2(ez_y1, e0z)), h1x_);
+                h1y_ = __ffma2_rn(make_float2(ca.y, cb.y), sub2(sub2(ez_x1, e0z), sub2(exb, e0x)), h1y_);
+                h1z_ = __ffma2_rn(make_float2(ca.z, cb.z), sub2(sub2(ex_y1, e0x), sub2(ey_x1, e0y)), h1z_);
+                *reinterpret_cast<float2 *>(sh1x + pr * PW + pc) = h1x_;
+                *reinterpret_cast<float2 *>(sh1z + pr * PW + pc) = h1z_;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(NCT) : "memory");
+
+            // ---------------- phase 2: E1(k) (zero outside the cavity: tangential at its far faces)
+            float2 e1x = zero2, e1y = zero2, e1z = zero2;
+            if (ok && do_e1 && r >= 1) {
+                const float2 hx_ym = *reinterpret_cast<const float2 *>(sh1x + (pr - 1) * PW + pc);
+                const float2 hz_ym = *reinterpret_cast<const float2 *>(sh1z + (pr - 1) * PW + pc);
+                const float hz_xm = __shfl_up_sync(0xffffffffu, h1z_.y, 1);
+                const float hy_xm = __shfl_up_sync(0xffffffffu, h1y_.y, 1);
+                float4 ca, cb;
+                coef(idpair, 0, ca, cb);
+                const bool inz = k < nz, k1 = k >= 1, j1 = gj >= 1;
+                const bool va = rowin && ina && inz, vb = rowin && inb && inz;
+                const bool i1a = gi >= 1;
+                const float2 cex = make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
+                const float2 cey = make_float2((i1a && k1) ? ca.y : 0.f, k1 ? cb.y : 0.f);
+                const float2 cez = make_float2((i1a && j1) ? ca.z : 0.f, j1 ? cb.z : 0.f);
+                e1x = __ffma2_rn(cex, sub2(sub2(h1z_, hz_ym), sub2(h1y_, h1py)), e0x);
+                e1y = __ffma2_rn(cey, sub2(sub2(h1x_, h1px), sub2(h1z_, make_float2(hz_xm, h1z_.x))), e0y);
+                e1z = __ffma2_rn(cez, sub2(sub2(h1y_, make_float2(hy_xm, h1y_.x)), sub2(h1x_, hx_ym)), e0z);
+                if (!va) { e1x.x = 0.f; e1y.x = 0.f; e1z.x = 0.f; }
+                if (!vb) { e1x.y = 0.f; e1y.y = 0.f; e1z.y = 0.f; }
+                *reinterpret_cast<float2 *>(e1cur + pr * PW + pc) = e1x;
+                *reinterpret_cast<float2 *>(e1cur + PF + pr * PW + pc) = e1z;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(NCT) : "memory");
+
+            // ---------------- phase 3: H2(k-1) = H1(k-1) - ch curl E1 (plane k-1, z+1 from plane k)
+            float2 h2x = zero2, h2y = zero2, h2z = zero2;
+            if (ok && do_h2 && r >= 1 && r <= TY + 1) {
+                const float2 ex_y1 = *reinterpret_cast<const float2 *>(e1prv + (pr + 1) * PW + pc);
+                const float2 ez_y1 = *reinterpret_cast<const float2 *>(e1prv + PF + (pr + 1) * PW + pc);
+                const float ey_x2 = __shfl_down_sync(0xffffffffu, e1py.x, 1);
+                const float ez_x2 = __shfl_down_sync(0xffffffffu, e1pz.x, 1);
+                float4 ca, cb;
+                coef(idprev, 1, ca, cb);
+                const float2 ez_x1 = make_float2(e1pz.y, ez_x2), ey_x1 = make_float2(e1py.y, ey_x2);
+                h2x = __ffma2_rn(make_float2(ca.x, cb.x), sub2(sub2(e1y, e1py), sub2(ez_y1, e1pz)), h1px);
+                h2y = __ffma2_rn(make_float2(ca.y, cb.y), sub2(sub2(ez_x1, e1pz), sub2(e1x, e1px)), h1py);
+                h2z = __ffma2_rn(make_float2(ca.z, cb.z), sub2(sub2(ex_y1, e1px), sub2(ey_x1, e1py)), h1pz);
+                *reinterpret_cast<float2 *>(sh2x + pr * PW + pc) = h2x;
+                *reinterpret_cast<float2 *>(sh2z + pr * PW + pc) = h2z;
+            }
+            // shuffles below are executed by whole warps; every lane takes part
+            const float h2z_xm = __shfl_up_sync(0xffffffffu, h2z.y, 1);
+            const float h2y_xm = __shfl_up_sync(0xffffffffu, h2y.y, 1);
+            asm volatile("bar.sync 1, %0;" ::"r"(NCT) : "memory");
+
+            // ---------------- phase 4: E2(k-1) = E1(k-1) + ce curl H2, and the level-2 stores
+            if (ok && do_e2 && out_row) {
+                const float2 hx_ym = *reinterpret_cast<const float2 *>(sh2x + (pr - 1) * PW + pc);
+                const float2 hz_ym = *reinterpret_cast<const float2 *>(sh2z + (pr - 1) * PW + pc);
+                float4 ca, cb;
+                coef(idprev, 0, ca, cb);
+                const int kk = k - 1;
+                const bool k1 = kk >= 1, j1 = gj >= 1, i1a = gi >= 1;
+                const float2 cex = make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
+                const float2 cey = make_float2((i1a && k1) ? ca.y : 0.f, k1 ? cb.y : 0.f);
+                const float2 cez = make_float2((i1a && j1) ? ca.z : 0.f, j1 ? cb.z : 0.f);
+                const float2 e2x = __ffma2_rn(cex, sub2(sub2(h2z, hz_ym), sub2(h2y, h2py)), e1px);
+                const float2 e2y = __ffma2_rn(cey, sub2(sub2(h2x, h2px), sub2(h2z, make_float2(h2z_xm, h2z.x))), e1py);
+                const float2 e2z = __ffma2_rn(cez, sub2(sub2(h2y, make_float2(h2y_xm, h2y.x)), sub2(h2x, hx_ym)), e1pz);
+                if (out_a) {
+                    const long long g = (long long)kk * plane + (long long)gj * pitch + gi;
+                    Pair<T>::st(dst[0] + g, e2x.x, e2x.y);
+                    Pair<T>::st(dst[1] + g, e2y.x, e2y.y);
+                    Pair<T>::st(dst[2] + g, e2z.x, e2z.y);
+                    Pair<T>::st(dst[3] + g, h2x.x, h2x.y);
+                    Pair<T>::st(dst[4] + g, h2y.x, h2y.y);
+                    Pair<T>::st(dst[5] + g, h2z.x, h2z.y);
+                }
+            }
+            // ---------------- carry the z neighbours to the next plane
+            h2px = h2x;
+            h2py = h2y;
+            h1px = h1x_;
+            h1py = h1y_;
+            h1pz = h1z_;
+            e1px = e1x;
+            e1py = e1y;
+            e1pz = e1z;
+            idprev = idpair;
+            // ---------------- release unit k (and k+1 after the last plane)
+            const bool last = k == kz1;
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[sa]);
+                if (last) mbar_arrive(&empty[sb]);
+            }
+            sa = sb;
+            pa = pb;
+            if (last && ++sa == S) {
+                sa = 0;
+                pa ^= 1u;
+            }
+        }
+    }
+}
+
+template <typename T, int TY>
+cudaError_t launch2_typed(const FusedLaunch &L, cudaStream_t s) {
+    const int smem = smem2_bytes<T, TY>(L.stages);
+    auto kern = fused2_step_kernel<T, TY>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    Fused2Params P;
+    P.recs = L.recs;
+    P.ntiles = L.ntiles;
+    P.parity = L.parity;
+    P.status = L.status;
+    P.stages = L.stages;
+    P.slot_bytes = slot2_bytes<T, TY>();
+    kern<<<L.grid, threads2<TY>(), smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <typename T, int TY>
+cudaError_t occupancy2_typed(int stages, int *n) {
+    const int smem = smem2_bytes<T, TY>(stages);
+    auto kern = fused2_step_kernel<T, TY>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, threads2<TY>(), smem);
+}
+
+#define FDTD_DISPATCH2(storage, tile_y, ...)                                                          \
+    do {                                                                                              \
+        if (storage == 0) {                                                                           \
+            if (tile_y == 8) { using T = float; constexpr int TY = 8; __VA_ARGS__; }                  \
+            else if (tile_y == 12) { using T = float; constexpr int TY = 12; __VA_ARGS__; }           \
+        } else if (storage == 1) {                                                                    \
+            if (tile_y == 8) { using T = __half; constexpr int TY = 8; __VA_ARGS__; }                 \
+            else if (tile_y == 12) { using T = __half; constexpr int TY = 12; __VA_ARGS__; }          \
+        } else if (storage == 2) {                                                                    \
+            if (tile_y == 8) { using T = __nv_bfloat16; constexpr int TY = 8; __VA_ARGS__; }          \
+            else if (tile_y == 12) { using T = __nv_bfloat16; constexpr int TY = 12; __VA_ARGS__; }   \
+        }                                                                                             \
+    } while (0)
+
+}  // namespace
+
+int fused2_tile_w(int storage) { return storage == 0 ? Geom2<float>::W : Geom2<__half>::W; }
+
+int fused2_smem_bytes(int storage, int tile_y, int stages) {
+    int r = -1;
+    FDTD_DISPATCH2(storage, tile_y, r = smem2_bytes<T, TY>(stages));
+    return r;
+}
+
+cudaError_t fused2_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm) {
+    cudaError_t e = cudaErrorInvalidValue;
+    FDTD_DISPATCH2(storage, tile_y, e = occupancy2_typed<T, TY>(stages, ctas_per_sm));
+    return e;
+}
+
+cudaError_t launch_fused2_step(int storage, const FusedLaunch &L, cudaStream_t s) {
+    if (L.ntiles <= 0) return cudaSuccess;
+    if (L.stages < 3 || L.stages > 8) return cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
+    FDTD_DISPATCH2(storage, L.tile_y, e = launch2_typed<T, TY>(L, s));
+    return e;
+}
+
+}  // namespace fdtd

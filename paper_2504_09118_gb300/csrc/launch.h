@@ -38,6 +38,11 @@ cudaError_t fused_occupancy(int storage, int tile_y, int stages, int *ctas_per_s
 cudaError_t launch_fused_step(int storage, const FusedLaunch &L, cudaStream_t s);
 // *counter += 1 on the stream (advances a batch's device launch counter after each step).
 cudaError_t launch_step_counter(long long *counter, cudaStream_t s);
+// Two-step (temporal blocking) kernel: output tile width along x, shared memory, occupancy, launch.
+int fused2_tile_w(int storage);
+int fused2_smem_bytes(int storage, int tile_y, int stages);
+cudaError_t fused2_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
+cudaError_t launch_fused2_step(int storage, const FusedLaunch &L, cudaStream_t s);
 // Box sizes used to encode the tensor maps of the fused kernel.
 void fused_box(int storage, int tile_y, int *box_x, int *box_y, int *halo_x);
 
