@@ -6,8 +6,27 @@
 namespace fdtd {
 namespace fused {
 
-// a - b for two packed floats in one instruction: fma(b, -1, a) rounds exactly like a - b.
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+#ifndef FDTD_SCALAR_MATH
+#define FDTD_SCALAR_MATH 1   // 1: per-element fmaf (measured faster); 0: packed FP32x2 instructions (same rounding)
+#endif
+
+// a * b + c on the two cells of a lane (one rounding per element).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+#if FDTD_SCALAR_MATH
+    return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+#else
+    return __ffma2_rn(a, b, c);
+#endif
+}
+
+// a - b on the two cells of a lane: fma(b, -1, a) rounds exactly like a - b.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+#if FDTD_SCALAR_MATH
+    return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+#else
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+#endif
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");

@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
             float2 cx, cy, cz;
             ch_pair(idu, -1, cx, cy, cz);
             const float2 ey_x1 = make_float2(ey_.y, ey_x2);
-            hx_ = __ffma2_rn(cx, sub2(sub2(eyb, ey_), sub2(ez_y1, ez_)), hx_);
-            hz_ = __ffma2_rn(cz, sub2(sub2(ex_y1, ex_), sub2(ey_x1, ey_)), hz_);
+            hx_ = fma2(cx, sub2(sub2(eyb, ey_), sub2(ez_y1, ez_)), hx_);
+            hz_ = fma2(cz, sub2(sub2(ex_y1, ex_), sub2(ey_x1, ey_)), hz_);
             *reinterpret_cast<float2 *>(hbuf_ + x + 2) = hx_;
             *reinterpret_cast<float2 *>(hbuf_ + 2 * HC + x + 2) = hz_;
         };
@@ -325,9 +325,9 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     // packed over the lane's two cells; operand order makes each bracket -(curl E), so
                     // H + ch * bracket rounds exactly like H - ch * curl E
                     const float2 ez_x1 = make_float2(ez.y, ez_x2), ey_x1 = make_float2(ey.y, ey_x2);
-                    hx = __ffma2_rn(chx, sub2(sub2(eyb, ey), sub2(ez_y1, ez)), hx);
-                    hy = __ffma2_rn(chy, sub2(sub2(ez_x1, ez), sub2(exb, ex)), hy);
-                    hz = __ffma2_rn(chz, sub2(sub2(ex_y1, ex), sub2(ey_x1, ey)), hz);
+                    hx = fma2(chx, sub2(sub2(eyb, ey), sub2(ez_y1, ez)), hx);
+                    hy = fma2(chy, sub2(sub2(ez_x1, ez), sub2(exb, ex)), hy);
+                    hz = fma2(chz, sub2(sub2(ex_y1, ex), sub2(ey_x1, ey)), hz);
                     const int o = by * HP + x + 2;
                     *reinterpret_cast<float2 *>(hn + o) = hx;
                     *reinterpret_cast<float2 *>(hn + HC + o) = hy;
@@ -387,9 +387,9 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     const float2 cey = make_float2((i1 && k1) ? ce_a.y : 0.f, k1 ? ce_b.y : 0.f);
                     const float2 cez = make_float2((i1 && j1) ? ce_a.z : 0.f, j1 ? ce_b.z : 0.f);
                     const float2 hz_xm2 = make_float2(hz_xm, hz.x), hy_xm2 = make_float2(hy_xm, hy.x);
-                    ex = __ffma2_rn(cex, sub2(sub2(hz, hz_ym), sub2(hy, hpy)), ex);
-                    ey = __ffma2_rn(cey, sub2(sub2(hx, hpx), sub2(hz, hz_xm2)), ey);
-                    ez = __ffma2_rn(cez, sub2(sub2(hy, hy_xm2), sub2(hx, hx_ym)), ez);
+                    ex = fma2(cex, sub2(sub2(hz, hz_ym), sub2(hy, hpy)), ex);
+                    ey = fma2(cey, sub2(sub2(hx, hpx), sub2(hz, hz_xm2)), ey);
+                    ez = fma2(cez, sub2(sub2(hy, hy_xm2), sub2(hx, hx_ym)), ez);
                     if (gj < ny && gi < nx) {
                         const long long g = (long long)k * plane + (long long)gj * pitch + gi;
                         Pair<T>::st(dst[0] + g, ex.x, ex.y);

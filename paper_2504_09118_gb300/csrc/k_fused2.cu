@@ -265,9 +265,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 float4 ca, cb;
                 coef(idpair, 1, ca, cb);
                 const float2 ez_x1 = make_float2(e0z.y, ez_x2), ey_x1 = make_float2(e0y.y, ey_x2);
-                h1x_ = __ffma2_rn(make_float2(ca.x, cb.x), sub2(sub2(eyb, e0y), sub2(ez_y1, e0z)), h1x_);
-                h1y_ = __ffma2_rn(make_float2(ca.y, cb.y), sub2(sub2(ez_x1, e0z), sub2(exb, e0x)), h1y_);
-                h1z_ = __ffma2_rn(make_float2(ca.z, cb.z), sub2(sub2(ex_y1, e0x), sub2(ey_x1, e0y)), h1z_);
+                h1x_ = fma2(make_float2(ca.x, cb.x), sub2(sub2(eyb, e0y), sub2(ez_y1, e0z)), h1x_);
+                h1y_ = fma2(make_float2(ca.y, cb.y), sub2(sub2(ez_x1, e0z), sub2(exb, e0x)), h1y_);
+                h1z_ = fma2(make_float2(ca.z, cb.z), sub2(sub2(ex_y1, e0x), sub2(ey_x1, e0y)), h1z_);
                 *reinterpret_cast<float2 *>(sh1x + pr * PW + pc) = h1x_;
                 *reinterpret_cast<float2 *>(sh1z + pr * PW + pc) = h1z_;
             }
@@ -288,9 +288,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 const float2 cex = make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
                 const float2 cey = make_float2((i1a && k1) ? ca.y : 0.f, k1 ? cb.y : 0.f);
                 const float2 cez = make_float2((i1a && j1) ? ca.z : 0.f, j1 ? cb.z : 0.f);
-                e1x = __ffma2_rn(cex, sub2(sub2(h1z_, hz_ym), sub2(h1y_, h1py)), e0x);
-                e1y = __ffma2_rn(cey, sub2(sub2(h1x_, h1px), sub2(h1z_, make_float2(hz_xm, h1z_.x))), e0y);
-                e1z = __ffma2_rn(cez, sub2(sub2(h1y_, make_float2(hy_xm, h1y_.x)), sub2(h1x_, hx_ym)), e0z);
+                e1x = fma2(cex, sub2(sub2(h1z_, hz_ym), sub2(h1y_, h1py)), e0x);
+                e1y = fma2(cey, sub2(sub2(h1x_, h1px), sub2(h1z_, make_float2(hz_xm, h1z_.x))), e0y);
+                e1z = fma2(cez, sub2(sub2(h1y_, make_float2(hy_xm, h1y_.x)), sub2(h1x_, hx_ym)), e0z);
                 if (!va) { e1x.x = 0.f; e1y.x = 0.f; e1z.x = 0.f; }
                 if (!vb) { e1x.y = 0.f; e1y.y = 0.f; e1z.y = 0.f; }
                 *reinterpret_cast<float2 *>(e1cur + pr * PW + pc) = e1x;
@@ -308,9 +308,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 float4 ca, cb;
                 coef(idprev, 1, ca, cb);
                 const float2 ez_x1 = make_float2(e1pz.y, ez_x2), ey_x1 = make_float2(e1py.y, ey_x2);
-                h2x = __ffma2_rn(make_float2(ca.x, cb.x), sub2(sub2(e1y, e1py), sub2(ez_y1, e1pz)), h1px);
-                h2y = __ffma2_rn(make_float2(ca.y, cb.y), sub2(sub2(ez_x1, e1pz), sub2(e1x, e1px)), h1py);
-                h2z = __ffma2_rn(make_float2(ca.z, cb.z), sub2(sub2(ex_y1, e1px), sub2(ey_x1, e1py)), h1pz);
+                h2x = fma2(make_float2(ca.x, cb.x), sub2(sub2(e1y, e1py), sub2(ez_y1, e1pz)), h1px);
+                h2y = fma2(make_float2(ca.y, cb.y), sub2(sub2(ez_x1, e1pz), sub2(e1x, e1px)), h1py);
+                h2z = fma2(make_float2(ca.z, cb.z), sub2(sub2(ex_y1, e1px), sub2(ey_x1, e1py)), h1pz);
                 *reinterpret_cast<float2 *>(sh2x + pr * PW + pc) = h2x;
                 *reinterpret_cast<float2 *>(sh2z + pr * PW + pc) = h2z;
             }
@@ -330,9 +330,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 const float2 cex = make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
                 const float2 cey = make_float2((i1a && k1) ? ca.y : 0.f, k1 ? cb.y : 0.f);
                 const float2 cez = make_float2((i1a && j1) ? ca.z : 0.f, j1 ? cb.z : 0.f);
-                const float2 e2x = __ffma2_rn(cex, sub2(sub2(h2z, hz_ym), sub2(h2y, h2py)), e1px);
-                const float2 e2y = __ffma2_rn(cey, sub2(sub2(h2x, h2px), sub2(h2z, make_float2(h2z_xm, h2z.x))), e1py);
-                const float2 e2z = __ffma2_rn(cez, sub2(sub2(h2y, make_float2(h2y_xm, h2y.x)), sub2(h2x, hx_ym)), e1pz);
+                const float2 e2x = fma2(cex, sub2(sub2(h2z, hz_ym), sub2(h2y, h2py)), e1px);
+                const float2 e2y = fma2(cey, sub2(sub2(h2x, h2px), sub2(h2z, make_float2(h2z_xm, h2z.x))), e1py);
+                const float2 e2z = fma2(cez, sub2(sub2(h2y, make_float2(h2y_xm, h2y.x)), sub2(h2x, hx_ym)), e1pz);
                 if (out_a) {
                     const long long g = (long long)kk * plane + (long long)gj * pitch + gi;
                     Pair<T>::st(dst[0] + g, e2x.x, e2x.y);

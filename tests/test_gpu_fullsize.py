@@ -71,6 +71,24 @@ def test_512_spheres_sampled_parity_and_invariants():
             assert np.all(g[c][ci.tangential_e_mask(name, *n)] == 0.0)
 
 
+def test_512_two_step_equals_one_step_bitwise():
+    """The bench's launch configuration (two-step kernel) against the one-step kernel at full size."""
+    from paper_2504_09118_gb300 import Cavity
+    w = bench.WORKLOADS["single512"]
+    n = w["n"]
+    ce, ch = bench.sphere_coefs(w)
+    f = ci.random_fields(w["field_seed"], *n)
+    out = []
+    for tuning in (dict(kernel=2, tile_y=8, stages=4, use_graph=1), bench.BENCH_TUNING):
+        with Cavity(*n, DT, 1.0, ce, ch) as cav:
+            cav.tune(**tuning)
+            cav.set_fields(f)
+            cav.step(20)
+            out.append(cav.get_fields())
+    for name, x, y in zip(ci.COMPONENTS, *out):
+        assert np.array_equal(x, y), name
+
+
 @pytest.mark.parametrize("storage", [1, 2])
 def test_384_precision_1000_steps(storage):
     from paper_2504_09118_gb300 import Cavity
