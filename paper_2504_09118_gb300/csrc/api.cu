@@ -11,7 +11,9 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <queue>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -87,7 +89,8 @@ struct fdtd_ctx {
     int maps_by[kMapSets] = {0, 0};         // box height each map set was encoded for (0: not yet)
     CavityDesc *d_desc = nullptr;
     struct TileList {
-        TileRec *d = nullptr;
+        TileRec *d = nullptr;   // records, followed by the per-CTA range offsets
+        int *first = nullptr;   // inside the same allocation as d
         int n = 0, grid = 0, key = 0;
     } tl[2];                                // [0] one-step kernel, [1] two-step kernel
     int ch_uniform = 1;
@@ -309,7 +312,8 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0) {
     return s;
 }
 
-// Planes per tile for a cavity given the column count and grid size (load balance vs prologue overhead).
+// Planes per tile for equal tiles dealt round-robin to `grid` CTAs: fewest plane-times on the
+// busiest CTA, counting `prologue_planes` of z-recurrence priming per tile.
 int choose_zlen(long long cols, int nz, int grid, int zchunk, int prologue_planes) {
     if (zchunk > 0) return std::min(zchunk, nz);
     long long best = -1;
@@ -324,6 +328,77 @@ int choose_zlen(long long cols, int nz, int grid, int zchunk, int prologue_plane
         }
     }
     return bestL;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Work split of one cavity over the persistent CTAs (one CTA per SM).  A tile is a column (tile_x x tile_y cells)
+// over a z-chunk of planes and costs (chunk + prologue) plane-times (the prologue planes prime the
+// z recurrence); every plane costs the same.  Tiles are listed chunk-major (all columns of chunk 0,
+// then chunk 1, ...) so that the tiles running at the same time are neighbours and share their
+// halos in L2, and each tile goes to the CTA that becomes free first (greedy list scheduling,
+// computed here).  The chunk plan is the one with the shortest simulated makespan among: n equal
+// chunks (n = 1..64), and n chunks of length L followed by the rest split into 1-4 pieces.
+
+// Makespan of the greedy schedule of `plan` (chunk lengths) over `cols` columns and G CTAs.
+// All tiles of a chunk have one length, so CTAs with equal finish times move together.
+long long simulate_plan(const std::vector<int> &plan, long long cols, int G, int prologue) {
+    std::map<long long, long long> busy;   // finish time -> number of CTAs
+    busy[0] = G;
+    for (int len : plan) {
+        long long m = cols;
+        const long long d = len + prologue;
+        while (m > 0) {
+            auto it = busy.begin();
+            const long long t = it->first, k = std::min(it->second, m);
+            if ((it->second -= k) == 0) busy.erase(it);
+            busy[t + d] += k;
+            m -= k;
+        }
+    }
+    return busy.rbegin()->first;
+}
+
+std::vector<int> plan_chunks(long long cols, int nz, int G, int prologue, int zchunk) {
+    std::vector<int> plan;
+    if (zchunk > 0) {
+        for (int z = 0; z < nz; z += zchunk) plan.push_back(std::min(zchunk, nz - z));
+        return plan;
+    }
+    static std::mutex mu;
+    static std::map<std::tuple<long long, int, int, int>, std::vector<int>> cache;
+    const auto key = std::make_tuple(cols, nz, G, prologue);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    long long best = -1;
+    auto consider = [&](const std::vector<int> &p) {
+        const long long t = simulate_plan(p, cols, G, prologue);
+        if (best < 0 || t < best) {
+            best = t;
+            plan = p;
+        }
+    };
+    for (int n = 1; n <= std::min(nz, 64); ++n) {   // n nearly equal chunks
+        std::vector<int> p;
+        for (int q = 0; q < n; ++q) p.push_back(nz / n + (q < nz % n ? 1 : 0));
+        consider(p);
+    }
+    for (int n = 1; n <= std::min(nz, 64); ++n) {   // n chunks of L = nz / (n + 1) .. nz / n, then a split tail
+        for (int L = std::max(1, nz / (n + 1)); L <= nz / n; ++L) {
+            const int rest = nz - n * L;
+            if (rest <= 0) continue;
+            for (int pieces = 1; pieces <= std::min(4, rest); ++pieces) {
+                std::vector<int> p(n, L);
+                for (int q = 0; q < pieces; ++q) p.push_back(rest / pieces + (q < rest % pieces ? 1 : 0));
+                consider(p);
+            }
+        }
+    }
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = plan;
+    return plan;
 }
 
 TileRec base_rec(const fdtd_ctx *c, int parity_off, int set = 0) {
@@ -352,21 +427,56 @@ TileRec base_rec(const fdtd_ctx *c, int parity_off, int set = 0) {
     return r;
 }
 
-// Tiles of the one-step kernel (kind 0: 64 cells wide) or the two-step kernel (kind 1: W wide).
-void append_tiles(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y, int zlen, int kind = 0) {
+// Tiles of the one-step kernel (kind 0: 64 cells wide) or the two-step kernel (kind 1: W wide),
+// chunk-major over the z-chunks of `plan`.
+void append_tiles_plan(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y,
+                       const std::vector<int> &plan, int kind) {
     const TileRec b = base_rec(c, parity_off, kind);
     const int tw = kind == 0 ? kTileX : fused2_tile_w(c->storage);
-    for (int z0 = 0; z0 < c->nz; z0 += zlen)
+    int z0 = 0;
+    for (int len : plan) {
         for (int y0 = 0; y0 < c->ny; y0 += tile_y)
             for (int x0 = 0; x0 < c->nx; x0 += tw) {
                 TileRec t = b;
                 t.x0 = x0;
                 t.y0 = y0;
                 t.kz0 = z0;
-                t.kz1 = std::min(c->nz, z0 + zlen);
+                t.kz1 = z0 + len;
                 t.id_x0 = (x0 - 2) & ~15;   // two-step kernel: 16-byte aligned origin of the id box
                 v.push_back(t);
             }
+        z0 += len;
+    }
+}
+
+void append_tiles(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y, int zlen, int kind = 0) {
+    std::vector<int> plan;
+    for (int z = 0; z < c->nz; z += zlen) plan.push_back(std::min(zlen, c->nz - z));
+    append_tiles_plan(v, c, parity_off, tile_y, plan, kind);
+}
+
+// Greedy assignment of the listed tiles to G CTAs (each tile to the CTA that frees first, lowest
+// index on ties); returns the tiles regrouped by CTA and, in first, each CTA's range (G + 1 entries).
+std::vector<TileRec> assign_tiles(const std::vector<TileRec> &v, int G, int prologue, std::vector<int> &first) {
+    using Slot = std::pair<long long, int>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> q;
+    for (int b = 0; b < G; ++b) q.push({0, b});
+    std::vector<std::vector<int>> per(G);
+    for (int i = 0; i < (int)v.size(); ++i) {
+        const Slot sl = q.top();
+        q.pop();
+        per[sl.second].push_back(i);
+        q.push({sl.first + (v[i].kz1 - v[i].kz0) + prologue, sl.second});
+    }
+    std::vector<TileRec> out;
+    out.reserve(v.size());
+    first.assign(G + 1, 0);
+    for (int b = 0; b < G; ++b) {
+        first[b] = (int)out.size();
+        for (int i : per[b]) out.push_back(v[i]);
+    }
+    first[G] = (int)out.size();
+    return out;
 }
 
 int build_tiles(fdtd_ctx *c, int kind) {
@@ -375,19 +485,38 @@ int build_tiles(fdtd_ctx *c, int kind) {
     if (tl.key == s.tile_y && tl.d && tl.grid) return FDTD_OK;
     int rc = encode_maps(c, kind, s.tile_y + (kind == 0 ? 2 : 4));
     if (rc) return rc;
-    const int G = num_sms() * s.ctas_per_sm;
     const int tw = kind == 0 ? kTileX : fused2_tile_w(c->storage);
     const long long cols = (long long)((c->nx + tw - 1) / tw) * ((c->ny + s.tile_y - 1) / s.tile_y);
-    const int zlen = choose_zlen(cols, c->nz, G, c->tuning.zchunk, kind == 0 ? 1 : 3);
-    std::vector<TileRec> v;
-    append_tiles(v, c, 0, s.tile_y, zlen, kind);
+    const int prologue = kind == 0 ? 1 : 3;
+    const int G = (int)std::min<long long>((long long)num_sms() * s.ctas_per_sm, cols * c->nz);
+    std::vector<TileRec> listed, v;
+    std::vector<int> first;
+    int grid;
+    if (s.ctas_per_sm == 1) {
+        // one CTA per SM: CTAs run at the same rate, so the greedy schedule is what the SMs see
+        append_tiles_plan(listed, c, 0, s.tile_y, plan_chunks(cols, c->nz, G, prologue, c->tuning.zchunk), kind);
+        grid = (int)std::min<size_t>(listed.size(), (size_t)G);
+        v = assign_tiles(listed, grid, prologue, first);
+    } else {
+        // co-resident CTAs share their SM's issue slots: equal tiles in round-robin waves
+        append_tiles(v, c, 0, s.tile_y, choose_zlen(cols, c->nz, G, c->tuning.zchunk, prologue), kind);
+        grid = (int)std::min<size_t>(v.size(), (size_t)G);
+    }
     pool_free(tl.d, c->stream);
     tl.d = nullptr;
-    CK(c, pool_alloc((void **)&tl.d, sizeof(TileRec) * v.size(), c->stream));
-    CK(c, cudaMemcpyAsync(tl.d, v.data(), sizeof(TileRec) * v.size(), cudaMemcpyHostToDevice, c->stream));
+    // tile records, then the grid + 1 range offsets (16-byte aligned after the 256-byte records)
+    const size_t rec_bytes = sizeof(TileRec) * v.size();
+    CK(c, pool_alloc((void **)&tl.d, rec_bytes + sizeof(int) * first.size(), c->stream));
+    CK(c, cudaMemcpyAsync(tl.d, v.data(), rec_bytes, cudaMemcpyHostToDevice, c->stream));
+    tl.first = nullptr;
+    if (!first.empty()) {
+        tl.first = reinterpret_cast<int *>(reinterpret_cast<char *>(tl.d) + rec_bytes);
+        CK(c, cudaMemcpyAsync(tl.first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice,
+                              c->stream));
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     tl.n = (int)v.size();
-    tl.grid = std::min<int>(tl.n, G);
+    tl.grid = grid;
     tl.key = s.tile_y;
     return FDTD_OK;
 }
@@ -420,6 +549,7 @@ int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind = 0) {
     L.stages = s.stages;
     L.grid = tl.grid;
     L.inject_timeout_us = inject_us;
+    L.first = tl.first;
     if (kind == 0)
         CK(c, launch_fused_step(c->storage, L, c->stream));
     else

@@ -69,6 +69,7 @@ struct FusedParams {
     int stages;
     int slot_bytes;
     int inject_timeout_us;
+    const int *first;   // per-CTA tile ranges (NULL: round-robin)
 };
 
 __host__ __device__ constexpr int align_up(int v, int a) { return (v + a - 1) / a * a; }
@@ -136,6 +137,10 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = P.stages, SB = P.slot_bytes;
     const long long step = P.step ? *P.step : 0;   // launch index within a batch
+    // this CTA's tiles: a host-balanced contiguous range, or every gridDim.x-th tile
+    const int t_begin = P.first ? __ldg(P.first + blockIdx.x) : (int)blockIdx.x;
+    const int t_end = P.first ? __ldg(P.first + blockIdx.x + 1) : P.ntiles;
+    const int t_step = P.first ? 1 : (int)gridDim.x;
     const bool inject = P.inject_timeout_us > 0 && blockIdx.x == 0;
     const uint64_t lim = inject ? (uint64_t)P.inject_timeout_us * 1000ull : kWaitLimitNs;
 
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
         int s = 0;           // slot of the next unit
         uint32_t rnd = 0;    // parity of the ring round of the next unit
         bool ok = true;
-        for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+        for (int t = t_begin; t < t_end && ok; t += t_step) {
             if (__ldg(&P.recs[t].stop) <= step) continue;   // member already took its last step
             TileRec *rec = &recs[m++ % NTR];
             int kb = 0, kz1 = 0;
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
     float2 hpx = make_float2(0.f, 0.f), hpy = make_float2(0.f, 0.f);   // H^{n+1/2}(k-1) of own cells
     auto wait_full = [&](int slot, uint32_t par) { return mbar_wait_abortable(&full[slot], par, lim, abort_flag, 0); };
 
-    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+    for (int t = t_begin; t < t_end; t += t_step) {
         if (__ldg(&P.recs[t].stop) <= step) continue;   // same skip rule as the producer
         bool ok = wait_full(sa, pa);   // the tile record is valid once its first unit has landed
         // every consumer warp is past the previous tile's E phase here; an abort anywhere ends the CTA
@@ -433,6 +438,7 @@ cudaError_t launch_typed(const FusedLaunch &L, cudaStream_t s) {
     P.stages = L.stages;
     P.slot_bytes = slot_bytes<T, TY>();
     P.inject_timeout_us = L.inject_timeout_us;
+    P.first = L.first;
     kern<<<L.grid, block_threads<TY>(), smem, s>>>(P);
     return cudaGetLastError();
 }

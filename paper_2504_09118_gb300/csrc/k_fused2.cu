@@ -49,6 +49,7 @@ struct Fused2Params {
     int *status;
     int stages;
     int slot_bytes;
+    const int *first;   // per-CTA tile ranges (NULL: round-robin)
 };
 
 __host__ __device__ constexpr int al(int v, int a) { return (v + a - 1) / a * a; }
@@ -97,6 +98,10 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = P.stages, SB = P.slot_bytes;
+    // this CTA's tiles: a host-balanced contiguous range, or every gridDim.x-th tile
+    const int t_begin = P.first ? __ldg(P.first + blockIdx.x) : (int)blockIdx.x;
+    const int t_end = P.first ? __ldg(P.first + blockIdx.x + 1) : P.ntiles;
+    const int t_step = P.first ? 1 : (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         *abort_flag = 0;
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         int issued = 0, m = 0, s = 0;
         uint32_t rnd = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+        for (int t = t_begin; t < t_end && ok; t += t_step) {
             TileRec *rec = &recs[m++ % NTR2];
             int kb = 0, klast = 0;
             for (int k = 0;; ++k) {
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
     };
     const float2 zero2 = make_float2(0.f, 0.f);
 
-    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+    for (int t = t_begin; t < t_end; t += t_step) {
         bool ok = wait_full(sa, pa);
         if (bar_sync_or(2, NCT, !ok || *abort_flag != 0)) {
             if (threadIdx.x == 0) atomicOr(P.status, STATUS_TIMEOUT);
@@ -383,6 +388,7 @@ cudaError_t launch2_typed(const FusedLaunch &L, cudaStream_t s) {
     P.status = L.status;
     P.stages = L.stages;
     P.slot_bytes = slot2_bytes<T, TY>();
+    P.first = L.first;
     kern<<<L.grid, threads2<TY>(), smem, s>>>(P);
     return cudaGetLastError();
 }

@@ -31,6 +31,8 @@ struct FusedLaunch {
     int stages;
     int grid;
     int inject_timeout_us;     // >0: do not issue the CTA 0's first unit; wait limit in us
+    const int *first;          // device, grid + 1 entries: CTA b takes tiles [first[b], first[b+1]) in order
+                               // (NULL: CTA b takes tiles b, b + grid, b + 2 grid, ...)
 };
 // Shared memory bytes and max co-resident CTAs per SM for a fused configuration.
 int fused_smem_bytes(int storage, int tile_y, int stages);
