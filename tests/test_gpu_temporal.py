@@ -52,8 +52,9 @@ def assert_bitwise(a, b):
         assert bad.size == 0, (ci.COMPONENTS[n], len(bad), bad[:6].tolist(), float(np.max(np.abs(x - y))))
 
 
+# x extents around the two-step kernel's tile edges (60 cells per tile in FP32)
 @pytest.mark.parametrize("dims", [(4, 4, 4), (7, 9, 11), (130, 67, 45), (1, 3, 2), (64, 8, 3), (61, 13, 1),
-                                  (121, 40, 33), (60, 12, 2), (2, 70, 5)])
+                                  (121, 40, 33), (60, 12, 2), (120, 10, 6), (181, 17, 9), (2, 70, 5)])
 @pytest.mark.parametrize("mat", ["vacuum", "spheres", "few"])
 def test_two_step_equals_one_step_bitwise_f32(dims, mat):
     ce, ch = materials(mat, dims, 5)
@@ -131,8 +132,8 @@ def test_two_step_16bit_vs_oracle(storage):
 
 
 @pytest.mark.parametrize("storage", [1, 2])
-def test_two_step_16bit_independent_of_tiling(storage):
-    dims = (67, 29, 18)
+@pytest.mark.parametrize("dims", [(67, 29, 18), (113, 21, 9), (168, 11, 7)])   # 16-bit x tiles: 56 cells
+def test_two_step_16bit_independent_of_tiling(storage, dims):
     f = ci.random_fields(6, *dims)
     a, *_ = run_gpu(f, dims, steps=12, storage=storage, tuning={"kernel": 3, "tile_y": 8})
     b, *_ = run_gpu(f, dims, steps=12, storage=storage, tuning={"kernel": 3, "tile_y": 12, "zchunk": 5, "stages": 3})
@@ -162,6 +163,7 @@ def test_two_step_pec_and_far_faces(storage):
 def test_two_step_tuning_rejects_bad_tile():
     from paper_2504_09118_gb300 import Cavity, FdtdError
     with Cavity(8, 8, 8, DT, 1.0, None, None, 0) as cav:
-        with pytest.raises(FdtdError):
-            cav.tune(kernel=3, tile_y=16)
+        for bad in (4, 10, 16):
+            with pytest.raises(FdtdError):
+                cav.tune(kernel=3, tile_y=bad)
         cav.tune(kernel=3, tile_y=12)
