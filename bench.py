@@ -60,7 +60,10 @@ ID_BYTES = 1  # material id per cell
 
 # DRAM traffic per fused launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the
 # SHA-256 of the kernel source it was measured on; ignored (reported null) once the source changes.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # ncu, 512^3 bench configuration, mean of three launches (profiles/fused2_step_512cube_f32_launches.md)
+    ("single512", "4fec3f8476d51e75"): 6.84e9,
+}
 
 
 def kernel_source_hash() -> str:
