@@ -152,6 +152,19 @@ FDTD_API int fdtd_sync(fdtd_ctx *ctx);
 /* fdtd_set_tuning - choose the step kernel and its launch shape (NULL = defaults). */
 FDTD_API int fdtd_set_tuning(fdtd_ctx *ctx, const fdtd_tuning *t);
 
+/* fdtd_autotune - choose the step kernel and launch shape by timing candidates on this
+ * context's own state: the one-step kernel with 4, 8, 16-row tiles and the two-step kernel with
+ * 8, 12-row tiles and 4 or 6 ring slots (graphs on).  Each candidate runs trial_steps steps
+ * (rounded up to a multiple of 16; <= 0: 16) after one untimed run of the same length, timed
+ * with CUDA events on the context's stream.  The fields are copied aside first (one extra copy
+ * of the active arrays, freed before return) and restored afterwards, so the state and
+ * fdtd_steps_done are unchanged.  The choice is kept per (nx, ny, nz, storage, coefficient
+ * kind) for the life of the process: a later call for the same shape applies it without
+ * trials.  Contexts with per-position coefficient arrays keep the unfused kernel.  out
+ * (may be NULL) receives the chosen tuning, ms_per_step (may be NULL) its time per step.
+ * Requires fdtd_set_fields; synchronises the stream. */
+FDTD_API int fdtd_autotune(fdtd_ctx *ctx, int trial_steps, fdtd_tuning *out, double *ms_per_step);
+
 /* fdtd_steps_done - steps taken since the last fdtd_set_fields (-1 for a NULL ctx). */
 FDTD_API long long fdtd_steps_done(const fdtd_ctx *ctx);
 
@@ -189,14 +202,26 @@ FDTD_API int fdtd_batch_remove(fdtd_batch *b, fdtd_ctx *ctx);
  * different step counts share launches without stopping the batch for each of them. */
 FDTD_API int fdtd_batch_set_steps(fdtd_batch *b, fdtd_ctx *ctx, long long nsteps);
 
-/* fdtd_batch_steps_done - batch launches enqueued since the batch was created (-1 for NULL). */
+/* fdtd_batch_steps_done - the batch's step clock: steps enqueued since the batch was created
+ * (-1 for NULL).  A member added at clock c with fdtd_batch_set_steps(n) is done at clock c + n. */
 FDTD_API long long fdtd_batch_steps_done(const fdtd_batch *b);
 
-/* fdtd_batch_step - advance every member nsteps steps, asynchronously on the batch stream. */
+/* fdtd_batch_step - advance every member nsteps steps, asynchronously on the batch stream.  With
+ * the TEMPORAL kernel each launch takes two steps; a member with one step left (its own count, or
+ * an odd nsteps) takes it in the same launch and stores its one-step result, so every member's
+ * result is bit-identical to stepping it alone with FP32 storage. */
 FDTD_API int fdtd_batch_step(fdtd_batch *b, int nsteps);
 
-/* fdtd_batch_set_tuning - launch shape for the batch kernel (kernel must be FUSED or AUTO). */
+/* fdtd_batch_set_tuning - launch shape for the batch kernel: FUSED (or AUTO: one step per launch)
+ * or TEMPORAL (two steps per launch); may change between fdtd_batch_step calls. */
 FDTD_API int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t);
+
+/* fdtd_batch_autotune - fdtd_autotune for a batch over its current members: the one-step kernel
+ * with 4, 8, 16-row tiles and the two-step kernel with 8, 12-row tiles, each timed over
+ * trial_steps batch steps (rounded up to a multiple of 16; <= 0: 16) after an untimed run.
+ * Members' fields, step counts and the batch clock are restored afterwards.  Not cached (the
+ * members change).  out / ms_per_step may be NULL.  Synchronises the batch stream. */
+FDTD_API int fdtd_batch_autotune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double *ms_per_step);
 
 /* fdtd_batch_size - number of members (-1 for NULL). */
 FDTD_API int fdtd_batch_size(const fdtd_batch *b);

@@ -30,7 +30,7 @@ EXPORTS = (
     "fdtd_batch_create", "fdtd_batch_add", "fdtd_batch_remove", "fdtd_batch_step", "fdtd_batch_set_tuning",
     "fdtd_batch_size", "fdtd_batch_sync", "fdtd_batch_destroy", "fdtd_batch_last_error",
     "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static", "fdtd_batch_set_steps",
-    "fdtd_batch_steps_done",
+    "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune",
 )
 
 
@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
             L.fdtd_batch_steps_done.restype = ll
             L.fdtd_version.restype = ctypes.c_char_p
             L.fdtd_energy_static.argtypes = [i, i, i, d, d, vp, vp, vp, vp, vp]
+            L.fdtd_autotune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d)]
+            L.fdtd_batch_autotune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d)]
             _LIB = L
         return _LIB
 
@@ -224,6 +226,19 @@ def fdtd_set_tuning(ctx, kernel=0, tile_y=0, zchunk=0, ctas_per_sm=0, stages=0, 
     _check(ctx, lib().fdtd_set_tuning(ctx, ctypes.byref(t)))
 
 
+def _tuning_dict(t) -> dict:
+    return {k: int(getattr(t, k)) for k, _ in fdtd_tuning._fields_}
+
+
+def fdtd_autotune(ctx, trial_steps: int = 16) -> tuple[dict, float]:
+    """Time the candidate launch shapes on the context's state (restored afterwards), keep the
+    fastest; returns (tuning, ms per step)."""
+    t = fdtd_tuning()
+    ms = ctypes.c_double()
+    _check(ctx, lib().fdtd_autotune(ctx, int(trial_steps), ctypes.byref(t), ctypes.byref(ms)))
+    return _tuning_dict(t), float(ms.value)
+
+
 def fdtd_steps_done(ctx) -> int:
     return int(lib().fdtd_steps_done(ctx))
 
@@ -308,6 +323,14 @@ def fdtd_batch_step(b, nsteps: int) -> None:
 def fdtd_batch_set_tuning(b, kernel=0, tile_y=0, zchunk=0, ctas_per_sm=0, stages=0, use_graph=0) -> None:
     t = fdtd_tuning(kernel, tile_y, zchunk, ctas_per_sm, stages, use_graph)
     _bcheck(b, lib().fdtd_batch_set_tuning(b, ctypes.byref(t)))
+
+
+def fdtd_batch_autotune(b, trial_steps: int = 16) -> tuple[dict, float]:
+    """fdtd_autotune over a batch's current members (state and clock restored afterwards)."""
+    t = fdtd_tuning()
+    ms = ctypes.c_double()
+    _bcheck(b, lib().fdtd_batch_autotune(b, int(trial_steps), ctypes.byref(t), ctypes.byref(ms)))
+    return _tuning_dict(t), float(ms.value)
 
 
 def fdtd_batch_set_steps(b, ctx, nsteps: int) -> None:

@@ -43,6 +43,10 @@ class Cavity:
     def tune(self, **kw):
         B.fdtd_set_tuning(self.handle, **kw)
 
+    def autotune(self, trial_steps: int = 16):
+        """Pick the fastest kernel and launch shape on this cavity's state; returns (tuning, ms/step)."""
+        return B.fdtd_autotune(self.handle, trial_steps)
+
     @property
     def steps_done(self):
         return B.fdtd_steps_done(self.handle)

@@ -106,15 +106,18 @@ struct fdtd_batch {
     struct Member {
         fdtd_ctx *c;
         int cur0;               // member's current copy when it joined
-        long long join;         // batch launch index at which it joined
-        long long stop;         // launch index from which it is skipped (LLONG_MAX: no limit)
+        long long join;         // batch step clock at which it joined
+        long long join_launch;  // batch launch count at which it joined
+        long long stop;         // step clock at which it has taken all its steps (LLONG_MAX: no limit)
         long long steps0;       // its step count when it joined
+        long long nlaunch;      // launches it took part in since joining (each flips its copy)
     };
     int storage = 0;
     cudaStream_t stream = nullptr;
     std::vector<Member> members;
-    long long step = 0;              // launches enqueued so far; the next launch has parity step & 1
-    long long *d_step = nullptr;     // device copy of the launch counter (advanced by a kernel per launch)
+    long long step = 0;              // step clock: steps enqueued so far (a two-step launch advances it by 2)
+    long long launches = 0;          // launches enqueued so far; the next launch has parity launches & 1
+    long long *d_step = nullptr;     // device copy of the step clock (advanced by a kernel after each launch)
     fdtd_tuning tuning{};
     TileRec *d_tiles = nullptr;
     int tiles_cap = 0, ntiles = 0, grid = 0;
@@ -882,6 +885,104 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
     return FDTD_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Autotuning: candidates are timed on the caller's own state, which is copied aside and restored.
+namespace {
+
+std::vector<fdtd_tuning> tune_candidates(bool batch) {
+    std::vector<fdtd_tuning> v;
+    for (int ty : {4, 8, 16}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, 4, 1});
+    for (int ty : {8, 12})
+        for (int st : {4, 6}) {
+            if (batch && st != 4) continue;
+            v.push_back(fdtd_tuning{FDTD_KERNEL_TEMPORAL, ty, 0, 0, st, 1});
+        }
+    return v;
+}
+
+int trial_length(int trial_steps) {   // whole 16-step graphs
+    const int n = trial_steps <= 0 ? 16 : trial_steps;
+    return (n + 15) / 16 * 16;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, std::pair<fdtd_tuning, double>> g_tune_cache;
+
+}  // namespace
+
+int fdtd_autotune(fdtd_ctx *c, int trial_steps, fdtd_tuning *out, double *ms_per_step) {
+    if (!c) return FDTD_ERR_ARG;
+    if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; tune the batch");
+    auto report = [&](const fdtd_tuning &t, double ms) {
+        if (out) *out = t;
+        if (ms_per_step) *ms_per_step = ms;
+        return FDTD_OK;
+    };
+    if (c->coef_mode == COEF_FULL) {   // per-position coefficient arrays: only the unfused kernel applies
+        fdtd_tuning t{FDTD_KERNEL_SIMPLE, 0, 0, 0, 0, c->tuning.use_graph};
+        if (int rc = fdtd_set_tuning(c, &t)) return rc;
+        return report(t, -1.0);
+    }
+    const auto key = std::make_tuple(c->nx, c->ny, c->nz, c->storage, c->coef_mode, c->ch_uniform);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            if (int rc = fdtd_set_tuning(c, &it->second.first)) return rc;
+            return report(it->second.first, it->second.second);
+        }
+    }
+    const int n = trial_length(trial_steps);
+    const size_t bytes = (size_t)c->pitch * c->ny * c->nz * esize(c->storage);
+    char *snap = nullptr;
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (pool_alloc((void **)&snap, 6 * bytes, c->stream) != cudaSuccess)
+        return fail(c, FDTD_ERR_OOM, "autotune: no room for a copy of the fields");
+    const int cur0 = c->cur;
+    const long long steps0 = c->steps;
+    for (int f = 0; f < 6; ++f)
+        CK(c, cudaMemcpyAsync(snap + f * bytes, c->fields[cur0][f], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    fdtd_tuning best{};
+    double best_ms = -1.0;
+    int rc = FDTD_OK;
+    for (const fdtd_tuning &t : tune_candidates(false)) {
+        if ((rc = fdtd_set_tuning(c, &t)) != FDTD_OK) break;
+        if ((rc = fdtd_step(c, n)) != FDTD_OK) break;   // untimed: tiles, maps and graphs are built here
+        cudaEventRecord(e0, c->stream);
+        if ((rc = fdtd_step(c, n)) != FDTD_OK) break;
+        cudaEventRecord(e1, c->stream);
+        if ((rc = fdtd_sync(c)) != FDTD_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / n;
+        if (best_ms < 0 || per < best_ms) {
+            best_ms = per;
+            best = t;
+        }
+    }
+    // put the state back whatever happened
+    cudaStreamSynchronize(c->stream);
+    for (int f = 0; f < 6; ++f)
+        cudaMemcpyAsync(c->fields[cur0][f], snap + f * bytes, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    pool_free(snap, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->cur = cur0;
+    c->steps = steps0;
+    if (rc != FDTD_OK) return rc;
+    if (int r2 = fdtd_set_tuning(c, &best)) return r2;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = {best, best_ms};
+    }
+    return report(best, best_ms);
+}
+
 int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
     if (!c || !f) return fail(c, FDTD_ERR_ARG, "NULL argument");
     for (int q = 0; q < 6; ++q)
@@ -1115,7 +1216,7 @@ int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *c) {
     if (c->storage != b->storage) return bfail(b, FDTD_ERR_ARG, "storage mismatch");
     if (c->coef_mode == COEF_FULL) return bfail(b, FDTD_ERR_ARG, "per-position coefficient arrays are not batched");
     // the member's pending work (set_fields) happened-before: its stream was synchronised by that call
-    b->members.push_back({c, c->cur, b->step, LLONG_MAX, c->steps});
+    b->members.push_back({c, c->cur, b->step, b->launches, LLONG_MAX, c->steps, 0});
     c->batch = b;
     b->dirty = true;
     return FDTD_OK;
@@ -1136,7 +1237,7 @@ int fdtd_batch_remove(fdtd_batch *b, fdtd_ctx *c) {
     fdtd_batch::Member *mb = find_member(b, c, &n);
     if (!mb) return bfail(b, FDTD_ERR_ARG, "context is not a member");
     const long long taken = std::min(b->step, mb->stop) - mb->join;
-    c->cur = mb->cur0 ^ (int)(taken & 1);
+    c->cur = mb->cur0 ^ (int)(mb->nlaunch & 1);
     c->steps = mb->steps0 + taken;
     c->batch = nullptr;
     // later work on the member's own stream (read-back, destroy) waits for the batch work enqueued so far
@@ -1152,9 +1253,11 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t) {
     if (!b) return FDTD_ERR_ARG;
     fdtd_tuning n{};
     if (t) n = *t;
-    if (n.kernel != FDTD_KERNEL_AUTO && n.kernel != FDTD_KERNEL_FUSED)
-        return bfail(b, FDTD_ERR_ARG, "batches use the one-step fused kernel");
-    if (n.tile_y && n.tile_y != 4 && n.tile_y != 8 && n.tile_y != 16) return bfail(b, FDTD_ERR_ARG, "bad tile_y");
+    if (n.kernel == FDTD_KERNEL_SIMPLE || n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL)
+        return bfail(b, FDTD_ERR_ARG, "batches use the fused kernels (FUSED or TEMPORAL)");
+    if (n.kernel == FDTD_KERNEL_TEMPORAL ? (n.tile_y && n.tile_y != 8 && n.tile_y != 12)
+                                         : (n.tile_y && n.tile_y != 4 && n.tile_y != 8 && n.tile_y != 16))
+        return bfail(b, FDTD_ERR_ARG, "bad tile_y");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return bfail(b, FDTD_ERR_ARG, "bad stages");
     b->tuning = n;
     b->dirty = true;
@@ -1171,25 +1274,30 @@ static void batch_free_retired_graphs(fdtd_batch *b) {   // call only when the b
     b->retired_graphs.clear();
 }
 
+static int batch_kind(const fdtd_batch *b) { return b->tuning.kernel == FDTD_KERNEL_TEMPORAL ? 1 : 0; }
+
 // Rebuild the packed tile list (asynchronously on the batch stream: the upload runs after the
 // launches already enqueued, and the old buffer is released in stream order).
 static int batch_rebuild(fdtd_batch *b) {
     if (!b->dirty) return FDTD_OK;
     batch_retire_graphs(b);
-    Shape s = resolve_shape(b->storage, b->tuning);
+    const int kind = batch_kind(b);
+    Shape s = resolve_shape(b->storage, b->tuning, kind);
+    const int box_y = s.tile_y + (kind == 0 ? 2 : 4);
     const int G = num_sms() * s.ctas_per_sm;
     std::vector<TileRec> tiles;
     long long total_cols_planes = 0;
     for (auto &mb : b->members)
-        if (mb.stop > b->step && mb.c->maps_by[0] != 0 && mb.c->maps_by[0] != s.tile_y + 2) {
+        if (mb.stop > b->step && mb.c->maps_by[kind] != 0 && mb.c->maps_by[kind] != box_y) {
             cudaStreamSynchronize(b->stream);   // launches in flight may still read the old maps
             break;
         }
+    const int tw = kind == 0 ? kTileX : fused2_tile_w(b->storage);
     for (auto &mb : b->members) {
         if (mb.stop <= b->step) continue;   // finished members carry no tiles
         fdtd_ctx *c = mb.c;
-        if (int rc = encode_maps(c, 0, s.tile_y + 2)) return bfail(b, rc, "member: %s", c->err.c_str());
-        total_cols_planes += (long long)((c->nx + kTileX - 1) / kTileX) * ((c->ny + s.tile_y - 1) / s.tile_y) * c->nz;
+        if (int rc = encode_maps(c, kind, box_y)) return bfail(b, rc, "member: %s", c->err.c_str());
+        total_cols_planes += (long long)((c->nx + tw - 1) / tw) * ((c->ny + s.tile_y - 1) / s.tile_y) * c->nz;
     }
     // one z-length for all members so tiles carry similar work; about 8 tiles per CTA
     const int zlen = b->tuning.zchunk > 0 ? b->tuning.zchunk
@@ -1197,7 +1305,7 @@ static int batch_rebuild(fdtd_batch *b) {
     for (auto &mb : b->members) {
         if (mb.stop <= b->step) continue;
         const size_t first = tiles.size();
-        append_tiles(tiles, mb.c, mb.cur0 ^ (int)(mb.join & 1), s.tile_y, std::min(zlen, mb.c->nz));
+        append_tiles(tiles, mb.c, mb.cur0 ^ (int)(mb.join_launch & 1), s.tile_y, std::min(zlen, mb.c->nz), kind);
         for (size_t q = first; q < tiles.size(); ++q) tiles[q].stop = mb.stop;
     }
     // longest tiles first, then round-robin over the persistent CTAs
@@ -1219,8 +1327,10 @@ static int batch_rebuild(fdtd_batch *b) {
     return FDTD_OK;
 }
 
-static int batch_launch(fdtd_batch *b, int parity) {
-    Shape s = resolve_shape(b->storage, b->tuning);
+// One launch advancing the batch clock by nsteps (1, or 2 with the two-step kernel), then the clock.
+static int batch_launch(fdtd_batch *b, int parity, int nsteps) {
+    const int kind = batch_kind(b);
+    Shape s = resolve_shape(b->storage, b->tuning, kind);
     FusedLaunch L{};
     L.recs = b->d_tiles;
     L.step = b->d_step;
@@ -1230,28 +1340,39 @@ static int batch_launch(fdtd_batch *b, int parity) {
     L.tile_y = s.tile_y;
     L.stages = s.stages;
     L.grid = b->grid;
-    cudaError_t e = launch_fused_step(b->storage, L, b->stream);
-    if (e == cudaSuccess) e = launch_step_counter(b->d_step, b->stream);
+    L.launch_steps = nsteps;
+    cudaError_t e = kind == 0 ? launch_fused_step(b->storage, L, b->stream) : launch_fused2_step(b->storage, L, b->stream);
+    if (e == cudaSuccess) e = launch_step_counter(b->d_step, nsteps, b->stream);
     if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
     return FDTD_OK;
+}
+
+// Host bookkeeping of one launch that starts at the current clock: members with steps left take part.
+static void batch_account(fdtd_batch *b, int nsteps) {
+    for (auto &mb : b->members)
+        if (mb.stop > b->step) ++mb.nlaunch;
+    b->step += nsteps;
+    ++b->launches;
 }
 
 int fdtd_batch_step(fdtd_batch *b, int nsteps) {
     if (!b || nsteps < 0) return bfail(b, FDTD_ERR_ARG, "bad argument");
     if (b->members.empty() || nsteps == 0) return FDTD_OK;
     if (int rc = batch_rebuild(b)) return rc;
+    const int kind = batch_kind(b);
+    const int per = kind == 0 ? 1 : 2;   // steps per launch
     int left = nsteps;
-    const int K = 16;
+    const int K = 16;                    // steps per graph (an even number of launches: parity unchanged)
     if (b->tuning.use_graph && b->stream != nullptr && left >= K) {
-        const int par = (int)(b->step & 1);
-        GraphKey key{K, par};
+        const int par = (int)(b->launches & 1);
+        GraphKey key{K, par, kind};
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
             cudaGraph_t g;
             if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return bfail(b, FDTD_ERR_CUDA, "capture");
             int rc = FDTD_OK;
-            for (int s = 0; s < K && !rc; ++s) rc = batch_launch(b, par ^ (s & 1));
+            for (int q = 0; q < K / per && !rc; ++q) rc = batch_launch(b, par ^ (q & 1), per);
             cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
             if (rc) return rc;
             if (ee != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "end capture: %s", cudaGetErrorString(ee));
@@ -1265,14 +1386,91 @@ int fdtd_batch_step(fdtd_batch *b, int nsteps) {
         }
         while (left >= K) {
             if (cudaGraphLaunch(it->second, b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "graph launch");
+            for (int q = 0; q < K / per; ++q) batch_account(b, per);
             left -= K;
-            b->step += K;
         }
     }
-    for (; left > 0; --left) {
-        if (int rc = batch_launch(b, (int)(b->step & 1))) return rc;
-        ++b->step;
+    while (left > 0) {
+        const int n = std::min(per, left);   // a two-step batch ends an odd count with a level-1 launch
+        if (int rc = batch_launch(b, (int)(b->launches & 1), n)) return rc;
+        batch_account(b, n);
+        left -= n;
     }
+    return FDTD_OK;
+}
+
+int fdtd_batch_autotune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double *ms_per_step) {
+    if (!b) return FDTD_ERR_ARG;
+    if (b->members.empty()) return bfail(b, FDTD_ERR_STATE, "autotune: the batch has no members");
+    const int n = trial_length(trial_steps);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "sync");
+    // each member's current copy, set aside; the clock and launch counts are restored afterwards
+    struct Saved {
+        char *snap;
+        size_t bytes;
+        int copy;
+        long long nlaunch;
+    };
+    std::vector<Saved> saved;
+    int rc = FDTD_OK;
+    for (auto &mb : b->members) {
+        fdtd_ctx *c = mb.c;
+        Saved sv{nullptr, (size_t)c->pitch * c->ny * c->nz * esize(c->storage), mb.cur0 ^ (int)(mb.nlaunch & 1),
+                 mb.nlaunch};
+        if (pool_alloc((void **)&sv.snap, 6 * sv.bytes, b->stream) != cudaSuccess) {
+            rc = bfail(b, FDTD_ERR_OOM, "autotune: no room for a copy of the members' fields");
+            break;
+        }
+        for (int f = 0; f < 6; ++f)
+            cudaMemcpyAsync(sv.snap + f * sv.bytes, c->fields[sv.copy][f], sv.bytes, cudaMemcpyDeviceToDevice,
+                            b->stream);
+        saved.push_back(sv);
+    }
+    const long long step0 = b->step, launches0 = b->launches;
+    const fdtd_tuning t0 = b->tuning;
+    fdtd_tuning best = t0;
+    double best_ms = -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = bfail(b, FDTD_ERR_CUDA, "event create");
+    if (!rc)
+        for (const fdtd_tuning &t : tune_candidates(true)) {
+            if ((rc = fdtd_batch_set_tuning(b, &t)) != FDTD_OK) break;
+            if ((rc = fdtd_batch_step(b, n)) != FDTD_OK) break;
+            cudaEventRecord(e0, b->stream);
+            if ((rc = fdtd_batch_step(b, n)) != FDTD_OK) break;
+            cudaEventRecord(e1, b->stream);
+            if ((rc = fdtd_batch_sync(b)) != FDTD_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best_ms < 0 || ms / n < best_ms) {
+                best_ms = ms / n;
+                best = t;
+            }
+        }
+    cudaStreamSynchronize(b->stream);
+    for (size_t q = 0; q < saved.size(); ++q) {
+        fdtd_batch::Member &mb = b->members[q];
+        for (int f = 0; f < 6; ++f)
+            cudaMemcpyAsync(mb.c->fields[saved[q].copy][f], saved[q].snap + f * saved[q].bytes, saved[q].bytes,
+                            cudaMemcpyDeviceToDevice, b->stream);
+        pool_free(saved[q].snap, b->stream);
+        mb.nlaunch = saved[q].nlaunch;
+    }
+    b->step = step0;
+    b->launches = launches0;
+    cudaMemcpyAsync(b->d_step, &step0, sizeof(long long), cudaMemcpyHostToDevice, b->stream);
+    cudaStreamSynchronize(b->stream);   // step0 is read by the copy above before it goes out of scope
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->dirty = true;
+    if (rc != FDTD_OK) {
+        b->tuning = t0;
+        return rc;
+    }
+    if (int r2 = fdtd_batch_set_tuning(b, &best)) return r2;
+    if (out) *out = best;
+    if (ms_per_step) *ms_per_step = best_ms;
     return FDTD_OK;
 }
 

@@ -124,7 +124,7 @@ struct alignas(16) TileRec {
     const float4 *table;         // COEF_ID8: per id two float4: (ce x,y,z,0), (ch x,y,z,0), folded
     const CUtensorMap *maps;     // kMapsPerCavity tensor maps in global memory
     void *dst[2][6];             // both copies of the six active arrays
-    long long stop;              // batch launch index from which this tile is skipped (member finished)
+    long long stop;              // batch step clock at which this tile's member has taken all its steps
     int ntab;                    // COEF_ID8: table entries
     int nz;
     int id_x0;                   // two-step kernel: x origin of the id box (a multiple of 16)

@@ -491,10 +491,10 @@ cudaError_t launch_fused_step(int storage, const FusedLaunch &L, cudaStream_t s)
     return e;
 }
 
-__global__ void step_counter_kernel(long long *c) { *c += 1; }
+__global__ void step_counter_kernel(long long *c, int inc) { *c += inc; }
 
-cudaError_t launch_step_counter(long long *counter, cudaStream_t s) {
-    step_counter_kernel<<<1, 1, 0, s>>>(counter);
+cudaError_t launch_step_counter(long long *counter, int inc, cudaStream_t s) {
+    step_counter_kernel<<<1, 1, 0, s>>>(counter, inc);
     return cudaGetLastError();
 }
 

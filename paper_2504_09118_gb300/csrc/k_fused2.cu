@@ -44,6 +44,8 @@ template <typename T> struct Geom2 {
 
 struct Fused2Params {
     const TileRec *recs;
+    const long long *step;   // batch step clock (NULL: a single cavity, no tile is skipped)
+    int launch_steps;        // 2, or 1: level 1 only
     int ntiles;
     int parity;
     int *status;
@@ -102,6 +104,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
     const int t_begin = P.first ? __ldg(P.first + blockIdx.x) : (int)blockIdx.x;
     const int t_end = P.first ? __ldg(P.first + blockIdx.x + 1) : P.ntiles;
     const int t_step = P.first ? 1 : (int)gridDim.x;
+    // Steps a tile takes in this launch: min(launch_steps, stop - clock); a batch member with one step
+    // left stores its level-1 result, a finished member's tiles are skipped (producer and consumers alike).
+    const long long clock = P.step ? *P.step : 0;
 
     if (threadIdx.x == 0) {
         *abort_flag = 0;
@@ -120,6 +125,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         uint32_t rnd = 0;
         bool ok = true;
         for (int t = t_begin; t < t_end && ok; t += t_step) {
+            if (__ldg(&P.recs[t].stop) <= clock) continue;   // member already took its last step
             TileRec *rec = &recs[m++ % NTR2];
             int kb = 0, klast = 0;
             for (int k = 0;; ++k) {
@@ -187,6 +193,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
     const float2 zero2 = make_float2(0.f, 0.f);
 
     for (int t = t_begin; t < t_end; t += t_step) {
+        if (__ldg(&P.recs[t].stop) <= clock) continue;   // same skip rule as the producer
         bool ok = wait_full(sa, pa);
         if (bar_sync_or(2, NCT, !ok || *abort_flag != 0)) {
             if (threadIdx.x == 0) atomicOr(P.status, STATUS_TIMEOUT);
@@ -219,6 +226,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         const bool out_row = r >= 2 && r < TY + 2 && gj < ny;      // level-2 outputs of this row are stored
         const bool out_a = lane >= 1 && 2 * lane - 2 < W && gi < nx; // both cells share the column window
         const int kb = kz0 > 2 ? kz0 - 2 : 0;
+        const bool level1_only = P.launch_steps == 1 || rec->stop - clock == 1;
 
         auto at = [&](const T *base, int f, int xx, int yy) { return base + f * FE + yy * BX + xx; };
         auto coef = [&](uint32_t ip, int which, float4 &a, float4 &b) {   // which: 0 ce, 1 ch
@@ -247,7 +255,8 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
             const T *B = reinterpret_cast<const T *>(slots + sb * SB);
             const uint8_t *ida = slots + sa * SB + 6 * FS;
             // H2(k-1) needs plane k-1 >= 0 (its inputs at plane -1 were never written)
-            const bool do_e1 = k >= kz0 - 1, do_h2 = k >= kz0 && k >= 1, do_e2 = k >= kz0 + 1;
+            const bool do_e1 = k >= kz0 - 1;
+            const bool do_h2 = !level1_only && k >= kz0 && k >= 1, do_e2 = !level1_only && k >= kz0 + 1;
             float *e1cur = e1b + (k & 1) * 2 * PF, *e1prv = e1b + ((k + 1) & 1) * 2 * PF;
 
             // ---------------- phase 1: H1(k) on the lane's two cells
@@ -300,6 +309,15 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 if (!vb) { e1x.y = 0.f; e1y.y = 0.f; e1z.y = 0.f; }
                 *reinterpret_cast<float2 *>(e1cur + pr * PW + pc) = e1x;
                 *reinterpret_cast<float2 *>(e1cur + PF + pr * PW + pc) = e1z;
+                if (level1_only && out_row && out_a && k >= kz0 && k < kz1) {   // one step: (H1, E1) is the result
+                    const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                    Pair<T>::st(dst[0] + g, e1x.x, e1x.y);
+                    Pair<T>::st(dst[1] + g, e1y.x, e1y.y);
+                    Pair<T>::st(dst[2] + g, e1z.x, e1z.y);
+                    Pair<T>::st(dst[3] + g, h1x_.x, h1x_.y);
+                    Pair<T>::st(dst[4] + g, h1y_.x, h1y_.y);
+                    Pair<T>::st(dst[5] + g, h1z_.x, h1z_.y);
+                }
             }
             asm volatile("bar.sync 1, %0;" ::"r"(NCT) : "memory");
 
@@ -383,6 +401,8 @@ cudaError_t launch2_typed(const FusedLaunch &L, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     Fused2Params P;
     P.recs = L.recs;
+    P.step = L.step;
+    P.launch_steps = L.launch_steps == 1 ? 1 : 2;
     P.ntiles = L.ntiles;
     P.parity = L.parity;
     P.status = L.status;

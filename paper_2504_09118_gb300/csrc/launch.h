@@ -23,7 +23,7 @@ int reduction_blocks();
 
 struct FusedLaunch {
     const TileRec *recs;       // device array, one record per tile
-    const long long *step;     // device launch counter compared with TileRec::stop (NULL: no tile skipped)
+    const long long *step;     // device step clock compared with TileRec::stop (NULL: no tile skipped)
     int ntiles;
     int parity;
     int *status;
@@ -33,13 +33,15 @@ struct FusedLaunch {
     int inject_timeout_us;     // >0: do not issue the CTA 0's first unit; wait limit in us
     const int *first;          // device, grid + 1 entries: CTA b takes tiles [first[b], first[b+1]) in order
                                // (NULL: CTA b takes tiles b, b + grid, b + 2 grid, ...)
+    int launch_steps;          // two-step kernel: 2, or 1 (every tile stores its level-1 result only)
 };
 // Shared memory bytes and max co-resident CTAs per SM for a fused configuration.
 int fused_smem_bytes(int storage, int tile_y, int stages);
 cudaError_t fused_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
 cudaError_t launch_fused_step(int storage, const FusedLaunch &L, cudaStream_t s);
 // *counter += 1 on the stream (advances a batch's device launch counter after each step).
-cudaError_t launch_step_counter(long long *counter, cudaStream_t s);
+// Adds inc to the device step clock of a batch (one thread; ordered after the launch it follows).
+cudaError_t launch_step_counter(long long *counter, int inc, cudaStream_t s);
 // Two-step (temporal blocking) kernel: output tile width along x, shared memory, occupancy, launch.
 int fused2_tile_w(int storage);
 int fused2_smem_bytes(int storage, int tile_y, int stages);

@@ -33,19 +33,21 @@ def make_members(storage=0, stream=None, seed=0):
 
 @pytest.mark.parametrize("storage", [0, 2])
 @pytest.mark.parametrize("use_graph", [0, 1])
-def test_batch_equals_alone_bitwise(storage, use_graph):
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_batch_equals_alone_bitwise(storage, use_graph, kernel):
+    # the same kernel alone and in the batch; 37 steps: two-step launches end with a one-step launch
     import torch
     from paper_2504_09118_gb300 import binding
     s = torch.cuda.Stream()
     alone = make_members(storage, s)
     for c, *_ in alone:
-        c.tune(kernel=2, tile_y=8)
+        c.tune(kernel=kernel, tile_y=8)
         c.step(37)
     ref = [c.get_fields() for c, *_ in alone]
     mixed = make_members(storage, s)
     b = binding.fdtd_batch_create(storage, s)
     try:
-        binding.fdtd_batch_set_tuning(b, kernel=2, tile_y=8, use_graph=use_graph)
+        binding.fdtd_batch_set_tuning(b, kernel=kernel, tile_y=8, use_graph=use_graph)
         for c, *_ in mixed:
             binding.fdtd_batch_add(b, c.handle)
         assert binding.fdtd_batch_size(b) == len(DIMS)
@@ -64,14 +66,15 @@ def test_batch_equals_alone_bitwise(storage, use_graph):
         c.close()
 
 
-def test_batch_member_matches_oracle():
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_batch_member_matches_oracle(kernel):
     import oracle
     import torch
     from paper_2504_09118_gb300 import binding
     s = torch.cuda.Stream()
     mem = make_members(0, s, seed=7)
     b = binding.fdtd_batch_create(0, s)
-    binding.fdtd_batch_set_tuning(b, use_graph=1)
+    binding.fdtd_batch_set_tuning(b, kernel=kernel, use_graph=1)
     for c, *_ in mem:
         binding.fdtd_batch_add(b, c.handle)
     binding.fdtd_batch_step(b, 40)
@@ -84,8 +87,9 @@ def test_batch_member_matches_oracle():
         c.close()
 
 
-def test_continuous_batching_join_and_leave():
-    """Members join and leave between steps; each result equals its solo run."""
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_continuous_batching_join_and_leave(kernel):
+    """Members join and leave between steps (odd clocks included); each result equals its solo run."""
     import torch
     from paper_2504_09118_gb300 import binding
     s = torch.cuda.Stream()
@@ -97,7 +101,7 @@ def test_continuous_batching_join_and_leave():
     ref = [c.get_fields() for c, *_ in solo[:4]]
     mem = make_members(0, s, seed=3)[:4]
     b = binding.fdtd_batch_create(0, s)
-    binding.fdtd_batch_set_tuning(b, tile_y=8, use_graph=1)
+    binding.fdtd_batch_set_tuning(b, kernel=kernel, tile_y=8, use_graph=1)
     remaining = {}
     t = 0
     while True:
@@ -158,8 +162,10 @@ def test_batch_rejects_mismatches():
         binding.fdtd_batch_destroy(b)
 
 
-def test_members_stop_at_their_own_step_counts():
-    """fdtd_batch_set_steps freezes each member after its own count, inside graph-replayed chunks."""
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_members_stop_at_their_own_step_counts(kernel):
+    """fdtd_batch_set_steps freezes each member after its own count, inside graph-replayed chunks
+    (with two-step launches, a member with an odd count takes its last step as a one-step store)."""
     import torch
     from paper_2504_09118_gb300 import binding
     s = torch.cuda.Stream()
@@ -172,7 +178,7 @@ def test_members_stop_at_their_own_step_counts():
     load = torch.cuda.Stream()   # members on their own stream: removal orders it after the batch
     mem = make_members(0, load, seed=11)[:len(counts)]
     b = binding.fdtd_batch_create(0, s)
-    binding.fdtd_batch_set_tuning(b, kernel=2, tile_y=8, use_graph=1)
+    binding.fdtd_batch_set_tuning(b, kernel=kernel, tile_y=8, use_graph=1)
     for (c, *_), n in zip(mem, counts):
         binding.fdtd_batch_add(b, c.handle)
         binding.fdtd_batch_set_steps(b, c.handle, n)
@@ -183,6 +189,33 @@ def test_members_stop_at_their_own_step_counts():
     binding.fdtd_batch_destroy(b)
     for (c, *_), n, r in zip(mem, counts, ref):
         assert c.steps_done == n
+        for x, y in zip(c.get_fields(), r):
+            assert np.array_equal(x, y)
+    for c, *_ in solo + mem:
+        c.close()
+
+
+def test_batch_switches_kernels_between_steps():
+    """One-step and two-step launches interleaved in one batch: every member stays bit-identical."""
+    import torch
+    from paper_2504_09118_gb300 import binding
+    s = torch.cuda.Stream()
+    solo = make_members(0, s, seed=13)[:6]
+    for c, *_ in solo:
+        c.tune(kernel=2, tile_y=8)
+        c.step(3 + 16 + 5 + 2)
+    ref = [c.get_fields() for c, *_ in solo]
+    mem = make_members(0, s, seed=13)[:6]
+    b = binding.fdtd_batch_create(0, s)
+    for c, *_ in mem:
+        binding.fdtd_batch_add(b, c.handle)
+    for kernel, n in ((3, 3), (2, 16), (3, 5), (2, 2)):
+        binding.fdtd_batch_set_tuning(b, kernel=kernel, use_graph=1)
+        binding.fdtd_batch_step(b, n)
+    assert binding.fdtd_batch_steps_done(b) == 26
+    binding.fdtd_batch_destroy(b)
+    for (c, *_), r in zip(mem, ref):
+        assert c.steps_done == 26
         for x, y in zip(c.get_fields(), r):
             assert np.array_equal(x, y)
     for c, *_ in solo + mem:
