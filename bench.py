@@ -54,6 +54,9 @@ WORKLOADS = {
 # Launch configuration the bench times (the full-size parity test uses the same): the two-step
 # temporal-blocking kernel, 60 x 12-cell tiles (FP32), 6-slot TMA ring, graphs of 8 launches.
 BENCH_TUNING = dict(kernel=3, tile_y=12, stages=6, zchunk=0, ctas_per_sm=0, use_graph=1)
+# Batches of the serving loop: two-step launches, 12-row tiles (what fdtd_batch_autotune picks for the
+# batch workload; the serving mix changes every chunk, so it is fixed rather than re-tuned).
+SERVE_TUNING = dict(kernel=3, tile_y=12, stages=4)
 STEPS_PER_LAUNCH = {1: 0.5, 2: 1, 3: 2}   # leapfrog steps per launch of each kernel kind (SIMPLE: H and E launches)
 DOMINANT_KERNEL = {1: "simple_h_kernel/simple_e_kernel", 2: "fused_step_kernel", 3: "fused2_step_kernel"}
 ID_BYTES = 1  # material id per cell
@@ -225,9 +228,12 @@ def run_batch(args, w):
     cells = sum(c.dims[0] * c.dims[1] * c.dims[2] for c in members)
     per = w["steps"]
     b = binding.fdtd_batch_create(w["storage"], stream)
-    binding.fdtd_batch_set_tuning(b, kernel=2, tile_y=8, stages=4, use_graph=1)
     for m in members:
         binding.fdtd_batch_add(b, m.handle)
+    # the batch's kernel and tile shape: timed on the members' own state by the library (restored after)
+    t_tune = time.perf_counter()
+    tuning, _ = binding.fdtd_batch_autotune(b, 32)
+    t_tune = time.perf_counter() - t_tune
     for _ in range(args.warmup):
         binding.fdtd_batch_step(b, per)
     binding.fdtd_batch_sync(b)
@@ -262,9 +268,12 @@ def run_batch(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch256", "cavities": len(members), "cells": cells,
-                       "leapfrog_steps_per_bench_step": per, "graph_steps": 16},
+                       "leapfrog_steps_per_bench_step": per, "graph_steps": 16,
+                       "autotuned": tuning, "autotune_s": round(t_tune, 3)},
             "plain_one_launch_per_step": round(plain, 3), "batched_vs_plain": round(value / plain, 3),
-            "clocks": clk.summary(), "gpu_launches": 2 * args.steps * per}   # fused step + step counter
+            "clocks": clk.summary(),
+            # each launch (one step, or two with the two-step kernel) is followed by the clock kernel
+            "gpu_launches": 2 * args.steps * per // (2 if tuning["kernel"] == 3 else 1)}
     print(json.dumps(line), flush=True)
 
 
@@ -283,7 +292,7 @@ def run_serve(args, w):
 
     reqs = [Request(q["id"], q["arrival_s"], q["nx"], q["ny"], q["nz"], q["steps"], q["bf16"]) for q in stream]
     srv = Server(ci.COURANT_HALF_DT, hbm_budget_bytes=int(w["budget_gb"] * (1 << 30)), K=16,
-                 tuning={"tile_y": 8, "stages": 4}, result="energy", fields_fn=fields_fn)
+                 tuning=SERVE_TUNING, result="energy", fields_fn=fields_fn)
     with ClockSampler(0, args.clocks_csv) as clk:
         st = srv.run(reqs)
     srv.close()
@@ -296,7 +305,7 @@ def run_serve(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 or bf16-storage per request", "data": "synthetic",
             "config": {"workload": "serve", "requests": st.n, "rate_hz": w["rate"], "budget_gb": w["budget_gb"],
-                       "graph_steps": 16},
+                       "graph_steps": 16, "tuning": SERVE_TUNING},
             "serving": {"p50_s": round(st.p50_s, 4), "p99_s": round(st.p99_s, 4), "mean_s": round(st.mean_s, 4),
                         "wall_s": round(st.wall_s, 3), "max_active": st.max_active,
                         "offered_gcells": round(st.cell_updates / max(r["arrival_s"] for r in stream) / 1e9, 2)},
