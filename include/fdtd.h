@@ -109,7 +109,9 @@ FDTD_API int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, doub
 /*
  * fdtd_set_fields - load the state (H^{n-1/2}, E^n) and reset the step counter.
  *   f[6]       canonical FP32 arrays; host pointers when on_device == 0, CUDA
- *              device pointers when on_device == 1.  Read during the call only.
+ *              device pointers when on_device == 1.  Read during the call only, on the
+ *              context's stream: device data written on another stream must be complete
+ *              before the call (the Python binding synchronises torch's current stream).
  * Tangential E on the faces is written as 0 whatever the input holds.
  * Synchronises the stream before returning.
  */
@@ -124,7 +126,8 @@ FDTD_API int fdtd_step(fdtd_ctx *ctx, int nsteps);
 
 /*
  * fdtd_get_fields - write the current state into f[6] (canonical FP32; host or
- * device pointers as on_device says).  Entries outside each extent are 0.
+ * device pointers as on_device says; device buffers are written on the context's
+ * stream, so other streams must be done with them).  Entries outside each extent are 0.
  * Synchronises the stream; returns a latched device error if one occurred.
  */
 FDTD_API int fdtd_get_fields(fdtd_ctx *ctx, float *const f[6], int on_device);

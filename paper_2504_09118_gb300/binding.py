@@ -168,6 +168,9 @@ def _field_ptrs(fields, shape, on_device: bool, writable: bool):
             if str(t.dtype) != "torch.float32" or not t.is_contiguous() or t.numel() != int(np.prod(shape)):
                 raise ValueError("device fields must be contiguous float32 tensors of the canonical size")
             ptrs.append(t.data_ptr())
+        # the library reads / writes them on its own stream: torch's pending work on them must be done
+        import torch
+        torch.cuda.current_stream(fields[0].device).synchronize()
         return ptrs, fields
     arrs = []
     for a in fields:

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <queue>
@@ -124,6 +125,11 @@ struct fdtd_batch {
     bool dirty = true;
     int *d_status = nullptr;
     cudaEvent_t done_ev = nullptr;   // recorded at member removal; the member's stream waits on it
+    // Completion marks: after each fdtd_batch_step call, an event and the clock it brings the batch
+    // to.  A removed member's stream waits only for the first mark at or past the clock at which the
+    // member took its last step (later launches skip it), not for everything enqueued since.
+    std::deque<std::pair<long long, cudaEvent_t>> marks;
+    std::vector<cudaEvent_t> free_marks;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::vector<cudaGraphExec_t> retired_graphs;   // destroyed at the next synchronisation point
     std::string err;
@@ -1236,14 +1242,28 @@ int fdtd_batch_remove(fdtd_batch *b, fdtd_ctx *c) {
     size_t n = 0;
     fdtd_batch::Member *mb = find_member(b, c, &n);
     if (!mb) return bfail(b, FDTD_ERR_ARG, "context is not a member");
-    const long long taken = std::min(b->step, mb->stop) - mb->join;
+    const long long last = std::min(b->step, mb->stop);   // clock after the member's last step
+    const long long taken = last - mb->join;
     c->cur = mb->cur0 ^ (int)(mb->nlaunch & 1);
     c->steps = mb->steps0 + taken;
     c->batch = nullptr;
-    // later work on the member's own stream (read-back, destroy) waits for the batch work enqueued so far
-    if (cudaEventRecord(b->done_ev, b->stream) != cudaSuccess ||
-        cudaStreamWaitEvent(c->stream, b->done_ev, 0) != cudaSuccess)
-        return bfail(b, FDTD_ERR_CUDA, "ordering the member's stream after the batch failed");
+    // later work on the member's own stream (read-back, destroy) waits for the batch launches that
+    // touched it: those up to the first completion mark at or past its last step
+    if (taken > 0 || mb->nlaunch > 0) {
+        cudaEvent_t ev = nullptr;
+        for (const auto &mk : b->marks)
+            if (mk.first >= last) {
+                ev = mk.second;
+                break;
+            }
+        if (!ev) {   // no mark covers it yet (not possible after fdtd_batch_step): wait for everything
+            if (cudaEventRecord(b->done_ev, b->stream) != cudaSuccess)
+                return bfail(b, FDTD_ERR_CUDA, "ordering the member's stream after the batch failed");
+            ev = b->done_ev;
+        }
+        if (cudaStreamWaitEvent(c->stream, ev, 0) != cudaSuccess)
+            return bfail(b, FDTD_ERR_CUDA, "ordering the member's stream after the batch failed");
+    }
     b->members.erase(b->members.begin() + n);
     b->dirty = true;
     return FDTD_OK;
@@ -1396,6 +1416,20 @@ int fdtd_batch_step(fdtd_batch *b, int nsteps) {
         batch_account(b, n);
         left -= n;
     }
+    // completion mark at the new clock; marks whose work has finished are recycled (the newest stays)
+    while (b->marks.size() > 1 && cudaEventQuery(b->marks.front().second) == cudaSuccess) {
+        b->free_marks.push_back(b->marks.front().second);
+        b->marks.pop_front();
+    }
+    cudaEvent_t ev = nullptr;
+    if (!b->free_marks.empty()) {
+        ev = b->free_marks.back();
+        b->free_marks.pop_back();
+    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        return bfail(b, FDTD_ERR_CUDA, "event create");
+    }
+    if (cudaEventRecord(ev, b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "event record");
+    b->marks.emplace_back(b->step, ev);
     return FDTD_OK;
 }
 
@@ -1461,6 +1495,8 @@ int fdtd_batch_autotune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double
     b->launches = launches0;
     cudaMemcpyAsync(b->d_step, &step0, sizeof(long long), cudaMemcpyHostToDevice, b->stream);
     cudaStreamSynchronize(b->stream);   // step0 is read by the copy above before it goes out of scope
+    for (auto &mk : b->marks) b->free_marks.push_back(mk.second);   // their clocks ran ahead of the restored one
+    b->marks.clear();
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     b->dirty = true;
@@ -1500,6 +1536,8 @@ void fdtd_batch_destroy(fdtd_batch *b) {
     pool_free(b->d_step, b->stream);
     cudaStreamSynchronize(b->stream);
     cudaEventDestroy(b->done_ev);
+    for (auto &mk : b->marks) cudaEventDestroy(mk.second);
+    for (cudaEvent_t e : b->free_marks) cudaEventDestroy(e);
     delete b;
 }
 
