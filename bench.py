@@ -169,9 +169,20 @@ def cpu_baseline(w, budget_s: float = 12.0):
     oracle.step(f, ce64, ch_s, steps, omp=True)
     dt = time.perf_counter() - t0
     rate = nx * ny * nzs * steps / dt / 1e9
+    # the same oracle on one thread (the paper's single-thread setting), 128^3 vacuum, a few steps
+    g = oracle.as_f64(ci.random_fields(w["field_seed"], 128, 128, 128))
+    t0 = time.perf_counter()
+    oracle.step(g, ci.COURANT_HALF_DT, ci.COURANT_HALF_DT, 1, omp=False)
+    one = time.perf_counter() - t0
+    s1 = max(1, min(20, int(0.25 * budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.step(g, ci.COURANT_HALF_DT, ci.COURANT_HALF_DT, s1, omp=False)
+    d1 = time.perf_counter() - t0
     return {"value": round(rate, 4), "unit": "Gcell-updates/s", "cores": oracle.threads(True), "kind": "oracle",
             "sample": f"{nx}x{ny}x{nzs} slab of the {w['n'][0]}x{w['n'][1]}x{w['n'][2]} workload "
-                      f"(same sphere layout), FP64 OpenMP oracle, {steps} steps in {dt:.1f} s"}
+                      f"(same sphere layout), FP64 OpenMP oracle, {steps} steps in {dt:.1f} s",
+            "single_thread": {"value": round(128 ** 3 * s1 / d1 / 1e9, 4), "unit": "Gcell-updates/s",
+                              "sample": f"128^3 vacuum, serial FP64 oracle, {s1} steps in {d1:.1f} s"}}
 
 
 def run_reference(args, w, wname):
