@@ -151,6 +151,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's); x itself for one rank."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ws: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time (weak scaling)."""
+    return units_per_rank * ws / seconds
+
+
 def cpu_baseline(w, budget_s: float = 12.0):
     """Time the FP64 oracle (OpenMP build, all host cores) on a bounded z-slab of the workload."""
     import oracle
@@ -462,12 +479,8 @@ def main():
     barrier()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = cells * per * args.steps * ws / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms, ws)
+    value = job_rate(cells * per * args.steps, ws, ms / 1e3) / 1e9
     clocks = clk.summary()
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time.  A launch of
@@ -506,10 +519,8 @@ def main():
         e2e_s = time.perf_counter() - t0
         if ws > 1:
             import torch.distributed as dist
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": round(cells * per * args.steps * ws / e2e_s / 1e9, 3), "unit": "Gcell-updates/s",
+            e2e_s = max_over_ranks(e2e_s, ws)
+        e2e = {"value": round(job_rate(cells * per * args.steps, ws, e2e_s) / 1e9, 3), "unit": "Gcell-updates/s",
                "h2d_bytes_per_step": int(sum(a.nbytes for a in host)), "d2h_bytes_per_step": 8}
 
     cpu = None
