@@ -32,6 +32,32 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+#ifndef FDTD_CHECK
+#define FDTD_CHECK 0   // 1: every global store and TMA x origin of the fused kernels is checked first
+#endif
+
+// Checked builds (FDTD_CHECK=1, the library variant built beside the normal one): an access that would
+// leave its buffer, or a TMA x origin off the 16-byte granule, is skipped and STATUS_BADINDEX latched
+// (reported by the next synchronising call).  In normal builds both checks are constant `true`.
+__device__ __forceinline__ bool store_ok(int *status, long long g, long long n, long long elems) {
+#if FDTD_CHECK
+    if (g < 0 || g + n > elems) {
+        atomicOr(status, STATUS_BADINDEX);
+        return false;
+    }
+#endif
+    return true;
+}
+__device__ __forceinline__ bool tma_x_ok(int *status, int x, int esize) {
+#if FDTD_CHECK
+    if (((long long)x * esize) % 16 != 0) {
+        atomicOr(status, STATUS_BADINDEX);
+        return false;
+    }
+#endif
+    return true;
+}
+
 // Named barrier over `nthreads` threads that also ORs a predicate across them.
 __device__ __forceinline__ bool bar_sync_or(int id, int nthreads, bool pred) {
     uint32_t r;

@@ -191,13 +191,19 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     const bool has_id = rec->mode == COEF_ID8;
                     unsigned char *dst = slots + s * SB;
                     fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? id_box_bytes<TY>() : 0));
-                    const CUtensorMap *mp = rec->maps + src_copy * 6;
+                    if (tma_x_ok(P.status, rec->x0 - HX, (int)sizeof(T)) &&
+                        (!has_id || tma_x_ok(P.status, rec->x0 - G::IDX_HALO, 1))) {
+                        mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? id_box_bytes<TY>() : 0));
+                        const CUtensorMap *mp = rec->maps + src_copy * 6;
 #pragma unroll
-                    for (int f = 0; f < 6; ++f)
-                        tma_load_3d(dst + f * FS, mp + f, rec->x0 - HX, rec->y0 - 1, kk, &full[s]);
-                    if (has_id)
-                        tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->x0 - G::IDX_HALO, rec->y0 - 1, kk, &full[s]);
+                        for (int f = 0; f < 6; ++f)
+                            tma_load_3d(dst + f * FS, mp + f, rec->x0 - HX, rec->y0 - 1, kk, &full[s]);
+                        if (has_id)
+                            tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->x0 - G::IDX_HALO, rec->y0 - 1, kk,
+                                        &full[s]);
+                    } else {
+                        mbar_arrive(&full[s]);   // checked build: the unit is skipped, the slot still completes
+                    }
                 }
                 __syncwarp();
                 ++issued;
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
         }
         const TileRec *rec = &recs[m++ % NTR];
         const int x0 = rec->x0, y0 = rec->y0, kz0 = rec->kz0, kz1 = rec->kz1;
-        const int nx = rec->nx, ny = rec->ny;
+        const int nx = rec->nx, ny = rec->ny, nz = rec->nz;
         const long long pitch = rec->pitch, plane = rec->plane;
         const bool id_mode = rec->mode == COEF_ID8;
         const bool ch_uni = rec->ch_uniform != 0;
@@ -337,8 +343,8 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     *reinterpret_cast<float2 *>(hn + o) = hx;
                     *reinterpret_cast<float2 *>(hn + HC + o) = hy;
                     *reinterpret_cast<float2 *>(hn + 2 * HC + o) = hz;
-                    if (!prologue && gj < ny && gi < nx) {
-                        const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                    const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                    if (!prologue && gj < ny && gi < nx && store_ok(P.status, g, 2, plane * nz)) {
                         Pair<T>::st(dst[3] + g, hx.x, hx.y);
                         Pair<T>::st(dst[4] + g, hy.x, hy.y);
                         Pair<T>::st(dst[5] + g, hz.x, hz.y);
@@ -395,8 +401,8 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     ex = fma2(cex, sub2(sub2(hz, hz_ym), sub2(hy, hpy)), ex);
                     ey = fma2(cey, sub2(sub2(hx, hpx), sub2(hz, hz_xm2)), ey);
                     ez = fma2(cez, sub2(sub2(hy, hy_xm2), sub2(hx, hx_ym)), ez);
-                    if (gj < ny && gi < nx) {
-                        const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                    const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                    if (gj < ny && gi < nx && store_ok(P.status, g, 2, plane * nz)) {
                         Pair<T>::st(dst[0] + g, ex.x, ex.y);
                         Pair<T>::st(dst[1] + g, ey.x, ey.y);
                         Pair<T>::st(dst[2] + g, ez.x, ez.y);

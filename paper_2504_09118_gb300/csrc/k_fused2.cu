@@ -154,12 +154,18 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                     const bool has_id = rec->mode == COEF_ID8;
                     unsigned char *dst = slots + s * SB;
                     fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? idbox_bytes<TY>() : 0));
-                    const CUtensorMap *mp = rec->maps + src_copy * 6;
+                    if (tma_x_ok(P.status, rec->x0 - HX, (int)sizeof(T)) &&
+                        (!has_id || tma_x_ok(P.status, rec->id_x0, 1))) {
+                        mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? idbox_bytes<TY>() : 0));
+                        const CUtensorMap *mp = rec->maps + src_copy * 6;
 #pragma unroll
-                    for (int f = 0; f < 6; ++f)
-                        tma_load_3d(dst + f * FS, mp + f, rec->x0 - HX, rec->y0 - 2, kk, &full[s]);
-                    if (has_id) tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
+                        for (int f = 0; f < 6; ++f)
+                            tma_load_3d(dst + f * FS, mp + f, rec->x0 - HX, rec->y0 - 2, kk, &full[s]);
+                        if (has_id)
+                            tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
+                    } else {
+                        mbar_arrive(&full[s]);   // checked build: the unit is skipped, the slot still completes
+                    }
                 }
                 __syncwarp();
                 ++issued;
@@ -309,8 +315,10 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 if (!vb) { e1x.y = 0.f; e1y.y = 0.f; e1z.y = 0.f; }
                 *reinterpret_cast<float2 *>(e1cur + pr * PW + pc) = e1x;
                 *reinterpret_cast<float2 *>(e1cur + PF + pr * PW + pc) = e1z;
-                if (level1_only && out_row && out_a && k >= kz0 && k < kz1) {   // one step: (H1, E1) is the result
-                    const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                const long long g1 = (long long)k * plane + (long long)gj * pitch + gi;
+                if (level1_only && out_row && out_a && k >= kz0 && k < kz1 &&
+                    store_ok(P.status, g1, 2, plane * nz)) {   // one step: (H1, E1) is the result
+                    const long long g = g1;
                     Pair<T>::st(dst[0] + g, e1x.x, e1x.y);
                     Pair<T>::st(dst[1] + g, e1y.x, e1y.y);
                     Pair<T>::st(dst[2] + g, e1z.x, e1z.y);
@@ -356,8 +364,8 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 const float2 e2x = fma2(cex, sub2(sub2(h2z, hz_ym), sub2(h2y, h2py)), e1px);
                 const float2 e2y = fma2(cey, sub2(sub2(h2x, h2px), sub2(h2z, make_float2(h2z_xm, h2z.x))), e1py);
                 const float2 e2z = fma2(cez, sub2(sub2(h2y, make_float2(h2y_xm, h2y.x)), sub2(h2x, hx_ym)), e1pz);
-                if (out_a) {
-                    const long long g = (long long)kk * plane + (long long)gj * pitch + gi;
+                const long long g = (long long)kk * plane + (long long)gj * pitch + gi;
+                if (out_a && store_ok(P.status, g, 2, plane * nz)) {
                     Pair<T>::st(dst[0] + g, e2x.x, e2x.y);
                     Pair<T>::st(dst[1] + g, e2y.x, e2y.y);
                     Pair<T>::st(dst[2] + g, e2z.x, e2z.y);

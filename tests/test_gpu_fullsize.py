@@ -71,6 +71,35 @@ def test_512_spheres_sampled_parity_and_invariants():
             assert np.all(g[c][ci.tangential_e_mask(name, *n)] == 0.0)
 
 
+def test_128_crop_of_the_512_layout_vs_oracle():
+    """A separate 128^3 cavity whose coefficients sample the 512^3 sphere layout on [0, 128]^3, its own
+    seeded fields, 200 steps in the bench's launch configuration, element-wise against the FP64 oracle."""
+    import oracle
+    from paper_2504_09118_gb300 import Cavity
+    w = bench.WORKLOADS["single512"]
+    sph = ci.sphere_list(w["sphere_seed"], w["spheres"], w["n"], 8.0, 40.0)
+    n = (128, 128, 128)
+    ce, ch = ci.sphere_coefficients(sph, *n, DT)
+    assert any(float(c.min()) < DT * 0.9 for c in ce)    # some sphere reaches into the crop
+    f = ci.random_fields(w["field_seed"] + 17, *n)
+    with Cavity(*n, DT, 1.0, ce, ch) as cav:
+        cav.tune(**bench.BENCH_TUNING)
+        cav.set_fields(f)
+        w0 = cav.energy()
+        cav.step(200)
+        w1 = cav.energy()
+        got = cav.get_fields()
+    ref = oracle.as_f64(f)
+    oracle.step(ref, [c.astype(np.float64) for c in ce], ch, 200, omp=True)
+    norm = float(np.sqrt(sum(np.sum(r ** 2) for r in ref)))
+    for c, name in enumerate(ci.COMPONENTS):
+        m = ci.extent_mask(name, *n)
+        d = np.linalg.norm(got[c][m].astype(np.float64) - ref[c][m])
+        r = np.linalg.norm(ref[c][m])
+        assert d / max(r, 1e-30 * norm) <= REL_L2_F32, (name, d / r)
+    assert abs(w1 - w0) / w0 <= ENERGY_DRIFT_F32
+
+
 def test_512_two_step_equals_one_step_bitwise():
     """The bench's launch configuration (two-step kernel) against the one-step kernel at full size."""
     from paper_2504_09118_gb300 import Cavity
