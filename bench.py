@@ -499,7 +499,12 @@ def main():
                 "frac": round(achieved / peak, 4), "traffic": tr,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": alg_bytes, "mean_launch_us": round(launch_s * 1e6, 2),
-                "kernel": DOMINANT_KERNEL[BENCH_TUNING["kernel"]], "steps_per_launch": spl}
+                "kernel": DOMINANT_KERNEL[BENCH_TUNING["kernel"]], "steps_per_launch": spl,
+                # the same time against one HBM sweep per step (12 x storage + 1 bytes per cell-update):
+                # temporal blocking moves spl steps per sweep, so this exceeds the physical fraction
+                "per_cell_update": {"bytes": 12 * esz + ID_BYTES,
+                                    "achieved": round(alg_bytes * spl / launch_s / 1e9, 1),
+                                    "frac": round(alg_bytes * spl / launch_s / 1e9 / peak, 4)}}
 
     # end to end through the C ABI with host buffers: H2D of the fields + solve + D2H of the energy
     e2e = None
