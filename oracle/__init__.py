@@ -63,6 +63,9 @@ def _lib(omp: bool = False) -> ctypes.CDLL:
             lib.oracle_update_e.argtypes = [i, i, i] + [P] * 9
             lib.oracle_pec_e.argtypes = [i, i, i, P, P, P]
             lib.oracle_step.argtypes = [i, i, i, PP, PP, PP, i]
+            PI = ctypes.POINTER(ctypes.c_int)
+            lib.oracle_step_sources.argtypes = [i, i, i, PP, PP, PP, i, i, i, PI, PI, PI, PI, P, i,
+                                                ctypes.c_double]
             lib.oracle_energy.argtypes = [i, i, i, PP, PP, PP, ctypes.c_double]
             lib.oracle_energy.restype = ctypes.c_double
             lib.oracle_divergence.argtypes = [i, i, i, PP, PP, PP, P, P]
@@ -121,6 +124,21 @@ def step(f, ce, ch, nsteps: int, omp: bool = False):
     ce = full_coef(ce, f[0].shape)
     ch = full_coef(ch, f[0].shape)
     _lib(omp).oracle_step(nx, ny, nz, _pp(f), _pp(ce), _pp(ch), int(nsteps))
+    return f
+
+
+def step_sources(f, ce, ch, nsteps: int, sources, wave, n0: int = 0, dx: float = 1.0, omp: bool = False):
+    """oracle.step with point currents: sources = [(comp, i, j, k), ...] (comp 0..2 = Ex, Ey, Ez),
+    wave = array (nsrc, wave_len) of J^{n+1/2} for steps n0, n0 + 1, ... (Eq. 1 with J != 0)."""
+    nx, ny, nz = _dims(f)
+    ce = full_coef(ce, f[0].shape)
+    ch = full_coef(ch, f[0].shape)
+    src = np.asarray(sources, dtype=np.int32).reshape(-1, 4)
+    w = np.ascontiguousarray(np.asarray(wave, dtype=np.float64).reshape(len(src), -1))
+    cols = [np.ascontiguousarray(src[:, q]) for q in range(4)]
+    PI = ctypes.POINTER(ctypes.c_int)
+    _lib(omp).oracle_step_sources(nx, ny, nz, _pp(f), _pp(ce), _pp(ch), int(nsteps), int(n0), len(src),
+                                  *[c.ctypes.data_as(PI) for c in cols], _ptr(w), w.shape[1], float(dx))
     return f
 
 

@@ -9,7 +9,8 @@
  * Electromagnetics: A Compiler-Guided Approach with High-Level Tensor
  * Abstractions", arXiv 2504.09118):
  *   - Maxwell's curl equations with J = 0 (Sec. 2, Eq. 1), discretised on the
- *     Yee grid, staggered in space and time (Sec. 2, Eq. 2);
+ *     Yee grid, staggered in space and time (Sec. 2, Eq. 2); oracle_step_sources
+ *     adds point currents J, the term of Eq. 1 the benchmark sets to zero;
  *   - one time step = H update from curl E, H boundary handling, E update from
  *     curl H, E boundary handling (Sec. 2.1, Listing 1);
  *   - the per-component update written as a plain triple loop (Listing 2),
@@ -131,6 +132,29 @@ void oracle_step(int nx, int ny, int nz, double *const f[6],
     for (int n = 0; n < nsteps; ++n) {
         oracle_update_h(nx, ny, nz, f[3], f[4], f[5], f[0], f[1], f[2], ch[0], ch[1], ch[2]);
         oracle_update_e(nx, ny, nz, f[0], f[1], f[2], f[3], f[4], f[5], ce[0], ce[1], ce[2]);
+        oracle_pec_e(nx, ny, nz, f[0], f[1], f[2]);
+    }
+}
+
+/* As oracle_step, with point currents: Eq. 1 of Sec. 2 with J != 0 gives dE/dt = (curl H - J)/eps,
+ * so the E update of the step from E^n to E^{n+1} also subtracts ce * dx * J^{n+1/2} at each source.
+ * Source s drives component comp[s] (0 Ex, 1 Ey, 2 Ez) at canonical index (i[s], j[s], k[s]) with
+ * J^{n+1/2} = wave[s * wave_len + n] for the n-th step counted from n0 (0 once n >= wave_len).  The
+ * source term is added after the curl H update and before handle_E_edge. */
+void oracle_step_sources(int nx, int ny, int nz, double *const f[6],
+                         const double *const ce[3], const double *const ch[3], int nsteps, int n0,
+                         int nsrc, const int *comp, const int *si, const int *sj, const int *sk,
+                         const double *wave, int wave_len, double dx)
+{
+    for (int n = 0; n < nsteps; ++n) {
+        oracle_update_h(nx, ny, nz, f[3], f[4], f[5], f[0], f[1], f[2], ch[0], ch[1], ch[2]);
+        oracle_update_e(nx, ny, nz, f[0], f[1], f[2], f[3], f[4], f[5], ce[0], ce[1], ce[2]);
+        const int t = n0 + n;
+        for (int q = 0; q < nsrc; ++q) {
+            const double J = t < wave_len ? wave[(size_t)q * wave_len + t] : 0.0;
+            const int c = comp[q];
+            AT(f[c], si[q], sj[q], sk[q]) -= AT(ce[c], si[q], sj[q], sk[q]) * dx * J;
+        }
         oracle_pec_e(nx, ny, nz, f[0], f[1], f[2]);
     }
 }
