@@ -168,6 +168,29 @@ FDTD_API int fdtd_set_tuning(fdtd_ctx *ctx, const fdtd_tuning *t);
  * Requires fdtd_set_fields; synchronises the stream. */
 FDTD_API int fdtd_autotune(fdtd_ctx *ctx, int trial_steps, fdtd_tuning *out, double *ms_per_step);
 
+/* fdtd_set_sources - point currents, the J of Sec. 2, Eq. 1 (the benchmark's J = 0): in the step
+ * from E^n to E^{n+1} (n counted from the last fdtd_set_fields) the E update also subtracts
+ *   ce_c(i,j,k) * dx * wave[s * wave_len + n]          (0 once n >= wave_len)
+ * at source s: component comp[s] (0 Ex, 1 Ey, 2 Ez) at canonical index ijk[3s..3s+2], which must be
+ * an E position inside the cavity and not tangential to a face (ERR_ARG otherwise).  Sources at the
+ * same position add up.  nsrc = 0 removes them.  All arrays are host memory, copied.  While currents
+ * or probes are set, steps run the one-step kernel followed by one small launch for them (the
+ * two-step kernel has no point between its steps where J could enter).  Synchronises the stream. */
+FDTD_API int fdtd_set_sources(fdtd_ctx *ctx, int nsrc, const int *comp, const int *ijk, const float *wave,
+                              int wave_len);
+
+/* fdtd_set_probes - after every step, record component comp[p] (0..5 = Ex..Hz; an H value is
+ * H^{n+1/2}) at canonical index ijk[3p..3p+2] (0 <= i < nx, 0 <= j < ny, 0 <= k < nz), in physical
+ * units, into a device buffer of `capacity` steps starting with the next step; samples beyond the
+ * capacity are dropped.  nprobe = 0 removes them.  fdtd_set_fields restarts the recording.
+ * Synchronises the stream. */
+FDTD_API int fdtd_set_probes(fdtd_ctx *ctx, int nprobe, const int *comp, const int *ijk, int capacity);
+
+/* fdtd_get_probes - copy the probe buffer to host memory out[nprobe * capacity] (probe-major:
+ * out[p * capacity + n] is probe p after the n-th recorded step) and the number of recorded steps.
+ * Synchronises the stream. */
+FDTD_API int fdtd_get_probes(fdtd_ctx *ctx, float *out, int *nrecorded);
+
 /* fdtd_steps_done - steps taken since the last fdtd_set_fields (-1 for a NULL ctx). */
 FDTD_API long long fdtd_steps_done(const fdtd_ctx *ctx);
 

@@ -30,7 +30,8 @@ EXPORTS = (
     "fdtd_batch_create", "fdtd_batch_add", "fdtd_batch_remove", "fdtd_batch_step", "fdtd_batch_set_tuning",
     "fdtd_batch_size", "fdtd_batch_sync", "fdtd_batch_destroy", "fdtd_batch_last_error",
     "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static", "fdtd_batch_set_steps",
-    "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune",
+    "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune", "fdtd_set_sources", "fdtd_set_probes",
+    "fdtd_get_probes",
 )
 
 
@@ -101,6 +102,9 @@ def lib() -> ctypes.CDLL:
             L.fdtd_energy_static.argtypes = [i, i, i, d, d, vp, vp, vp, vp, vp]
             L.fdtd_autotune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d)]
             L.fdtd_batch_autotune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d)]
+            L.fdtd_set_sources.argtypes = [vp, i, vp, vp, vp, i]
+            L.fdtd_set_probes.argtypes = [vp, i, vp, vp, i]
+            L.fdtd_get_probes.argtypes = [vp, vp, ctypes.POINTER(i)]
             _LIB = L
         return _LIB
 
@@ -240,6 +244,36 @@ def fdtd_autotune(ctx, trial_steps: int = 16) -> tuple[dict, float]:
     ms = ctypes.c_double()
     _check(ctx, lib().fdtd_autotune(ctx, int(trial_steps), ctypes.byref(t), ctypes.byref(ms)))
     return _tuning_dict(t), float(ms.value)
+
+
+def fdtd_set_sources(ctx, sources, wave) -> None:
+    """sources: [(comp, i, j, k), ...] with comp 0..2 (Ex, Ey, Ez); wave: (nsrc, wave_len) current J of
+    each step (empty sources remove them)."""
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1, 4))
+    n = len(src)
+    comp = np.ascontiguousarray(src[:, 0])
+    ijk = np.ascontiguousarray(src[:, 1:])
+    w = np.ascontiguousarray(np.asarray(wave, dtype=np.float32).reshape(n, -1)) if n else np.zeros((0, 1), np.float32)
+    _check(ctx, lib().fdtd_set_sources(ctx, n, comp.ctypes.data if n else None, ijk.ctypes.data if n else None,
+                                       w.ctypes.data if n else None, int(w.shape[1])))
+
+
+def fdtd_set_probes(ctx, probes, capacity: int) -> None:
+    """probes: [(comp, i, j, k), ...] with comp 0..5 (Ex..Hz); capacity: steps recorded."""
+    pr = np.ascontiguousarray(np.asarray(probes, dtype=np.int32).reshape(-1, 4))
+    n = len(pr)
+    comp = np.ascontiguousarray(pr[:, 0])
+    ijk = np.ascontiguousarray(pr[:, 1:])
+    _check(ctx, lib().fdtd_set_probes(ctx, n, comp.ctypes.data if n else None, ijk.ctypes.data if n else None,
+                                      int(capacity)))
+
+
+def fdtd_get_probes(ctx, nprobe: int, capacity: int) -> np.ndarray:
+    """(nprobe, recorded steps) float32 array of the probed values."""
+    out = np.zeros((nprobe, capacity), dtype=np.float32)
+    n = ctypes.c_int()
+    _check(ctx, lib().fdtd_get_probes(ctx, out.ctypes.data, ctypes.byref(n)))
+    return out[:, :n.value]
 
 
 def fdtd_steps_done(ctx) -> int:

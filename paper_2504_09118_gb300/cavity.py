@@ -43,6 +43,20 @@ class Cavity:
     def tune(self, **kw):
         B.fdtd_set_tuning(self.handle, **kw)
 
+    def set_sources(self, sources, wave):
+        """Point currents (Eq. 1's J): sources [(comp 0..2, i, j, k), ...], wave (nsrc, steps)."""
+        B.fdtd_set_sources(self.handle, sources, wave)
+
+    def set_probes(self, probes, capacity: int):
+        """Record [(comp 0..5, i, j, k), ...] after every step, up to `capacity` steps."""
+        self._probes = (len(probes), int(capacity))
+        B.fdtd_set_probes(self.handle, probes, capacity)
+
+    def get_probes(self):
+        """(nprobe, recorded steps) array of the probed values (physical units)."""
+        n, cap = getattr(self, "_probes", (0, 0))
+        return B.fdtd_get_probes(self.handle, n, cap)
+
     def autotune(self, trial_steps: int = 16):
         """Pick the fastest kernel and launch shape on this cavity's state; returns (tuning, ms/step)."""
         return B.fdtd_autotune(self.handle, trial_steps)

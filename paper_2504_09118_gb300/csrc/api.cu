@@ -98,6 +98,13 @@ struct fdtd_ctx {
     fdtd_tuning tuning{};
     std::map<GraphKey, cudaGraphExec_t> graphs;
     int inject_us = 0;
+    // point currents and probes (fdtd_set_sources / fdtd_set_probes): run after every step
+    int nsrc = 0, wave_len = 0, nprobe = 0, probe_cap = 0;
+    long long probe_start = 0;         // step index of a probe buffer's first sample
+    int *d_src_comp = nullptr, *d_probe_comp = nullptr;
+    long long *d_src_off = nullptr, *d_probe_off = nullptr;
+    float *d_wave = nullptr, *d_probe_buf = nullptr;
+    long long *d_xclock = nullptr;     // device: steps taken since fdtd_set_fields (advanced by the extras launch)
     long long bytes = 0;
     fdtd_batch *batch = nullptr;
     std::string err;
@@ -566,6 +573,28 @@ int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind = 0) {
     return FDTD_OK;
 }
 
+bool extras_on(const fdtd_ctx *c) { return c->nsrc > 0 || c->nprobe > 0; }
+
+// The point-current / probe launch after a step that left the state in copy `copy`.
+int launch_extras_after(fdtd_ctx *c, int copy) {
+    ExtrasParams X{};
+    X.clock = c->d_xclock;
+    X.nsrc = c->nsrc;
+    X.wave_len = c->wave_len;
+    X.src_comp = c->d_src_comp;
+    X.src_off = c->d_src_off;
+    X.wave = c->d_wave;
+    X.dx = (float)c->dx;
+    X.nprobe = c->nprobe;
+    X.capacity = c->probe_cap;
+    X.probe_start = c->probe_start;
+    X.probe_comp = c->d_probe_comp;
+    X.probe_off = c->d_probe_off;
+    X.probe_buf = c->d_probe_buf;
+    CK(c, launch_extras(c->storage, make_desc(c, 0), copy, X, c->stream));
+    return FDTD_OK;
+}
+
 int check_status(fdtd_ctx *c, int *d_status, cudaStream_t s) {
     int h = 0;
     CK(c, cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -865,7 +894,8 @@ void fdtd_destroy(fdtd_ctx *c) {
     for (void *p : {(void *)c->id, (void *)c->table, (void *)c->inv_table, (void *)c->table_fused,
                     (void *)c->d_status, (void *)c->d_partial, (void *)c->d_out, (void *)c->d_stage,
                     (void *)c->d_max, (void *)c->d_maps, (void *)c->d_desc, (void *)c->tl[0].d,
-                    (void *)c->tl[1].d})
+                    (void *)c->tl[1].d, (void *)c->d_src_comp, (void *)c->d_src_off, (void *)c->d_wave,
+                    (void *)c->d_probe_comp, (void *)c->d_probe_off, (void *)c->d_probe_buf, (void *)c->d_xclock})
         pool_free(p, st);
     cudaStreamSynchronize(st);
     delete c;
@@ -920,6 +950,7 @@ int fdtd_autotune(fdtd_ctx *c, int trial_steps, fdtd_tuning *out, double *ms_per
     if (!c) return FDTD_ERR_ARG;
     if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
     if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; tune the batch");
+    if (extras_on(c)) return fail(c, FDTD_ERR_STATE, "tune before setting currents or probes");
     auto report = [&](const fdtd_tuning &t, double ms) {
         if (out) *out = t;
         if (ms_per_step) *ms_per_step = ms;
@@ -1048,6 +1079,10 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
         }
         CK(c, launch_pack(c->storage, d, 0, q, src, q >= 3 ? c->face[q - 3] : nullptr, c->stream));
     }
+    if (c->d_xclock) CK(c, cudaMemsetAsync(c->d_xclock, 0, sizeof(long long), c->stream));
+    if (c->d_probe_buf)
+        CK(c, cudaMemsetAsync(c->d_probe_buf, 0, sizeof(float) * (size_t)c->nprobe * c->probe_cap, c->stream));
+    c->probe_start = 0;
     CK(c, cudaStreamSynchronize(c->stream));
     c->cur = 0;
     c->steps = 0;
@@ -1080,16 +1115,24 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
     if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; step the batch");
     if (nsteps == 0) return FDTD_OK;
     const bool fused = use_fused(c);
-    const bool temporal = use_temporal(c);
+    const bool extras = extras_on(c);
+    // currents enter between the E update of one step and the H update of the next: one step per launch
+    const bool temporal = use_temporal(c) && !extras;
     if (fused)
         if (int rc = build_tiles(c, 0)) return rc;
     if (temporal)
         if (int rc = build_tiles(c, 1)) return rc;
+    // one launch from copy `parity` (fused kernels write copy parity ^ 1; the unfused one works in
+    // place on copy cur), then the point currents and probes of that step
+    auto step_launch = [&](int parity, int inj, int kind) -> int {
+        if (int rc = launch_one(c, parity, inj, kind)) return rc;
+        return extras ? launch_extras_after(c, fused ? parity ^ 1 : c->cur) : FDTD_OK;
+    };
     int left = nsteps;
     if (c->inject_us > 0 && fused) {
         const int inj = c->inject_us;
         c->inject_us = 0;
-        if (int rc = launch_one(c, c->cur, inj)) return rc;
+        if (int rc = step_launch(c->cur, inj, 0)) return rc;
         c->cur ^= 1;
         ++c->steps;
         --left;
@@ -1100,13 +1143,13 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
     const int per = temporal ? 2 : 1;
     const int K = 16;   // steps per graph
     if (c->tuning.use_graph && fused && c->stream != nullptr && left >= K) {
-        GraphKey key{K, c->cur, kind};
+        GraphKey key{K, c->cur, kind + (extras ? 2 : 0)};
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             cudaGraph_t g;
             CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             int rc = FDTD_OK;
-            for (int s = 0; s < K / per && !rc; ++s) rc = launch_one(c, c->cur ^ (s & 1), 0, kind);
+            for (int s = 0; s < K / per && !rc; ++s) rc = step_launch(c->cur ^ (s & 1), 0, kind);
             cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
             if (rc) return rc;
             CK(c, ee);
@@ -1123,16 +1166,121 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
     }
     if (temporal)
         for (; left >= 2; left -= 2) {
-            if (int rc = launch_one(c, c->cur, 0, 1)) return rc;
+            if (int rc = step_launch(c->cur, 0, 1)) return rc;
             c->cur ^= 1;
             c->steps += 2;
         }
     for (; left > 0; --left) {
-        if (int rc = launch_one(c, c->cur, 0)) return rc;
+        if (int rc = step_launch(c->cur, 0, 0)) return rc;
         if (fused) c->cur ^= 1;
         ++c->steps;
     }
     return FDTD_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Point currents and probes.
+static int free_extras(fdtd_ctx *c, bool sources, bool probes) {
+    CK(c, cudaStreamSynchronize(c->stream));   // no launch may still read the old arrays
+    drop_graphs(c->graphs);                   // graphs hold (or lack) the extras launch
+    if (sources) {
+        for (void *p : {(void *)c->d_src_comp, (void *)c->d_src_off, (void *)c->d_wave}) pool_free(p, c->stream);
+        c->d_src_comp = nullptr;
+        c->d_src_off = nullptr;
+        c->d_wave = nullptr;
+        c->nsrc = c->wave_len = 0;
+    }
+    if (probes) {
+        for (void *p : {(void *)c->d_probe_comp, (void *)c->d_probe_off, (void *)c->d_probe_buf})
+            pool_free(p, c->stream);
+        c->d_probe_comp = nullptr;
+        c->d_probe_off = nullptr;
+        c->d_probe_buf = nullptr;
+        c->nprobe = c->probe_cap = 0;
+    }
+    return FDTD_OK;
+}
+
+// The device step clock, started at the context's step count when the first current or probe is set.
+static int ensure_xclock(fdtd_ctx *c) {
+    if (c->d_xclock) return FDTD_OK;
+    CK(c, pool_alloc((void **)&c->d_xclock, sizeof(long long), c->stream));
+    const long long n = c->steps;
+    CK(c, cudaMemcpyAsync(c->d_xclock, &n, sizeof n, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FDTD_OK;
+}
+
+static int upload(fdtd_ctx *c, void **dst, const void *src, size_t bytes) {
+    CK(c, pool_alloc(dst, bytes, c->stream));
+    CK(c, cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return FDTD_OK;
+}
+
+int fdtd_set_sources(fdtd_ctx *c, int nsrc, const int *comp, const int *ijk, const float *wave, int wave_len) {
+    if (!c) return FDTD_ERR_ARG;
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
+    if (nsrc < 0 || (nsrc > 0 && (!comp || !ijk || !wave || wave_len < 1)))
+        return fail(c, FDTD_ERR_ARG, "bad source arguments");
+    std::vector<long long> off(nsrc);
+    for (int s = 0; s < nsrc; ++s) {
+        const int q = comp[s], i = ijk[3 * s], j = ijk[3 * s + 1], k = ijk[3 * s + 2];
+        // an E position inside the cavity and not tangential to a face (those stay 0: PEC)
+        const bool ok = (q == 0 && i >= 0 && i < c->nx && j >= 1 && j < c->ny && k >= 1 && k < c->nz) ||
+                        (q == 1 && i >= 1 && i < c->nx && j >= 0 && j < c->ny && k >= 1 && k < c->nz) ||
+                        (q == 2 && i >= 1 && i < c->nx && j >= 1 && j < c->ny && k >= 0 && k < c->nz);
+        if (!ok) return fail(c, FDTD_ERR_ARG, "source %d: component %d at (%d, %d, %d) is not an interior E position",
+                             s, q, i, j, k);
+        off[s] = (long long)k * c->pitch * c->ny + (long long)j * c->pitch + i;
+    }
+    if (int rc = free_extras(c, true, false)) return rc;
+    if (nsrc == 0) return FDTD_OK;
+    if (int rc = upload(c, (void **)&c->d_src_comp, comp, sizeof(int) * nsrc)) return rc;
+    if (int rc = upload(c, (void **)&c->d_src_off, off.data(), sizeof(long long) * nsrc)) return rc;
+    if (int rc = upload(c, (void **)&c->d_wave, wave, sizeof(float) * (size_t)nsrc * wave_len)) return rc;
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->nsrc = nsrc;
+    c->wave_len = wave_len;
+    return ensure_xclock(c);
+}
+
+int fdtd_set_probes(fdtd_ctx *c, int nprobe, const int *comp, const int *ijk, int capacity) {
+    if (!c) return FDTD_ERR_ARG;
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
+    if (nprobe < 0 || (nprobe > 0 && (!comp || !ijk || capacity < 1)))
+        return fail(c, FDTD_ERR_ARG, "bad probe arguments");
+    std::vector<long long> off(nprobe);
+    for (int p = 0; p < nprobe; ++p) {
+        const int q = comp[p], i = ijk[3 * p], j = ijk[3 * p + 1], k = ijk[3 * p + 2];
+        if (q < 0 || q > 5 || i < 0 || i >= c->nx || j < 0 || j >= c->ny || k < 0 || k >= c->nz)
+            return fail(c, FDTD_ERR_ARG, "probe %d: component %d at (%d, %d, %d) is outside [0,nx)x[0,ny)x[0,nz)",
+                        p, q, i, j, k);
+        off[p] = (long long)k * c->pitch * c->ny + (long long)j * c->pitch + i;
+    }
+    if (int rc = free_extras(c, false, true)) return rc;
+    if (nprobe == 0) return FDTD_OK;
+    if (int rc = upload(c, (void **)&c->d_probe_comp, comp, sizeof(int) * nprobe)) return rc;
+    if (int rc = upload(c, (void **)&c->d_probe_off, off.data(), sizeof(long long) * nprobe)) return rc;
+    CK(c, pool_alloc((void **)&c->d_probe_buf, sizeof(float) * (size_t)nprobe * capacity, c->stream));
+    CK(c, cudaMemsetAsync(c->d_probe_buf, 0, sizeof(float) * (size_t)nprobe * capacity, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->nprobe = nprobe;
+    c->probe_cap = capacity;
+    c->probe_start = c->steps;
+    return ensure_xclock(c);
+}
+
+int fdtd_get_probes(fdtd_ctx *c, float *out, int *nrecorded) {
+    if (!c || !out || !nrecorded) return fail(c, FDTD_ERR_ARG, "NULL argument");
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
+    if (c->nprobe == 0) return fail(c, FDTD_ERR_STATE, "no probes are set");
+    long long n = 0;
+    CK(c, cudaMemcpyAsync(&n, c->d_xclock, sizeof n, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(out, c->d_probe_buf, sizeof(float) * (size_t)c->nprobe * c->probe_cap,
+                          cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *nrecorded = (int)std::max<long long>(0, std::min<long long>(c->probe_cap, n - c->probe_start));
+    return check_status(c, c->d_status, c->stream);
 }
 
 int fdtd_sync(fdtd_ctx *c) {
@@ -1221,6 +1369,7 @@ int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *c) {
     if (!c->has_fields) return bfail(b, FDTD_ERR_STATE, "context has no fields yet");
     if (c->storage != b->storage) return bfail(b, FDTD_ERR_ARG, "storage mismatch");
     if (c->coef_mode == COEF_FULL) return bfail(b, FDTD_ERR_ARG, "per-position coefficient arrays are not batched");
+    if (extras_on(c)) return bfail(b, FDTD_ERR_ARG, "contexts with currents or probes are not batched");
     // the member's pending work (set_fields) happened-before: its stream was synchronised by that call
     b->members.push_back({c, c->cur, b->step, b->launches, LLONG_MAX, c->steps, 0});
     c->batch = b;

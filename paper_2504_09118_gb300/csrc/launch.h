@@ -40,6 +40,22 @@ int fused_smem_bytes(int storage, int tile_y, int stages);
 cudaError_t fused_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
 cudaError_t launch_fused_step(int storage, const FusedLaunch &L, cudaStream_t s);
 // *counter += 1 on the stream (advances a batch's device launch counter after each step).
+// Point currents and probes applied after a step (k_extras.cu).
+struct ExtrasParams {
+    long long *clock;          // device: steps taken since fdtd_set_fields; advanced by the launch
+    int nsrc, wave_len;
+    const int *src_comp;       // 0..2 (Ex, Ey, Ez)
+    const long long *src_off;  // active-array offsets
+    const float *wave;         // nsrc x wave_len: J^{n+1/2} of step n
+    float dx;
+    int nprobe, capacity;
+    long long probe_start;     // step index of the probe buffer's first sample
+    const int *probe_comp;     // 0..5
+    const long long *probe_off;
+    float *probe_buf;          // nprobe x capacity, physical units
+};
+cudaError_t launch_extras(int storage, const CavityDesc &d, int copy, const ExtrasParams &X, cudaStream_t s);
+
 // Adds inc to the device step clock of a batch (one thread; ordered after the launch it follows).
 cudaError_t launch_step_counter(long long *counter, int inc, cudaStream_t s);
 // Two-step (temporal blocking) kernel: output tile width along x, shared memory, occupancy, launch.
