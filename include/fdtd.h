@@ -70,7 +70,8 @@ enum fdtd_status {
 
 /* Step kernels (fdtd_tuning.kernel). */
 enum fdtd_kernel {
-    FDTD_KERNEL_AUTO = 0,    /* fused kernel with the library's default tile */
+    FDTD_KERNEL_AUTO = 0,    /* TEMPORAL with 12-row tiles where it applies (else FUSED; SIMPLE for
+                                per-position coefficient arrays); fdtd_autotune picks by timing */
     FDTD_KERNEL_SIMPLE = 1,  /* two launches per step (H, then E), one thread per cell; unfused baseline */
     FDTD_KERNEL_FUSED = 2,   /* one TMA-pipelined launch per step: H then E fused in a z-march */
     FDTD_KERNEL_TEMPORAL = 3 /* two steps per launch (temporal blocking); an odd count ends with one FUSED step */
@@ -79,8 +80,9 @@ enum fdtd_kernel {
 /* Launch configuration of the step kernel; zero fields take the default. */
 typedef struct fdtd_tuning {
     int kernel;       /* enum fdtd_kernel */
-    int tile_y;       /* fused: cells per tile along y (4, 8 or 16; TEMPORAL: 8 or 12); x tile is 64
-                         cells (TEMPORAL: 60 for FP32, 56 for 16-bit storage) */
+    int tile_y;       /* fused: cells per tile along y (FUSED: 4, 8 or 16; TEMPORAL: 8 or 12; AUTO: any
+                         of these, each kernel taking its default when the value is not one of its
+                         own); x tile is 64 cells (TEMPORAL: 60 for FP32, 56 for 16-bit storage) */
     int zchunk;       /* fused: planes per tile along z (>= 1); 0 = choose for load balance */
     int ctas_per_sm;  /* fused: persistent CTAs per SM (1 or 2); 0 = as many as fit */
     int stages;       /* fused: TMA pipeline depth in planes (3..8, lowered to fit shared memory); 0 = default */

@@ -304,8 +304,8 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0) {
     if (kind == 0)
         s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 16) ? t.tile_y : 8;
     else
-        s.tile_y = (t.tile_y == 8 || t.tile_y == 12) ? t.tile_y : 8;
-    s.stages = (t.stages >= 3 && t.stages <= 8) ? t.stages : 4;
+        s.tile_y = (t.tile_y == 8 || t.tile_y == 12) ? t.tile_y : 12;
+    s.stages = (t.stages >= 3 && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : 6);
     auto smem = [&](int st) {
         return kind == 0 ? fused_smem_bytes(storage, s.tile_y, st) : fused2_smem_bytes(storage, s.tile_y, st);
     };
@@ -546,7 +546,10 @@ bool use_fused(const fdtd_ctx *c) {
     return c->coef_mode != COEF_FULL && c->tuning.kernel != FDTD_KERNEL_SIMPLE;
 }
 
-bool use_temporal(const fdtd_ctx *c) { return use_fused(c) && c->tuning.kernel == FDTD_KERNEL_TEMPORAL; }
+// AUTO takes the two-step kernel: faster than the one-step kernel at every size measured
+bool use_temporal(const fdtd_ctx *c) {
+    return use_fused(c) && (c->tuning.kernel == FDTD_KERNEL_TEMPORAL || c->tuning.kernel == FDTD_KERNEL_AUTO);
+}
 
 // One launch of a single context (no graph): kind 0 advances one step, kind 1 two steps.
 int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind = 0) {
@@ -909,8 +912,10 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
     fdtd_tuning n{};
     if (t) n = *t;
     if (n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
-    if (n.kernel == FDTD_KERNEL_TEMPORAL ? (n.tile_y && n.tile_y != 8 && n.tile_y != 12)
-                                         : (n.tile_y && n.tile_y != 4 && n.tile_y != 8 && n.tile_y != 16))
+    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16, ty_two = n.tile_y == 8 || n.tile_y == 12;
+    if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL ? ty_two
+                      : n.kernel == FDTD_KERNEL_AUTO   ? (ty_one || ty_two)
+                                                       : ty_one))
         return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (8 or 12 for the two-step kernel)");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return fail(c, FDTD_ERR_ARG, "stages must be in [3, 8]");
     if (n.zchunk < 0 || n.ctas_per_sm < 0) return fail(c, FDTD_ERR_ARG, "negative tuning value");
@@ -1424,8 +1429,10 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t) {
     if (t) n = *t;
     if (n.kernel == FDTD_KERNEL_SIMPLE || n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL)
         return bfail(b, FDTD_ERR_ARG, "batches use the fused kernels (FUSED or TEMPORAL)");
-    if (n.kernel == FDTD_KERNEL_TEMPORAL ? (n.tile_y && n.tile_y != 8 && n.tile_y != 12)
-                                         : (n.tile_y && n.tile_y != 4 && n.tile_y != 8 && n.tile_y != 16))
+    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16, ty_two = n.tile_y == 8 || n.tile_y == 12;
+    if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL ? ty_two
+                      : n.kernel == FDTD_KERNEL_AUTO   ? (ty_one || ty_two)
+                                                       : ty_one))
         return bfail(b, FDTD_ERR_ARG, "bad tile_y");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return bfail(b, FDTD_ERR_ARG, "bad stages");
     b->tuning = n;
@@ -1443,7 +1450,9 @@ static void batch_free_retired_graphs(fdtd_batch *b) {   // call only when the b
     b->retired_graphs.clear();
 }
 
-static int batch_kind(const fdtd_batch *b) { return b->tuning.kernel == FDTD_KERNEL_TEMPORAL ? 1 : 0; }
+static int batch_kind(const fdtd_batch *b) {
+    return b->tuning.kernel == FDTD_KERNEL_TEMPORAL || b->tuning.kernel == FDTD_KERNEL_AUTO ? 1 : 0;
+}
 
 // Rebuild the packed tile list (asynchronously on the batch stream: the upload runs after the
 // launches already enqueued, and the old buffer is released in stream order).
