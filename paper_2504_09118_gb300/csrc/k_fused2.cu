@@ -75,7 +75,9 @@ template <typename T, int TY> __host__ __device__ constexpr int smem2_bytes(int 
 }
 template <int TY> __host__ __device__ constexpr int threads2() { return (TY + 4) * 32; }
 
-template <typename T, int TY>
+// BATCH: tiles carry their member's stop clock (skip finished members, one-step stores for a member
+// with one step left); a single cavity's launch compiles without those checks.
+template <typename T, int TY, bool BATCH>
 __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fused2Params P) {
     using G = Geom2<T>;
     constexpr int HX = G::HX, BX = G::BX, W = G::W;
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
     const int t_step = P.first ? 1 : (int)gridDim.x;
     // Steps a tile takes in this launch: min(launch_steps, stop - clock); a batch member with one step
     // left stores its level-1 result, a finished member's tiles are skipped (producer and consumers alike).
-    const long long clock = P.step ? *P.step : 0;
+    const long long clock = BATCH ? *P.step : 0;
 
     if (threadIdx.x == 0) {
         *abort_flag = 0;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         uint32_t rnd = 0;
         bool ok = true;
         for (int t = t_begin; t < t_end && ok; t += t_step) {
-            if (__ldg(&P.recs[t].stop) <= clock) continue;   // member already took its last step
+            if (BATCH && __ldg(&P.recs[t].stop) <= clock) continue;   // member already took its last step
             TileRec *rec = &recs[m++ % NTR2];
             int kb = 0, klast = 0;
             for (int k = 0;; ++k) {
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
     const float2 zero2 = make_float2(0.f, 0.f);
 
     for (int t = t_begin; t < t_end; t += t_step) {
-        if (__ldg(&P.recs[t].stop) <= clock) continue;   // same skip rule as the producer
+        if (BATCH && __ldg(&P.recs[t].stop) <= clock) continue;   // same skip rule as the producer
         bool ok = wait_full(sa, pa);
         if (bar_sync_or(2, NCT, !ok || *abort_flag != 0)) {
             if (threadIdx.x == 0) atomicOr(P.status, STATUS_TIMEOUT);
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         const bool out_row = r >= 2 && r < TY + 2 && gj < ny;      // level-2 outputs of this row are stored
         const bool out_a = lane >= 1 && 2 * lane - 2 < W && gi < nx; // both cells share the column window
         const int kb = kz0 > 2 ? kz0 - 2 : 0;
-        const bool level1_only = P.launch_steps == 1 || rec->stop - clock == 1;
+        const bool level1_only = BATCH && (P.launch_steps == 1 || rec->stop - clock == 1);
 
         auto at = [&](const T *base, int f, int xx, int yy) { return base + f * FE + yy * BX + xx; };
         auto coef = [&](uint32_t ip, int which, float4 &a, float4 &b) {   // which: 0 ce, 1 ch
@@ -248,6 +250,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         float2 h2px = zero2, h2py = zero2;                 // H2(j-2) (Hx, Hy)
         uint32_t idprev = 0;                               // material ids of plane j-1
 
+#pragma unroll 2   // consecutive planes renamed instead of copied (the carried z neighbours)
         for (int k = kb; k <= kz1; ++k) {
             int sb = sa + 1;
             uint32_t pb = pa;
@@ -315,16 +318,16 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 if (!vb) { e1x.y = 0.f; e1y.y = 0.f; e1z.y = 0.f; }
                 *reinterpret_cast<float2 *>(e1cur + pr * PW + pc) = e1x;
                 *reinterpret_cast<float2 *>(e1cur + PF + pr * PW + pc) = e1z;
-                const long long g1 = (long long)k * plane + (long long)gj * pitch + gi;
-                if (level1_only && out_row && out_a && k >= kz0 && k < kz1 &&
-                    store_ok(P.status, g1, 2, plane * nz)) {   // one step: (H1, E1) is the result
-                    const long long g = g1;
-                    Pair<T>::st(dst[0] + g, e1x.x, e1x.y);
-                    Pair<T>::st(dst[1] + g, e1y.x, e1y.y);
-                    Pair<T>::st(dst[2] + g, e1z.x, e1z.y);
-                    Pair<T>::st(dst[3] + g, h1x_.x, h1x_.y);
-                    Pair<T>::st(dst[4] + g, h1y_.x, h1y_.y);
-                    Pair<T>::st(dst[5] + g, h1z_.x, h1z_.y);
+                if (level1_only && out_row && out_a && k >= kz0 && k < kz1) {   // one step: (H1, E1) is the result
+                    const long long g = (long long)k * plane + (long long)gj * pitch + gi;
+                    if (store_ok(P.status, g, 2, plane * nz)) {
+                        Pair<T>::st(dst[0] + g, e1x.x, e1x.y);
+                        Pair<T>::st(dst[1] + g, e1y.x, e1y.y);
+                        Pair<T>::st(dst[2] + g, e1z.x, e1z.y);
+                        Pair<T>::st(dst[3] + g, h1x_.x, h1x_.y);
+                        Pair<T>::st(dst[4] + g, h1y_.x, h1y_.y);
+                        Pair<T>::st(dst[5] + g, h1z_.x, h1z_.y);
+                    }
                 }
             }
             asm volatile("bar.sync 1, %0;" ::"r"(NCT) : "memory");
@@ -401,10 +404,10 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
     }
 }
 
-template <typename T, int TY>
+template <typename T, int TY, bool BATCH>
 cudaError_t launch2_typed(const FusedLaunch &L, cudaStream_t s) {
     const int smem = smem2_bytes<T, TY>(L.stages);
-    auto kern = fused2_step_kernel<T, TY>;
+    auto kern = fused2_step_kernel<T, TY, BATCH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     Fused2Params P;
@@ -424,7 +427,7 @@ cudaError_t launch2_typed(const FusedLaunch &L, cudaStream_t s) {
 template <typename T, int TY>
 cudaError_t occupancy2_typed(int stages, int *n) {
     const int smem = smem2_bytes<T, TY>(stages);
-    auto kern = fused2_step_kernel<T, TY>;
+    auto kern = fused2_step_kernel<T, TY, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, threads2<TY>(), smem);
@@ -464,7 +467,10 @@ cudaError_t launch_fused2_step(int storage, const FusedLaunch &L, cudaStream_t s
     if (L.ntiles <= 0) return cudaSuccess;
     if (L.stages < 3 || L.stages > 8) return cudaErrorInvalidValue;
     cudaError_t e = cudaErrorInvalidValue;
-    FDTD_DISPATCH2(storage, L.tile_y, e = launch2_typed<T, TY>(L, s));
+    if (L.step || L.launch_steps == 1)   // a batch launch (or a one-step store launch)
+        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, true>(L, s)));
+    else
+        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false>(L, s)));
     return e;
 }
 
