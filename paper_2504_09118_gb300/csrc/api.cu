@@ -275,6 +275,18 @@ int encode_maps(fdtd_ctx *c, int set, int box_y) {
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return fail(c, FDTD_ERR_CUDA, "tensor map encode failed (%d)", (int)r);
         }
+    if (set == 1)   // two-step kernel: slot cp * 6 holds one 4-D map over the copy's six arrays
+        for (int cp = 0; cp < 2; ++cp) {
+            cuuint64_t gdim4[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, 6};
+            cuuint64_t gstr4[3] = {(cuuint64_t)c->pitch * es, (cuuint64_t)c->pitch * c->ny * es,
+                                   (cuuint64_t)c->arr_elems * es};
+            cuuint32_t box4[4] = {(cuuint32_t)bx, (cuuint32_t)box_y, 1, 6};
+            cuuint32_t estr4[4] = {1, 1, 1, 1};
+            CUresult r = enc(&maps[cp * 6], dt, 4, c->fields[cp][0], gdim4, gstr4, box4, estr4,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(c, FDTD_ERR_CUDA, "4-D tensor map encode failed (%d)", (int)r);
+        }
     if (c->id) {
         cuuint64_t gstr[2] = {(cuuint64_t)c->pitch, (cuuint64_t)c->pitch * c->ny};
         cuuint32_t box[3] = {(cuuint32_t)(kTileX + 16), (cuuint32_t)box_y, 1};
@@ -773,12 +785,14 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
     };
     cudaError_t e;
     const size_t es = esize(storage);
-    for (int cp = 0; cp < 2; ++cp)
-        for (int f = 0; f < 6; ++f) {
-            if ((e = dmalloc(c, &c->fields[cp][f], c->arr_elems * es)) != cudaSuccess) return cfail("field alloc", e);
-            if ((e = cudaMemsetAsync(c->fields[cp][f], 0, c->arr_elems * es, c->stream)) != cudaSuccess)
-                return cfail("memset", e);
-        }
+    // each copy's six arrays in one allocation, arr_elems apart, so that one 4-D tensor map (x, y, z,
+    // field) covers all of them (the two-step kernel loads a unit's six boxes with one TMA instruction)
+    for (int cp = 0; cp < 2; ++cp) {
+        if ((e = dmalloc(c, &c->fields[cp][0], 6 * c->arr_elems * es)) != cudaSuccess) return cfail("field alloc", e);
+        if ((e = cudaMemsetAsync(c->fields[cp][0], 0, 6 * c->arr_elems * es, c->stream)) != cudaSuccess)
+            return cfail("memset", e);
+        for (int f = 1; f < 6; ++f) c->fields[cp][f] = static_cast<char *>(c->fields[cp][0]) + f * c->arr_elems * es;
+    }
     const size_t nface[3] = {(size_t)ny * nz, (size_t)nx * nz, (size_t)nx * ny};
     for (int q = 0; q < 3; ++q) {
         if ((e = dmalloc(c, (void **)&c->face[q], nface[q] * 4)) != cudaSuccess) return cfail("face alloc", e);
@@ -888,7 +902,7 @@ void fdtd_destroy(fdtd_ctx *c) {
     drop_graphs(c->graphs);
     cudaStream_t st = c->stream;
     for (int cp = 0; cp < 2; ++cp)
-        for (int f = 0; f < 6; ++f) pool_free(c->fields[cp][f], st);
+        pool_free(c->fields[cp][0], st);   // the six arrays share one allocation
     for (int q = 0; q < 3; ++q) {
         pool_free(c->face[q], st);
         pool_free(c->face_ch[q], st);

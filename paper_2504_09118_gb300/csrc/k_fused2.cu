@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
     using G = Geom2<T>;
     constexpr int HX = G::HX, BX = G::BX, W = G::W;
     constexpr int FB = box_bytes<T, TY>(), FS = box_stride<T, TY>(), FE = FS / (int)sizeof(T);
+    static_assert(FS == FB, "field boxes must be whole 128-byte blocks: one 4-D load writes them back to back");
     constexpr int NCW = TY + 3, NCT = NCW * 32;
     constexpr int PF = plane_floats<TY>();
 
@@ -159,10 +160,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                     if (tma_x_ok(P.status, rec->x0 - HX, (int)sizeof(T)) &&
                         (!has_id || tma_x_ok(P.status, rec->id_x0, 1))) {
                         mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? idbox_bytes<TY>() : 0));
-                        const CUtensorMap *mp = rec->maps + src_copy * 6;
-#pragma unroll
-                        for (int f = 0; f < 6; ++f)
-                            tma_load_3d(dst + f * FS, mp + f, rec->x0 - HX, rec->y0 - 2, kk, &full[s]);
+                        // the six field boxes in one load: a 4-D box (x, y, plane, field) lands as six
+                        // consecutive FB-byte boxes (FS == FB)
+                        tma_load_4d(dst, rec->maps + src_copy * 6, rec->x0 - HX, rec->y0 - 2, kk, 0, &full[s]);
                         if (has_id)
                             tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
                     } else {
