@@ -136,57 +136,94 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
-// Per block, in a fixed grid-stride order over the cells (far-face H appended):
+// FP32 sum with Kahan compensation (Kahan 1965): the rounding error of every addition is carried
+// into the next, so a lane's partial over one row is exact to a few units in the last place
+// however many cells it holds; partials are folded into FP64 once per row.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double take() {
+        const double r = (double)s - (double)c;
+        s = c = 0.f;
+        return r;
+    }
+};
+
+// Per block, in a fixed order (warps over rows, lanes along x; far-face H appended):
 //   WHAT == 0: energy sum  E^2/ce + H^2/ch - H curl E   (W without the 1/2 dt/dx factor)
 //   WHAT == 1: sum of divE^2 over interior nodes and of divH^2 over cells.
 // Each cell's terms are formed in FP32 with precomputed reciprocal coefficients (relative
-// error of order 2^-23 per term, unbiased) and accumulated in FP64.
+// error of order 2^-23 per term, unbiased), summed per lane and row with Kahan compensation,
+// and accumulated in FP64 (GB300's FP64 rate is a small fraction of its FP32 rate, so FP64
+// work is kept to one addition per lane and row).
 template <typename T, int WHAT>
 __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const CavityDesc d, int copy, double *partial) {
     __shared__ double sh[kRedThreads / 32];
+    __shared__ float itab[8 * kMaxTable];   // reciprocal coefficient table (material-id mode)
     const int nx = d.nx, ny = d.ny, nz = d.nz;
     const long long P = d.pitch, Z = d.plane;
-    const long long ncell = (long long)nx * ny * nz;
     double s0 = 0.0, s1 = 0.0;
+    Kahan k0, k1;
+    const bool ids = d.coef_mode == COEF_ID8;
+    if (ids)
+        for (int e = threadIdx.x; e < 8 * d.ntab; e += kRedThreads) itab[e] = d.inv_table[e];
+    __syncthreads();
     auto F = [&](int f, long long o) -> float { return ld_field<T>(d, copy, f, o); };
-    auto IC = [&](int c, long long o) -> float { return ld_inv_coef(d, c, o); };
+    // 1/ce (c = 0..2) or 1/ch (c = 3..5) at offset o; `m` is the cell's material id in id mode
+    auto ICm = [&](int c, long long o, int m) -> float {
+        if (ids) return itab[8 * m + (c < 3 ? c : c + 1)];
+        return ld_inv_coef(d, c, o);
+    };
+    auto IC = [&](int c, long long o) -> float { return ICm(c, o, ids ? d.id[o] : 0); };
     auto face_inv_ch = [&](int c, long long fi) -> float {
         return d.coef_mode == COEF_SCALAR ? d.inv_ch[c] : 1.0f / d.face_ch[c][fi];
     };
-    for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < ncell;
-         n += (long long)gridDim.x * kRedThreads) {
-        const int i = (int)(n % nx);
-        const long long t = n / nx;
-        const int j = (int)(t % ny), k = (int)(t / ny);
-        const long long o = (long long)k * Z + (long long)j * P + i;
-        const float ex = F(0, o), ey = F(1, o), ez = F(2, o), hx = F(3, o), hy = F(4, o), hz = F(5, o);
-        if (WHAT == 0) {
-            const float ex_j1 = j + 1 < ny ? F(0, o + P) : 0.f, ex_k1 = k + 1 < nz ? F(0, o + Z) : 0.f;
-            const float ey_i1 = i + 1 < nx ? F(1, o + 1) : 0.f, ey_k1 = k + 1 < nz ? F(1, o + Z) : 0.f;
-            const float ez_i1 = i + 1 < nx ? F(2, o + 1) : 0.f, ez_j1 = j + 1 < ny ? F(2, o + P) : 0.f;
-            const float cx = (ez_j1 - ez) - (ey_k1 - ey);
-            const float cy = (ex_k1 - ex) - (ez_i1 - ez);
-            const float cz = (ey_i1 - ey) - (ex_j1 - ex);
-            const float e = ex * ex * IC(0, o) + ey * ey * IC(1, o) + ez * ez * IC(2, o);
-            const float h = (hx * hx * IC(3, o) - hx * cx) + (hy * hy * IC(4, o) - hy * cy) +
-                            (hz * hz * IC(5, o) - hz * cz);
-            s0 += (double)e + (double)h;
-        } else {
-            if (i >= 1 && j >= 1 && k >= 1) {
-                const float de = (ex * IC(0, o) - F(0, o - 1) * IC(0, o - 1)) +
-                                 (ey * IC(1, o) - F(1, o - P) * IC(1, o - P)) +
-                                 (ez * IC(2, o) - F(2, o - Z) * IC(2, o - Z));
-                s0 += (double)de * de;
+    // one warp per (j, k) row, lanes along x: coalesced loads and one division per row, not per cell
+    const int lane = threadIdx.x & 31;
+    const long long nrows = (long long)ny * nz;
+    const long long nwarps = ((long long)gridDim.x * kRedThreads) >> 5;
+    for (long long r = ((long long)blockIdx.x * kRedThreads + threadIdx.x) >> 5; r < nrows; r += nwarps) {
+        const int j = (int)(r % ny), k = (int)(r / ny);
+        for (int i = lane; i < nx; i += 32) {
+            const long long o = (long long)k * Z + (long long)j * P + i;
+            const float ex = F(0, o), ey = F(1, o), ez = F(2, o), hx = F(3, o), hy = F(4, o), hz = F(5, o);
+            const int m = ids ? d.id[o] : 0;
+            if (WHAT == 0) {
+                const float ex_j1 = j + 1 < ny ? F(0, o + P) : 0.f, ex_k1 = k + 1 < nz ? F(0, o + Z) : 0.f;
+                const float ey_i1 = i + 1 < nx ? F(1, o + 1) : 0.f, ey_k1 = k + 1 < nz ? F(1, o + Z) : 0.f;
+                const float ez_i1 = i + 1 < nx ? F(2, o + 1) : 0.f, ez_j1 = j + 1 < ny ? F(2, o + P) : 0.f;
+                const float cx = (ez_j1 - ez) - (ey_k1 - ey);
+                const float cy = (ex_k1 - ex) - (ez_i1 - ez);
+                const float cz = (ey_i1 - ey) - (ex_j1 - ex);
+                const float e = ex * ex * ICm(0, o, m) + ey * ey * ICm(1, o, m) + ez * ez * ICm(2, o, m);
+                const float h = (hx * hx * ICm(3, o, m) - hx * cx) + (hy * hy * ICm(4, o, m) - hy * cy) +
+                                (hz * hz * ICm(5, o, m) - hz * cz);
+                k0.add(e);
+                k0.add(h);
+            } else {
+                if (i >= 1 && j >= 1 && k >= 1) {
+                    const float de = (ex * ICm(0, o, m) - F(0, o - 1) * IC(0, o - 1)) +
+                                     (ey * ICm(1, o, m) - F(1, o - P) * IC(1, o - P)) +
+                                     (ez * ICm(2, o, m) - F(2, o - Z) * IC(2, o - Z));
+                    k0.add(de * de);
+                }
+                const float bx1 = i + 1 < nx ? F(3, o + 1) * IC(3, o + 1)
+                                             : d.face[0][(long long)k * ny + j] * face_inv_ch(0, (long long)k * ny + j);
+                const float by1 = j + 1 < ny ? F(4, o + P) * IC(4, o + P)
+                                             : d.face[1][(long long)k * nx + i] * face_inv_ch(1, (long long)k * nx + i);
+                const float bz1 = k + 1 < nz ? F(5, o + Z) * IC(5, o + Z)
+                                             : d.face[2][(long long)j * nx + i] * face_inv_ch(2, (long long)j * nx + i);
+                const float dh = (bx1 - hx * ICm(3, o, m)) + (by1 - hy * ICm(4, o, m)) + (bz1 - hz * ICm(5, o, m));
+                k1.add(dh * dh);
             }
-            const float bx1 = i + 1 < nx ? F(3, o + 1) * IC(3, o + 1)
-                                         : d.face[0][(long long)k * ny + j] * face_inv_ch(0, (long long)k * ny + j);
-            const float by1 = j + 1 < ny ? F(4, o + P) * IC(4, o + P)
-                                         : d.face[1][(long long)k * nx + i] * face_inv_ch(1, (long long)k * nx + i);
-            const float bz1 = k + 1 < nz ? F(5, o + Z) * IC(5, o + Z)
-                                         : d.face[2][(long long)j * nx + i] * face_inv_ch(2, (long long)j * nx + i);
-            const float dh = (bx1 - hx * IC(3, o)) + (by1 - hy * IC(4, o)) + (bz1 - hz * IC(5, o));
-            s1 += (double)dh * dh;
         }
+        s0 += k0.take();
+        s1 += k1.take();
     }
     if (WHAT == 0) {
         // constant far-face normal H: curl E vanishes there, so its energy term is H^2/ch
