@@ -84,6 +84,9 @@ struct fdtd_ctx {
     int *d_status = nullptr;
     double *d_partial = nullptr, *d_out = nullptr;
     float *d_stage = nullptr;    // canonical staging buffer for host transfers (lazy)
+    float *d_stage2 = nullptr;   // second staging buffer: host loads copy one field while packing another
+    cudaStream_t copy_stream = nullptr;   // host-to-device copies of fdtd_set_fields (lazy)
+    cudaEvent_t staged[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr};
     unsigned *d_max = nullptr;
     CUtensorMap *d_maps = nullptr;          // kMapSets x kMapsPerCavity
     std::vector<CUtensorMap> host_maps[kMapSets];
@@ -631,6 +634,20 @@ int ensure_stage(fdtd_ctx *c) {
     return FDTD_OK;
 }
 
+// Two staging buffers, a copy stream and its events for pipelined host loads.
+int ensure_stage2(fdtd_ctx *c) {
+    if (int rc = ensure_stage(c)) return rc;
+    if (c->d_stage2) return FDTD_OK;
+    const size_t n = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+    CK(c, dmalloc(c, (void **)&c->d_stage2, n * sizeof(float)));
+    CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        CK(c, cudaEventCreateWithFlags(&c->staged[b], cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->packed[b], cudaEventDisableTiming));
+    }
+    return FDTD_OK;
+}
+
 // Compress per-position coefficients: one byte per active cell + table when <= 256 distinct tuples.
 struct Tuple {
     float v[6];
@@ -914,7 +931,16 @@ void fdtd_destroy(fdtd_ctx *c) {
                     (void *)c->tl[1].d, (void *)c->d_src_comp, (void *)c->d_src_off, (void *)c->d_wave,
                     (void *)c->d_probe_comp, (void *)c->d_probe_off, (void *)c->d_probe_buf, (void *)c->d_xclock})
         pool_free(p, st);
+    pool_free(c->d_stage2, st);
     cudaStreamSynchronize(st);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (c->staged[b]) cudaEventDestroy(c->staged[b]);
+        if (c->packed[b]) cudaEventDestroy(c->packed[b]);
+    }
     delete c;
 }
 
@@ -1090,13 +1116,25 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
     }
     if (int rc = upload_desc(c)) return rc;
     CavityDesc d = make_desc(c, 0);
-    for (int q = 0; q < 6; ++q) {
-        const float *src = f[q];
-        if (!on_device) {
-            CK(c, cudaMemcpyAsync(c->d_stage, f[q], n * 4, cudaMemcpyHostToDevice, c->stream));
-            src = c->d_stage;
+    if (on_device) {
+        for (int q = 0; q < 6; ++q)
+            CK(c, launch_pack(c->storage, d, 0, q, f[q], q >= 3 ? c->face[q - 3] : nullptr, c->stream));
+    } else {
+        // host fields: field q is copied into staging buffer q & 1 on the copy stream while the
+        // previous field is packed on the context's stream (the copy waits until buffer q & 1 is free)
+        if (int rc = ensure_stage2(c)) return rc;
+        CK(c, cudaEventRecord(c->packed[0], c->stream));   // orders the copies after earlier work
+        CK(c, cudaEventRecord(c->packed[1], c->stream));
+        for (int q = 0; q < 6; ++q) {
+            const int b = q & 1;
+            float *stage = b ? c->d_stage2 : c->d_stage;
+            CK(c, cudaStreamWaitEvent(c->copy_stream, c->packed[b], 0));
+            CK(c, cudaMemcpyAsync(stage, f[q], n * 4, cudaMemcpyHostToDevice, c->copy_stream));
+            CK(c, cudaEventRecord(c->staged[b], c->copy_stream));
+            CK(c, cudaStreamWaitEvent(c->stream, c->staged[b], 0));
+            CK(c, launch_pack(c->storage, d, 0, q, stage, q >= 3 ? c->face[q - 3] : nullptr, c->stream));
+            CK(c, cudaEventRecord(c->packed[b], c->stream));
         }
-        CK(c, launch_pack(c->storage, d, 0, q, src, q >= 3 ? c->face[q - 3] : nullptr, c->stream));
     }
     if (c->d_xclock) CK(c, cudaMemsetAsync(c->d_xclock, 0, sizeof(long long), c->stream));
     if (c->d_probe_buf)
