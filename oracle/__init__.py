@@ -13,6 +13,9 @@ Python API (arrays are canonical (nz+1, ny+1, nx+1) float64, x fastest):
     update_h(fields, ch) / update_e(fields, ce) / pec_e(fields)
     energy(fields, ce, ch, dt_over_dx) -> float
     divergence(fields, ce, ch) -> (divE nodes, divH cells)
+    step4 / update_h4 / update_e4 / energy4 / divergence4: the same with the fourth-order
+        differences c1 [f(p+1/2) - f(p-1/2)] + c2 [f(p+3/2) - f(p-3/2)] (default c1 = 9/8,
+        c2 = -1/24) and image-closed PEC walls
 ce / ch may be a scalar or a list of three scalars/arrays; they are broadcast
 to full canonical arrays.
 """
@@ -70,6 +73,13 @@ def _lib(omp: bool = False) -> ctypes.CDLL:
             lib.oracle_energy.restype = ctypes.c_double
             lib.oracle_divergence.argtypes = [i, i, i, PP, PP, PP, P, P]
             lib.oracle_threads.restype = ctypes.c_int
+            d = ctypes.c_double
+            lib.oracle_update_h4.argtypes = [i, i, i] + [P] * 9 + [d, d]
+            lib.oracle_update_e4.argtypes = [i, i, i] + [P] * 9 + [d, d]
+            lib.oracle_step4.argtypes = [i, i, i, PP, PP, PP, i, d, d, i, i, PI, PI, PI, PI, P, i, d]
+            lib.oracle_energy4.argtypes = [i, i, i, PP, PP, PP, d, d, d]
+            lib.oracle_energy4.restype = ctypes.c_double
+            lib.oracle_divergence4.argtypes = [i, i, i, PP, PP, PP, P, P, d, d]
             _LIBS[omp] = lib
         return _LIBS[omp]
 
@@ -140,6 +150,60 @@ def step_sources(f, ce, ch, nsteps: int, sources, wave, n0: int = 0, dx: float =
     _lib(omp).oracle_step_sources(nx, ny, nz, _pp(f), _pp(ce), _pp(ch), int(nsteps), int(n0), len(src),
                                   *[c.ctypes.data_as(PI) for c in cols], _ptr(w), w.shape[1], float(dx))
     return f
+
+
+# Coefficients of the staggered fourth-order difference (exact for cubics)
+C1_4 = 9.0 / 8.0
+C2_4 = -1.0 / 24.0
+
+
+def update_h4(f, ch, c1=C1_4, c2=C2_4):
+    nx, ny, nz = _dims(f)
+    ch = full_coef(ch, f[0].shape)
+    _lib().oracle_update_h4(nx, ny, nz, *[_ptr(a) for a in (f[3], f[4], f[5], f[0], f[1], f[2])],
+                            *[_ptr(a) for a in ch], float(c1), float(c2))
+
+
+def update_e4(f, ce, c1=C1_4, c2=C2_4):
+    nx, ny, nz = _dims(f)
+    ce = full_coef(ce, f[0].shape)
+    _lib().oracle_update_e4(nx, ny, nz, *[_ptr(a) for a in (f[0], f[1], f[2], f[3], f[4], f[5])],
+                            *[_ptr(a) for a in ce], float(c1), float(c2))
+
+
+def step4(f, ce, ch, nsteps: int, c1=C1_4, c2=C2_4, sources=(), wave=None, n0: int = 0, dx: float = 1.0,
+          omp: bool = False):
+    """Fourth-order (2,4) steps in place; optional point currents as in step_sources."""
+    nx, ny, nz = _dims(f)
+    ce = full_coef(ce, f[0].shape)
+    ch = full_coef(ch, f[0].shape)
+    src = np.asarray(sources, dtype=np.int32).reshape(-1, 4)
+    w = np.zeros((max(len(src), 1), 1)) if wave is None else np.asarray(wave, dtype=np.float64)
+    w = np.ascontiguousarray(w.reshape(max(len(src), 1), -1))
+    cols = [np.ascontiguousarray(src[:, q]) for q in range(4)]
+    PI = ctypes.POINTER(ctypes.c_int)
+    _lib(omp).oracle_step4(nx, ny, nz, _pp(f), _pp(ce), _pp(ch), int(nsteps), float(c1), float(c2), int(n0),
+                           len(src), *[c.ctypes.data_as(PI) for c in cols], _ptr(w), w.shape[1], float(dx))
+    return f
+
+
+def energy4(f, ce, ch, dt_over_dx: float, c1=C1_4, c2=C2_4) -> float:
+    nx, ny, nz = _dims(f)
+    ce = full_coef(ce, f[0].shape)
+    ch = full_coef(ch, f[0].shape)
+    return float(_lib().oracle_energy4(nx, ny, nz, _pp(f), _pp(ce), _pp(ch), float(dt_over_dx), float(c1),
+                                       float(c2)))
+
+
+def divergence4(f, ce, ch, c1=C1_4, c2=C2_4):
+    """Fourth-order (divE at nodes, canonical shape; divH at cells, shape (nz, ny, nx))."""
+    nx, ny, nz = _dims(f)
+    de = np.zeros(f[0].shape, dtype=np.float64)
+    dh = np.zeros((nz, ny, nx), dtype=np.float64)
+    ce = full_coef(ce, f[0].shape)
+    ch = full_coef(ch, f[0].shape)
+    _lib().oracle_divergence4(nx, ny, nz, _pp(f), _pp(ce), _pp(ch), _ptr(de), _ptr(dh), float(c1), float(c2))
+    return de, dh
 
 
 def energy(f, ce, ch, dt_over_dx: float) -> float:

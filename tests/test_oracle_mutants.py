@@ -20,7 +20,8 @@ from tests.yee_matrix import YeeSpace, one_step_matrix
 DT = ci.COURANT_HALF_DT
 
 MUTANTS = {
-    "h_sign_flip": ("AT(hy, i, j, k) -= AT(chy, i, j, k) * c;", "AT(hy, i, j, k) += AT(chy, i, j, k) * c;"),
+    "h_sign_flip": ("AT(ez, i, j, k));\n                AT(hy, i, j, k) -= AT(chy, i, j, k) * c;",
+                    "AT(ez, i, j, k));\n                AT(hy, i, j, k) += AT(chy, i, j, k) * c;"),
     "energy_wrong_index": ("- (AT(ex, i, j + 1, k) - AT(ex, i, j, k));\n                    double h = AT(hz",
                            "- (AT(ex, i + 1, j, k) - AT(ex, i, j, k));\n                    double h = AT(hz"),
     "wrong_index": ("- (AT(ex, i, j + 1, k) - AT(ex, i, j, k));\n                AT(hz",
@@ -29,7 +30,8 @@ MUTANTS = {
                        "+ AT(ey, i, j, k) / AT(ce[1], i, j, k) - AT(ey, i, j - 1, k) / AT(ce[1], i, j, k)"),
     "dropped_term": ("double c = (AT(hy, i, j, k) - AT(hy, i - 1, j, k)) - (AT(hx, i, j, k) - AT(hx, i, j - 1, k));",
                      "double c = (AT(hy, i, j, k) - AT(hy, i - 1, j, k));"),
-    "swapped_coef": ("AT(ex, i, j, k) += AT(cex, i, j, k) * c;", "AT(ex, i, j, k) += AT(cey, i, j, k) * c;"),
+    "swapped_coef": ("AT(hy, i, j, k - 1));\n                AT(ex, i, j, k) += AT(cex, i, j, k) * c;",
+                     "AT(hy, i, j, k - 1));\n                AT(ex, i, j, k) += AT(cey, i, j, k) * c;"),
     "transposed_stencil": ("- (AT(hz, i, j, k) - AT(hz, i - 1, j, k));", "- (AT(hz, i, j, k) - AT(hz, i, j - 1, k));"),
     # (skipping Hz's k = 0 plane would be an equivalent mutant: curl E vanishes on that face)
     "skipped_plane": ("for (k = 1; k < nz; ++k)\n        for (j = 1; j < ny; ++j)\n            for (i = 0; i < nx; ++i) {\n                /* (curl H)_x",
@@ -39,10 +41,10 @@ MUTANTS = {
 }
 
 
-def _build_mutant(tmp_path, name):
+def _build_mutant(tmp_path, name, table=MUTANTS):
     import oracle
     src = open(os.path.join(os.path.dirname(oracle.__file__), "yee_oracle.c")).read()
-    old, new = MUTANTS[name]
+    old, new = table[name]
     assert src.count(old) == 1, f"mutation anchor for {name} not unique/not found"
     path = tmp_path / f"{name}.c"
     path.write_text(src.replace(old, new))

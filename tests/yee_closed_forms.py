@@ -16,6 +16,10 @@ TE101 (Ey, Hx, Hz):  sin^2(w dt/2) = ce ch (s_x^2 + s_z^2)
 
 The general dispersion relation for mode (m, n, p) is
   sin^2(w dt/2) = ce ch (sin^2(pi m/(2nx)) + sin^2(pi n/(2ny)) + sin^2(pi p/(2nz))).
+
+With the fourth-order differences (order=4) the same standing waves are exact
+eigenmodes (the image-closed walls keep sine and cosine profiles intact); every
+sin(pi m/(2n)) above becomes c1 sin(pi m/(2n)) + c2 sin(3 pi m/(2n)).
 """
 from __future__ import annotations
 
@@ -24,6 +28,7 @@ import math
 import numpy as np
 
 import cavity_inputs as ci
+from tests.yee_matrix import sigma
 
 
 def omega(ce: float, ch: float, dt: float, sx2: float, sy2: float, sz2: float = 0.0) -> float:
@@ -44,11 +49,11 @@ def _clean(fields, nx, ny, nz):
     return fields
 
 
-def tm110(nx, ny, nz, dt, n, ce=None, ch=None):
+def tm110(nx, ny, nz, dt, n, ce=None, ch=None, order=2):
     """State (H^{n-1/2}, E^n) of the TM110 mode, float64 canonical arrays."""
     ce = dt if ce is None else ce
     ch = dt if ch is None else ch
-    sx, sy = math.sin(math.pi / (2 * nx)), math.sin(math.pi / (2 * ny))
+    sx, sy = float(sigma(1, nx, order)), float(sigma(1, ny, order))
     w = omega(ce, ch, dt, sx * sx, sy * sy)
     sig = math.sin(w * dt / 2)
     ax, ay = -ch * sy / sig, ch * sx / sig
@@ -61,11 +66,11 @@ def tm110(nx, ny, nz, dt, n, ce=None, ch=None):
     return _clean(f, nx, ny, nz), w
 
 
-def te101(nx, ny, nz, dt, n, ce=None, ch=None):
+def te101(nx, ny, nz, dt, n, ce=None, ch=None, order=2):
     """State (H^{n-1/2}, E^n) of the TE101 mode, float64 canonical arrays."""
     ce = dt if ce is None else ce
     ch = dt if ch is None else ch
-    sx, sz = math.sin(math.pi / (2 * nx)), math.sin(math.pi / (2 * nz))
+    sx, sz = float(sigma(1, nx, order)), float(sigma(1, nz, order))
     w = omega(ce, ch, dt, sx * sx, 0.0, sz * sz)
     sig = math.sin(w * dt / 2)
     bx, bz = ch * sz / sig, -ch * sx / sig

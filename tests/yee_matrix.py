@@ -12,6 +12,12 @@ The curl of a field G at point q is, for each cyclic (a, b, c),
 with one doubled-lattice step being half a cell, so each difference spans one
 cell (dx = 1).  PEC: E points on a face tangential to it are not unknowns and
 read as zero.
+
+order=4 builds the fourth-order differences instead,
+    c1 [G(q + e) - G(q - e)] + c2 [G(q + 3e) - G(q - 3e)],   c1 = 9/8, c2 = -1/24,
+where a tap past a wall is the mirror point across it, with sign -1 for an E
+point and +1 for an H point (tangential E odd, tangential H even about a PEC
+wall); the divergences mirror normal components with the opposite parities.
 """
 from __future__ import annotations
 
@@ -25,9 +31,13 @@ AXES = 3
 CYCLIC = ((0, 1, 2), (1, 2, 0), (2, 0, 1))
 
 
+C1_4, C2_4 = 9.0 / 8.0, -1.0 / 24.0
+
+
 class YeeSpace:
-    def __init__(self, nx: int, ny: int, nz: int):
+    def __init__(self, nx: int, ny: int, nz: int, order: int = 2):
         self.n = (nx, ny, nz)
+        self.taps = ((1, 1.0),) if order == 2 else ((1, C1_4), (3, C2_4))
         self.e_pts, self.h_pts = [], []
         lim = (2 * nx, 2 * ny, 2 * nz)
         for q in itertools.product(*(range(L + 1) for L in lim)):
@@ -52,7 +62,20 @@ class YeeSpace:
     def _inside(self, q):
         return all(0 <= q[a] <= self.lim[a] for a in range(AXES))
 
-    def _curl(self, rows, src_idx, strict):
+    def _mirror(self, p, axis, odd_sign):
+        """The point p, with its coordinate along axis reflected into the box, and the image's sign."""
+        p = list(p)
+        if p[axis] < 0:
+            p[axis] = -p[axis]
+        elif p[axis] > self.lim[axis]:
+            p[axis] = 2 * self.lim[axis] - p[axis]
+        else:
+            return tuple(p), 1.0
+        assert self._inside(p), f"tap reaches more than one wall image at {p}"
+        return tuple(p), odd_sign
+
+    def _curl(self, rows, src_idx, src_is_e):
+        strict = not src_is_e   # every H point exists; tangential E points on a face are not unknowns
         M = np.zeros((len(rows), len(src_idx)))
         for r, q in enumerate(rows):
             a = self.comp_of(q)
@@ -60,28 +83,31 @@ class YeeSpace:
                 if aa != a:
                     continue
                 for comp_axis, diff_axis, sign in ((c, b, +1.0), (b, c, -1.0)):
-                    for step, s2 in ((+1, +1.0), (-1, -1.0)):
-                        p = list(q)
-                        p[diff_axis] += step
-                        p = tuple(p)
-                        if not self._inside(p):
-                            raise AssertionError(f"stencil leaves the box at {p}")
-                        assert self.comp_of(p) == comp_axis
-                        col = src_idx.get(p)
-                        if col is None:
-                            if strict:
-                                raise AssertionError(f"missing unknown at {p}")
-                            continue  # tangential PEC edge: E = 0
-                        M[r, col] += sign * s2
+                    for dist, w in self.taps:
+                        for step, s2 in ((+dist, +w), (-dist, -w)):
+                            p = list(q)
+                            p[diff_axis] += step
+                            p = tuple(p)
+                            if len(self.taps) == 1 and not self._inside(p):
+                                raise AssertionError(f"stencil leaves the box at {p}")
+                            # tangential E: odd image; tangential H: even image
+                            p, img = self._mirror(p, diff_axis, -1.0 if src_is_e else 1.0)
+                            assert self.comp_of(p) == comp_axis
+                            col = src_idx.get(p)
+                            if col is None:
+                                if strict:
+                                    raise AssertionError(f"missing unknown at {p}")
+                                continue  # tangential PEC edge: E = 0
+                            M[r, col] += sign * s2 * img
         return M
 
     def curl_e(self):
         """(H points) x (E unknowns): curl E evaluated at every H point."""
-        return self._curl(self.h_pts, self.e_idx, strict=False)
+        return self._curl(self.h_pts, self.e_idx, src_is_e=True)
 
     def curl_h(self):
         """(E unknowns) x (H points): curl H evaluated at every interior E point."""
-        return self._curl(self.e_pts, self.h_idx, strict=True)
+        return self._curl(self.e_pts, self.h_idx, src_is_e=False)
 
     def div_nodes(self):
         """Interior nodes x E unknowns: sum_a E_a(q + e_a) - E_a(q - e_a)."""
@@ -90,9 +116,11 @@ class YeeSpace:
         D = np.zeros((len(nodes), len(self.e_pts)))
         for r, q in enumerate(nodes):
             for a in range(AXES):
-                for step, s in ((+1, 1.0), (-1, -1.0)):
-                    p = list(q); p[a] += step
-                    D[r, self.e_idx[tuple(p)]] += s
+                for dist, w in self.taps:
+                    for step, s in ((+dist, w), (-dist, -w)):
+                        p = list(q); p[a] += step
+                        p, img = self._mirror(p, a, 1.0)    # normal E: even image
+                        D[r, self.e_idx[p]] += s * img
         return D
 
     def div_cells(self):
@@ -101,9 +129,11 @@ class YeeSpace:
         D = np.zeros((len(cells), len(self.h_pts)))
         for r, q in enumerate(cells):
             for a in range(AXES):
-                for step, s in ((+1, 1.0), (-1, -1.0)):
-                    p = list(q); p[a] += step
-                    D[r, self.h_idx[tuple(p)]] += s
+                for dist, w in self.taps:
+                    for step, s in ((+dist, w), (-dist, -w)):
+                        p = list(q); p[a] += step
+                        p, img = self._mirror(p, a, -1.0)   # normal H: odd image
+                        D[r, self.h_idx[p]] += s * img
         return D
 
     # --- mapping between unknown vectors and canonical (nz+1, ny+1, nx+1) arrays ---
@@ -143,15 +173,21 @@ def one_step_matrix(space: YeeSpace, ce3, ch3):
     return B @ A, CE, CH
 
 
-def mode_frequencies(nx, ny, nz, ce, ch, dt):
+def sigma(m, n, order=2):
+    """Symbol of the staggered difference on the standing wave sin(pi m x / n): D -> 2 sigma."""
+    if order == 2:
+        return np.sin(np.pi * m / (2 * n))
+    return C1_4 * np.sin(np.pi * m / (2 * n)) + C2_4 * np.sin(3 * np.pi * m / (2 * n))
+
+
+def mode_frequencies(nx, ny, nz, ce, ch, dt, order=2):
     """omega*dt of every discrete cavity mode, with TE/TM multiplicity."""
     out = []
     for m, n, p in itertools.product(range(nx), range(ny), range(nz)):
         nz_count = (m > 0) + (n > 0) + (p > 0)
         if nz_count < 2:
             continue
-        s = (np.sin(np.pi * m / (2 * nx)) ** 2 + np.sin(np.pi * n / (2 * ny)) ** 2
-             + np.sin(np.pi * p / (2 * nz)) ** 2)
+        s = sigma(m, nx, order) ** 2 + sigma(n, ny, order) ** 2 + sigma(p, nz, order) ** 2
         w = 2.0 * np.arcsin(np.sqrt(ce * ch * s))
         out += [w] * (2 if nz_count == 3 else 1)
     return np.sort(np.array(out))
