@@ -8,7 +8,8 @@
  *   Sec. 2, Eq. 1   - the curl equations;
  *   Sec. 2, Eq. 2   - the staggered update of the six components;
  *   Sec. 2.1, Listing 1 - one step = H from curl E, boundary, E from curl H, boundary;
- *   Sec. 4          - the benchmark workload: a PEC cavity from a random state.
+ *   Sec. 4          - the benchmark workload: a PEC cavity from a random state;
+ *   Sec. 6          - higher-order schemes (fdtd_set_order: the fourth-order differences).
  *
  * Units and conventions
  *   nx, ny, nz are cell counts; dx = dy = dz = dx.  State after n steps is
@@ -154,8 +155,34 @@ FDTD_API int fdtd_divergence(fdtd_ctx *ctx, double *divE_l2, double *divH_l2);
 /* fdtd_sync - wait for the context's stream; returns a latched device error, if any. */
 FDTD_API int fdtd_sync(fdtd_ctx *ctx);
 
-/* fdtd_set_tuning - choose the step kernel and its launch shape (NULL = defaults). */
+/* fdtd_set_tuning - choose the step kernel and its launch shape (NULL = defaults).  With spatial
+ * order 4 (fdtd_set_order) kernel TEMPORAL and stages = 3 are FDTD_ERR_ARG. */
 FDTD_API int fdtd_set_tuning(fdtd_ctx *ctx, const fdtd_tuning *t);
+
+/*
+ * fdtd_set_order - spatial order of the curl differences: 2 (Eq. 2; the default) or 4.
+ *
+ * Sec. 6 names higher-order schemes as the way to raise FDTD's arithmetic intensity; order 4 is the
+ * staggered fourth-order (2,4) scheme: every difference f(p+1/2) - f(p-1/2) of Eq. 2 becomes
+ *   c1 [f(p+1/2) - f(p-1/2)] + c2 [f(p+3/2) - f(p-3/2)],   c1 = 9/8, c2 = -1/24,
+ * with the PEC walls closed by image theory (about each wall tangential E is odd and tangential H
+ * even; a tap one position past a wall reads that image).  Time stepping, layout, PEC (tangential E
+ * stays 0, normal H constant) and currents are unchanged.  fdtd_energy and fdtd_divergence then use
+ * the same differences (the energy W^n with the fourth-order curl, the divergences with D = E/ce
+ * mirrored evenly and B = H/ch oddly past a wall), the invariants of this scheme.
+ *
+ * Kernels with order 4: FUSED (and AUTO) run the fused fourth-order kernel (one launch per step;
+ * tile_y 4, 8 or 16; stages 4..8), SIMPLE the unfused one (also the path for per-position
+ * coefficient arrays); TEMPORAL is not available.  Returns FDTD_ERR_UNSTABLE when the scheme's
+ * Courant bound fails (order 4: max sqrt(3 ce ch) * 7/6 > 1, as the difference's symbol reaches
+ * c1 - c2 = 7/6), FDTD_ERR_ARG for another order or a TEMPORAL / stages = 3 tuning, FDTD_ERR_STATE
+ * for a batch member (fourth-order contexts are not batched).  Applies from the next call on;
+ * synchronises the stream.
+ */
+FDTD_API int fdtd_set_order(fdtd_ctx *ctx, int order);
+
+/* fdtd_get_order - the context's spatial order (2 or 4), -1 for NULL. */
+FDTD_API int fdtd_get_order(const fdtd_ctx *ctx);
 
 /* fdtd_autotune - choose the step kernel and launch shape by timing candidates on this
  * context's own state: the one-step kernel with 4, 8, 16-row tiles and the two-step kernel with
@@ -164,8 +191,10 @@ FDTD_API int fdtd_set_tuning(fdtd_ctx *ctx, const fdtd_tuning *t);
  * with CUDA events on the context's stream.  The fields are copied aside first (one extra copy
  * of the active arrays, freed before return) and restored afterwards, so the state and
  * fdtd_steps_done are unchanged.  The choice is kept per (nx, ny, nz, storage, coefficient
- * kind) for the life of the process: a later call for the same shape applies it without
- * trials.  Contexts with per-position coefficient arrays keep the unfused kernel.  out
+ * kind, spatial order) for the life of the process: a later call for the same shape applies it
+ * without trials.  Contexts with per-position coefficient arrays keep the unfused kernel; with
+ * order 4 the candidates are the fused fourth-order kernel with 4, 8, 16-row tiles and 4 or 6
+ * ring slots.  out
  * (may be NULL) receives the chosen tuning, ms_per_step (may be NULL) its time per step.
  * Requires fdtd_set_fields; synchronises the stream. */
 FDTD_API int fdtd_autotune(fdtd_ctx *ctx, int trial_steps, fdtd_tuning *out, double *ms_per_step);

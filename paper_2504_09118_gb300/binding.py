@@ -31,7 +31,7 @@ EXPORTS = (
     "fdtd_batch_size", "fdtd_batch_sync", "fdtd_batch_destroy", "fdtd_batch_last_error",
     "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static", "fdtd_batch_set_steps",
     "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune", "fdtd_set_sources", "fdtd_set_probes",
-    "fdtd_get_probes",
+    "fdtd_get_probes", "fdtd_set_order", "fdtd_get_order",
 )
 
 
@@ -105,6 +105,8 @@ def lib() -> ctypes.CDLL:
             L.fdtd_set_sources.argtypes = [vp, i, vp, vp, vp, i]
             L.fdtd_set_probes.argtypes = [vp, i, vp, vp, i]
             L.fdtd_get_probes.argtypes = [vp, vp, ctypes.POINTER(i)]
+            L.fdtd_set_order.argtypes = [vp, i]
+            L.fdtd_get_order.argtypes = [vp]
             _LIB = L
         return _LIB
 
@@ -231,6 +233,15 @@ def fdtd_sync(ctx) -> None:
 def fdtd_set_tuning(ctx, kernel=0, tile_y=0, zchunk=0, ctas_per_sm=0, stages=0, use_graph=0) -> None:
     t = fdtd_tuning(kernel, tile_y, zchunk, ctas_per_sm, stages, use_graph)
     _check(ctx, lib().fdtd_set_tuning(ctx, ctypes.byref(t)))
+
+
+def fdtd_set_order(ctx, order: int) -> None:
+    """Spatial order of the curl differences: 2 (Eq. 2) or 4 (the staggered (2,4) scheme)."""
+    _check(ctx, lib().fdtd_set_order(ctx, int(order)))
+
+
+def fdtd_get_order(ctx) -> int:
+    return int(lib().fdtd_get_order(ctx))
 
 
 def _tuning_dict(t) -> dict:

@@ -11,13 +11,24 @@ class Cavity:
 
     ce/ch: None (vacuum), a scalar, or three canonical (nz+1, ny+1, nx+1) arrays of
     dt/(eps dx) at E positions and dt/(mu dx) at H positions.
+    order: 2 (Eq. 2) or 4 (the staggered fourth-order (2,4) scheme, image-closed PEC walls).
     """
 
-    def __init__(self, nx, ny, nz, dt, dx=1.0, ce=None, ch=None, storage=B.FDTD_F32, stream=None):
+    def __init__(self, nx, ny, nz, dt, dx=1.0, ce=None, ch=None, storage=B.FDTD_F32, stream=None, order=2):
         self.dims = (int(nx), int(ny), int(nz))
         self.dt, self.dx, self.storage = float(dt), float(dx), int(storage)
         self.shape = (nz + 1, ny + 1, nx + 1)
         self.handle = B.fdtd_create(nx, ny, nz, dt, dx, ce, ch, storage, stream)
+        if order != 2:
+            try:
+                B.fdtd_set_order(self.handle, order)
+            except Exception:
+                self.close()
+                raise
+
+    @property
+    def order(self):
+        return B.fdtd_get_order(self.handle)
 
     def set_fields(self, fields, on_device=False):
         B.fdtd_set_fields(self.handle, fields, int(on_device), dims=self.dims)

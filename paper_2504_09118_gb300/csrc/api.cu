@@ -90,13 +90,15 @@ struct fdtd_ctx {
     unsigned *d_max = nullptr;
     CUtensorMap *d_maps = nullptr;          // kMapSets x kMapsPerCavity
     std::vector<CUtensorMap> host_maps[kMapSets];
-    int maps_by[kMapSets] = {0, 0};         // box height each map set was encoded for (0: not yet)
+    int maps_by[kMapSets] = {0, 0, 0};      // box height each map set was encoded for (0: not yet)
     CavityDesc *d_desc = nullptr;
     struct TileList {
         TileRec *d = nullptr;   // records, followed by the per-CTA range offsets
         int *first = nullptr;   // inside the same allocation as d
         int n = 0, grid = 0, key = 0;
-    } tl[2];                                // [0] one-step kernel, [1] two-step kernel
+    } tl[3];                                // [0] one-step, [1] two-step, [2] fourth-order kernel
+    int order = 2;                          // spatial order of the differences (2: Eq. 2, 4: the (2,4) scheme)
+    double courant = 0.0;                   // max over cells of 3 ce ch (stable for order 2 when <= 1)
     int ch_uniform = 1;
     fdtd_tuning tuning{};
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -278,7 +280,7 @@ int encode_maps(fdtd_ctx *c, int set, int box_y) {
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return fail(c, FDTD_ERR_CUDA, "tensor map encode failed (%d)", (int)r);
         }
-    if (set == 1)   // two-step kernel: slot cp * 6 holds one 4-D map over the copy's six arrays
+    if (set >= 1)   // two-step and fourth-order kernels: slot cp * 6 holds one 4-D map over the six arrays
         for (int cp = 0; cp < 2; ++cp) {
             cuuint64_t gdim4[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, 6};
             cuuint64_t gstr4[3] = {(cuuint64_t)c->pitch * es, (cuuint64_t)c->pitch * c->ny * es,
@@ -292,7 +294,8 @@ int encode_maps(fdtd_ctx *c, int set, int box_y) {
         }
     if (c->id) {
         cuuint64_t gstr[2] = {(cuuint64_t)c->pitch, (cuuint64_t)c->pitch * c->ny};
-        cuuint32_t box[3] = {(cuuint32_t)(kTileX + 16), (cuuint32_t)box_y, 1};
+        // ids from 16 bytes left of the tile; the fourth-order kernel also needs its right halo
+        cuuint32_t box[3] = {(cuuint32_t)(kTileX + (set == 2 ? 32 : 16)), (cuuint32_t)box_y, 1};
         CUresult r = enc(&maps[12], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->id, gdim, gstr, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -306,7 +309,7 @@ int encode_maps(fdtd_ctx *c, int set, int box_y) {
 }
 
 struct Shape {
-    int kind;   // 0: one step per launch, 1: two steps per launch
+    int kind;   // 0: one step per launch, 1: two steps per launch, 2: one fourth-order step
     int tile_y, stages, ctas_per_sm;
 };
 
@@ -316,15 +319,18 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0) {
     static std::map<int, int> occ_cache;   // (kind, storage, tile_y, stages) -> max CTAs per SM
     Shape s;
     s.kind = kind;
-    if (kind == 0)
+    if (kind != 1)
         s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 16) ? t.tile_y : 8;
     else
         s.tile_y = (t.tile_y == 8 || t.tile_y == 12) ? t.tile_y : 12;
-    s.stages = (t.stages >= 3 && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : 6);
+    const int min_st = kind == 2 ? 4 : 3;
+    s.stages = (t.stages >= min_st && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : kind == 1 ? 6 : 5);
     auto smem = [&](int st) {
-        return kind == 0 ? fused_smem_bytes(storage, s.tile_y, st) : fused2_smem_bytes(storage, s.tile_y, st);
+        return kind == 0 ? fused_smem_bytes(storage, s.tile_y, st)
+               : kind == 1 ? fused2_smem_bytes(storage, s.tile_y, st)
+                           : fused4_smem_bytes(storage, s.tile_y, st);
     };
-    while (s.stages > 3 && smem(s.stages) > 227 * 1024) --s.stages;
+    while (s.stages > min_st && smem(s.stages) > 227 * 1024) --s.stages;
     const int key = ((kind * 4 + storage) * 64 + s.tile_y) * 16 + s.stages;
     int occ = 0;
     {
@@ -333,8 +339,9 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0) {
         if (it != occ_cache.end()) {
             occ = it->second;
         } else {
-            cudaError_t e = kind == 0 ? fused_occupancy(storage, s.tile_y, s.stages, &occ)
-                                      : fused2_occupancy(storage, s.tile_y, s.stages, &occ);
+            cudaError_t e = kind == 0   ? fused_occupancy(storage, s.tile_y, s.stages, &occ)
+                            : kind == 1 ? fused2_occupancy(storage, s.tile_y, s.stages, &occ)
+                                        : fused4_occupancy(storage, s.tile_y, s.stages, &occ);
             if (e != cudaSuccess || occ < 1) occ = 1;
             occ_cache[key] = occ;
         }
@@ -463,7 +470,7 @@ TileRec base_rec(const fdtd_ctx *c, int parity_off, int set = 0) {
 void append_tiles_plan(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y,
                        const std::vector<int> &plan, int kind) {
     const TileRec b = base_rec(c, parity_off, kind);
-    const int tw = kind == 0 ? kTileX : fused2_tile_w(c->storage);
+    const int tw = kind == 1 ? fused2_tile_w(c->storage) : kTileX;
     int z0 = 0;
     for (int len : plan) {
         for (int y0 = 0; y0 < c->ny; y0 += tile_y)
@@ -514,11 +521,11 @@ int build_tiles(fdtd_ctx *c, int kind) {
     Shape s = resolve_shape(c->storage, c->tuning, kind);
     fdtd_ctx::TileList &tl = c->tl[kind];
     if (tl.key == s.tile_y && tl.d && tl.grid) return FDTD_OK;
-    int rc = encode_maps(c, kind, s.tile_y + (kind == 0 ? 2 : 4));
+    int rc = encode_maps(c, kind, s.tile_y + (kind == 0 ? 2 : kind == 1 ? 4 : 6));
     if (rc) return rc;
-    const int tw = kind == 0 ? kTileX : fused2_tile_w(c->storage);
+    const int tw = kind == 1 ? fused2_tile_w(c->storage) : kTileX;
     const long long cols = (long long)((c->nx + tw - 1) / tw) * ((c->ny + s.tile_y - 1) / s.tile_y);
-    const int prologue = kind == 0 ? 1 : 3;
+    const int prologue = kind == 0 ? 1 : kind == 1 ? 3 : 4;
     const int G = (int)std::min<long long>((long long)num_sms() * s.ctas_per_sm, cols * c->nz);
     std::vector<TileRec> listed, v;
     std::vector<int> first;
@@ -561,15 +568,23 @@ bool use_fused(const fdtd_ctx *c) {
     return c->coef_mode != COEF_FULL && c->tuning.kernel != FDTD_KERNEL_SIMPLE;
 }
 
-// AUTO takes the two-step kernel: faster than the one-step kernel at every size measured
+// AUTO takes the two-step kernel: faster than the one-step kernel at every size measured (second
+// order only: the fourth-order scheme has a one-step kernel)
 bool use_temporal(const fdtd_ctx *c) {
-    return use_fused(c) && (c->tuning.kernel == FDTD_KERNEL_TEMPORAL || c->tuning.kernel == FDTD_KERNEL_AUTO);
+    return use_fused(c) && c->order == 2 &&
+           (c->tuning.kernel == FDTD_KERNEL_TEMPORAL || c->tuning.kernel == FDTD_KERNEL_AUTO);
 }
 
-// One launch of a single context (no graph): kind 0 advances one step, kind 1 two steps.
+// Tile kind of a context's one-step launches: 0 (Eq. 2) or 2 (fourth order).
+int one_step_kind(const fdtd_ctx *c) { return c->order == 4 ? 2 : 0; }
+
+// One launch of a single context (no graph): kinds 0 and 2 advance one step, kind 1 two steps.
 int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind = 0) {
     if (!use_fused(c)) {
-        CK(c, launch_simple_step(c->storage, make_desc(c, 0), c->cur, c->stream));
+        if (c->order == 4)
+            CK(c, launch_simple4_step(c->storage, make_desc(c, 0), c->cur, c->stream));
+        else
+            CK(c, launch_simple_step(c->storage, make_desc(c, 0), c->cur, c->stream));
         return FDTD_OK;
     }
     Shape s = resolve_shape(c->storage, c->tuning, kind);
@@ -586,8 +601,10 @@ int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind = 0) {
     L.first = tl.first;
     if (kind == 0)
         CK(c, launch_fused_step(c->storage, L, c->stream));
-    else
+    else if (kind == 1)
         CK(c, launch_fused2_step(c->storage, L, c->stream));
+    else
+        CK(c, launch_fused4_step(c->storage, L, c->stream));
     return FDTD_OK;
 }
 
@@ -697,6 +714,7 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
     std::vector<uint8_t> ids;
     std::vector<Tuple> table;
     bool full = false;
+    double courant = 3.0 * vac * vac;   // max over cells of 3 ce ch
     if (have_ce || have_ch) {
         ids.resize((size_t)nx * ny * nz);
         std::unordered_map<Tuple, int, TupleHash> map;
@@ -761,6 +779,7 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
         if (worst > 1.0 + 1e-6)
             return fail(nullptr, FDTD_ERR_UNSTABLE, "Courant bound violated: max sqrt(3 ce ch) = %.6f > 1",
                         std::sqrt(worst));
+        courant = worst;
         // far-face ch values (Hx at i = nx, Hy at j = ny, Hz at k = nz) are used by energy and divergence
         if (have_ch) {
             for (int k = 0; k < nz; ++k)
@@ -786,6 +805,7 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
     c->nz = nz;
     c->dt = dt;
     c->dx = dx;
+    c->courant = courant;
     c->storage = storage;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->pitch = (nx + 31) / 32 * 32;
@@ -928,7 +948,7 @@ void fdtd_destroy(fdtd_ctx *c) {
     for (void *p : {(void *)c->id, (void *)c->table, (void *)c->inv_table, (void *)c->table_fused,
                     (void *)c->d_status, (void *)c->d_partial, (void *)c->d_out, (void *)c->d_stage,
                     (void *)c->d_max, (void *)c->d_maps, (void *)c->d_desc, (void *)c->tl[0].d,
-                    (void *)c->tl[1].d, (void *)c->d_src_comp, (void *)c->d_src_off, (void *)c->d_wave,
+                    (void *)c->tl[1].d, (void *)c->tl[2].d, (void *)c->d_src_comp, (void *)c->d_src_off, (void *)c->d_wave,
                     (void *)c->d_probe_comp, (void *)c->d_probe_off, (void *)c->d_probe_buf, (void *)c->d_xclock})
         pool_free(p, st);
     pool_free(c->d_stage2, st);
@@ -952,26 +972,55 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
     fdtd_tuning n{};
     if (t) n = *t;
     if (n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
+    if (n.kernel == FDTD_KERNEL_TEMPORAL && c->order != 2)
+        return fail(c, FDTD_ERR_ARG, "the two-step kernel runs the second-order scheme only");
     const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16, ty_two = n.tile_y == 8 || n.tile_y == 12;
     if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL ? ty_two
                       : n.kernel == FDTD_KERNEL_AUTO   ? (ty_one || ty_two)
                                                        : ty_one))
         return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (8 or 12 for the two-step kernel)");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return fail(c, FDTD_ERR_ARG, "stages must be in [3, 8]");
+    if (n.stages == 3 && c->order == 4) return fail(c, FDTD_ERR_ARG, "the fourth-order kernel needs stages >= 4");
     if (n.zchunk < 0 || n.ctas_per_sm < 0) return fail(c, FDTD_ERR_ARG, "negative tuning value");
     c->tuning = n;
-    c->tl[0].key = c->tl[1].key = 0;   // force tile rebuilds
+    c->tl[0].key = c->tl[1].key = c->tl[2].key = 0;   // force tile rebuilds
     cudaStreamSynchronize(c->stream);   // no graph of this context may still be running
     drop_graphs(c->graphs);
     return FDTD_OK;
 }
 
+int fdtd_set_order(fdtd_ctx *c, int order) {
+    if (!c) return FDTD_ERR_ARG;
+    if (order != 2 && order != 4) return fail(c, FDTD_ERR_ARG, "order must be 2 or 4");
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member");
+    // the (2,4) difference has symbol up to c1 - c2 = 7/6 times the second-order one
+    const double gain = order == 4 ? 7.0 / 6.0 : 1.0;
+    if (c->courant * gain * gain > 1.0 + 1e-6)
+        return fail(c, FDTD_ERR_UNSTABLE, "Courant bound of order %d violated: max sqrt(3 ce ch) * %.4f = %.6f > 1",
+                    order, gain, std::sqrt(c->courant) * gain);
+    if (order == 4 && c->tuning.kernel == FDTD_KERNEL_TEMPORAL)
+        return fail(c, FDTD_ERR_ARG, "the two-step kernel runs the second-order scheme only; retune first");
+    if (order == 4 && c->tuning.stages == 3)
+        return fail(c, FDTD_ERR_ARG, "the fourth-order kernel needs stages >= 4; retune first");
+    cudaStreamSynchronize(c->stream);   // no graph of this context may still be running
+    drop_graphs(c->graphs);
+    c->order = order;
+    return FDTD_OK;
+}
+
+int fdtd_get_order(const fdtd_ctx *c) { return c ? c->order : -1; }
+
 // ---------------------------------------------------------------------------------------------
 // Autotuning: candidates are timed on the caller's own state, which is copied aside and restored.
 namespace {
 
-std::vector<fdtd_tuning> tune_candidates(bool batch) {
+std::vector<fdtd_tuning> tune_candidates(bool batch, int order = 2) {
     std::vector<fdtd_tuning> v;
+    if (order == 4) {   // the fused fourth-order kernel's tile heights and ring depths
+        for (int ty : {4, 8, 16})
+            for (int st : {4, 6}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, st, 1});
+        return v;
+    }
     for (int ty : {4, 8, 16}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, 4, 1});
     for (int ty : {8, 12})
         for (int st : {4, 6}) {
@@ -987,7 +1036,7 @@ int trial_length(int trial_steps) {   // whole 16-step graphs
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int>, std::pair<fdtd_tuning, double>> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<fdtd_tuning, double>> g_tune_cache;
 
 }  // namespace
 
@@ -1006,7 +1055,7 @@ int fdtd_autotune(fdtd_ctx *c, int trial_steps, fdtd_tuning *out, double *ms_per
         if (int rc = fdtd_set_tuning(c, &t)) return rc;
         return report(t, -1.0);
     }
-    const auto key = std::make_tuple(c->nx, c->ny, c->nz, c->storage, c->coef_mode, c->ch_uniform);
+    const auto key = std::make_tuple(c->nx, c->ny, c->nz, c->storage, c->coef_mode, c->ch_uniform, c->order);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -1031,7 +1080,7 @@ int fdtd_autotune(fdtd_ctx *c, int trial_steps, fdtd_tuning *out, double *ms_per
     fdtd_tuning best{};
     double best_ms = -1.0;
     int rc = FDTD_OK;
-    for (const fdtd_tuning &t : tune_candidates(false)) {
+    for (const fdtd_tuning &t : tune_candidates(false, c->order)) {
         if ((rc = fdtd_set_tuning(c, &t)) != FDTD_OK) break;
         if ((rc = fdtd_step(c, n)) != FDTD_OK) break;   // untimed: tiles, maps and graphs are built here
         cudaEventRecord(e0, c->stream);
@@ -1110,7 +1159,7 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
             CK(c, cudaMemcpyAsync(c->table_fused, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, c->stream));
             CK(c, cudaStreamSynchronize(c->stream));
         }
-        c->tl[0].key = c->tl[1].key = 0;   // tile records embed the folded coefficients: rebuild them
+        c->tl[0].key = c->tl[1].key = c->tl[2].key = 0;   // tile records embed the folded coefficients
         cudaStreamSynchronize(c->stream);
         drop_graphs(c->graphs);
     }
@@ -1175,8 +1224,9 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
     const bool extras = extras_on(c);
     // currents enter between the E update of one step and the H update of the next: one step per launch
     const bool temporal = use_temporal(c) && !extras;
+    const int k1 = one_step_kind(c);
     if (fused)
-        if (int rc = build_tiles(c, 0)) return rc;
+        if (int rc = build_tiles(c, k1)) return rc;
     if (temporal)
         if (int rc = build_tiles(c, 1)) return rc;
     // one launch from copy `parity` (fused kernels write copy parity ^ 1; the unfused one works in
@@ -1189,18 +1239,18 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
     if (c->inject_us > 0 && fused) {
         const int inj = c->inject_us;
         c->inject_us = 0;
-        if (int rc = step_launch(c->cur, inj, 0)) return rc;
+        if (int rc = step_launch(c->cur, inj, k1)) return rc;
         c->cur ^= 1;
         ++c->steps;
         --left;
     }
     // kind 1 advances two steps per launch; either kind reads copy cur and writes copy 1 - cur.
     // An odd remainder takes one launch of the one-step kernel at the end.
-    const int kind = temporal ? 1 : 0;
+    const int kind = temporal ? 1 : k1;
     const int per = temporal ? 2 : 1;
     const int K = 16;   // steps per graph
     if (c->tuning.use_graph && fused && c->stream != nullptr && left >= K) {
-        GraphKey key{K, c->cur, kind + (extras ? 2 : 0)};
+        GraphKey key{K, c->cur, kind + (extras ? 4 : 0)};
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             cudaGraph_t g;
@@ -1228,7 +1278,7 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
             c->steps += 2;
         }
     for (; left > 0; --left) {
-        if (int rc = step_launch(c->cur, 0, 0)) return rc;
+        if (int rc = step_launch(c->cur, 0, k1)) return rc;
         if (fused) c->cur ^= 1;
         ++c->steps;
     }
@@ -1350,7 +1400,7 @@ static int run_reductions(fdtd_ctx *c, int what, double out[3]) {
     if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
     if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
     CK(c, launch_reductions(c->storage, make_desc(c, 0), c->cur, what, c->d_partial, reduction_blocks(), c->d_out,
-                            c->stream));
+                            c->stream, c->order));
     CK(c, cudaMemcpyAsync(out, c->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return check_status(c, c->d_status, c->stream);
@@ -1427,6 +1477,7 @@ int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *c) {
     if (c->storage != b->storage) return bfail(b, FDTD_ERR_ARG, "storage mismatch");
     if (c->coef_mode == COEF_FULL) return bfail(b, FDTD_ERR_ARG, "per-position coefficient arrays are not batched");
     if (extras_on(c)) return bfail(b, FDTD_ERR_ARG, "contexts with currents or probes are not batched");
+    if (c->order != 2) return bfail(b, FDTD_ERR_ARG, "fourth-order contexts are not batched");
     // the member's pending work (set_fields) happened-before: its stream was synchronised by that call
     b->members.push_back({c, c->cur, b->step, b->launches, LLONG_MAX, c->steps, 0});
     c->batch = b;

@@ -303,8 +303,11 @@ cudaError_t launch_simple_step(int storage, const CavityDesc &d, int copy, cudaS
 int reduction_blocks() { return kRedBlocks; }
 
 cudaError_t launch_reductions(int storage, const CavityDesc &d, int copy, int what, double *partial, int nblocks,
-                              double *out, cudaStream_t s) {
-    if (what == 0)
+                              double *out, cudaStream_t s, int order) {
+    if (order == 4) {
+        cudaError_t e = launch_reductions4(storage, d, copy, what, partial, nblocks, s);
+        if (e != cudaSuccess) return e;
+    } else if (what == 0)
         FDTD_STORAGE_DISPATCH(storage, reduce_kernel<T, 0><<<nblocks, kRedThreads, 0, s>>>(d, copy, partial));
     else
         FDTD_STORAGE_DISPATCH(storage, reduce_kernel<T, 1><<<nblocks, kRedThreads, 0, s>>>(d, copy, partial));

@@ -17,8 +17,14 @@ cudaError_t launch_maxabs(const float *canon, int comp, int nx, int ny, int nz, 
 cudaError_t launch_simple_step(int storage, const CavityDesc &d, int copy, cudaStream_t s);
 // Reductions accumulated in FP64: what == 0 gives out[0] = sum E^2/ce + H.(H - ch curl E)/ch;
 // what == 1 gives out[1] = sum divE^2, out[2] = sum divH^2.  partial holds nblocks*3 doubles.
+// order 4 takes the curl and divergences of the fourth-order scheme.
 cudaError_t launch_reductions(int storage, const CavityDesc &d, int copy, int what, double *partial, int nblocks,
-                              double *out, cudaStream_t s);
+                              double *out, cudaStream_t s, int order = 2);
+// Fourth-order scheme (k_order4.cu): one unfused step in place on copy `copy`, and the per-block
+// partials of its reductions (same layout as launch_reductions' partial).
+cudaError_t launch_simple4_step(int storage, const CavityDesc &d, int copy, cudaStream_t s);
+cudaError_t launch_reductions4(int storage, const CavityDesc &d, int copy, int what, double *partial, int nblocks,
+                               cudaStream_t s);
 int reduction_blocks();
 
 struct FusedLaunch {
@@ -63,6 +69,10 @@ int fused2_tile_w(int storage);
 int fused2_smem_bytes(int storage, int tile_y, int stages);
 cudaError_t fused2_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
 cudaError_t launch_fused2_step(int storage, const FusedLaunch &L, cudaStream_t s);
+// Fused fourth-order kernel (k_fused4.cu): shared memory, occupancy, launch (stages 4..8).
+int fused4_smem_bytes(int storage, int tile_y, int stages);
+cudaError_t fused4_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
+cudaError_t launch_fused4_step(int storage, const FusedLaunch &L, cudaStream_t s);
 // Box sizes used to encode the tensor maps of the fused kernel.
 void fused_box(int storage, int tile_y, int *box_x, int *box_y, int *halo_x);
 
