@@ -50,6 +50,12 @@ WORKLOADS = {
     "serve": dict(kind="serve", rate=200.0, seed=6, budget_gb=120),
     # error study: 384^3 spheres, 1000 steps, FP32 / FP16 / BF16 storage against the FP64 oracle
     "precision": dict(kind="precision", n=(384, 384, 384), steps=1000, sphere_seed=3, field_seed=4, spheres=32),
+    # the fourth-order (2,4) scheme on the single512 cavity (fused fourth-order kernel, one step per launch)
+    "order4_512": dict(n=(512, 512, 512), steps=200, storage=0, sphere_seed=1, field_seed=2, spheres=32, order=4,
+                       tuning=dict(kernel=2, tile_y=8, stages=7, zchunk=0, ctas_per_sm=0, use_graph=1)),
+    # small case of the same for ncu captures
+    "order4_256": dict(n=(256, 256, 256), steps=20, storage=0, sphere_seed=1, field_seed=2, spheres=8, order=4,
+                       tuning=dict(kernel=2, tile_y=8, stages=7, zchunk=0, ctas_per_sm=0, use_graph=1)),
 }
 # Launch configuration the bench times (the full-size parity test uses the same): the two-step
 # temporal-blocking kernel, 60 x 12-cell tiles (FP32), 6-slot TMA ring, graphs of 8 launches.
@@ -66,11 +72,29 @@ ID_BYTES = 1  # material id per cell
 MEASURED_TRAFFIC = {
     # ncu, 512^3 bench configuration, mean of three launches (profiles/fused2_step_512cube_f32_launches.md)
     ("single512", "785dd87ecd68ad08"): 6.73e9,
+    # ncu on the 256^3 case of the same kernel and launch shape (profiles/fused4_step_256cube_f32_full.md),
+    # scaled by the cell count (x 8): traffic grows in proportion to the cells
+    ("order4_512", "437a80be2782445b"): 6.35e9,
 }
 
 
-def kernel_source_hash() -> str:
-    src = {2: "k_fused.cu", 3: "k_fused2.cu"}.get(BENCH_TUNING["kernel"], "k_simple.cu")
+def tuning_of(w) -> dict:
+    return w.get("tuning", BENCH_TUNING)
+
+
+def dominant_kernel(w) -> str:
+    k = tuning_of(w)["kernel"]
+    if w.get("order", 2) == 4:
+        return {1: "simple4_h_kernel/simple4_e_kernel"}.get(k, "fused4_step_kernel")
+    return DOMINANT_KERNEL[k]
+
+
+def kernel_source_hash(w=None) -> str:
+    k = tuning_of(w or {})["kernel"]
+    if (w or {}).get("order", 2) == 4:
+        src = "k_order4.cu" if k == 1 else "k_fused4.cu"
+    else:
+        src = {2: "k_fused.cu", 3: "k_fused2.cu"}.get(k, "k_simple.cu")
     p = os.path.join(ROOT, "paper_2504_09118_gb300", "csrc", src)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
@@ -178,26 +202,28 @@ def cpu_baseline(w, budget_s: float = 12.0):
     ce_s, ch_s = ci.sphere_coefficients(sph, nx, ny, nzs, ci.COURANT_HALF_DT)
     f = oracle.as_f64(ci.random_fields(w["field_seed"], nx, ny, nzs))
     ce64 = [c.astype(np.float64) for c in ce_s]
+    step = oracle.step4 if w.get("order", 2) == 4 else oracle.step
     t0 = time.perf_counter()
-    oracle.step(f, ce64, ch_s, 1, omp=True)
+    step(f, ce64, ch_s, 1, omp=True)
     one = time.perf_counter() - t0
     steps = max(1, min(200, int(budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
-    oracle.step(f, ce64, ch_s, steps, omp=True)
+    step(f, ce64, ch_s, steps, omp=True)
     dt = time.perf_counter() - t0
     rate = nx * ny * nzs * steps / dt / 1e9
     # the same oracle on one thread (the paper's single-thread setting), 128^3 vacuum, a few steps
     g = oracle.as_f64(ci.random_fields(w["field_seed"], 128, 128, 128))
     t0 = time.perf_counter()
-    oracle.step(g, ci.COURANT_HALF_DT, ci.COURANT_HALF_DT, 1, omp=False)
+    step(g, ci.COURANT_HALF_DT, ci.COURANT_HALF_DT, 1, omp=False)
     one = time.perf_counter() - t0
     s1 = max(1, min(20, int(0.25 * budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
-    oracle.step(g, ci.COURANT_HALF_DT, ci.COURANT_HALF_DT, s1, omp=False)
+    step(g, ci.COURANT_HALF_DT, ci.COURANT_HALF_DT, s1, omp=False)
     d1 = time.perf_counter() - t0
     return {"value": round(rate, 4), "unit": "Gcell-updates/s", "cores": oracle.threads(True), "kind": "oracle",
             "sample": f"{nx}x{ny}x{nzs} slab of the {w['n'][0]}x{w['n'][1]}x{w['n'][2]} workload "
-                      f"(same sphere layout), FP64 OpenMP oracle, {steps} steps in {dt:.1f} s",
+                      f"(same sphere layout), FP64 OpenMP oracle (order {w.get('order', 2)}), {steps} steps "
+                      f"in {dt:.1f} s",
             "single_thread": {"value": round(128 ** 3 * s1 / d1 / 1e9, 4), "unit": "Gcell-updates/s",
                               "sample": f"128^3 vacuum, serial FP64 oracle, {s1} steps in {d1:.1f} s"}}
 
@@ -218,12 +244,15 @@ def run_reference(args, w, wname):
     ce64 = [c.astype(np.float64) for c in ce_s]
     f = oracle.as_f64(ci.random_fields(w["field_seed"], nx, ny, nzs))
     per_step = 2  # oracle leapfrog steps per bench step: a bounded sample of the solve
+    order4 = w.get("order", 2) == 4
+    step = oracle.step4 if order4 else oracle.step
+    energy = oracle.energy4 if order4 else oracle.energy
     for _ in range(args.warmup):
-        oracle.step(f, ce64, ch_s, 1, omp=True)
+        step(f, ce64, ch_s, 1, omp=True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.step(f, ce64, ch_s, per_step, omp=True)
-        oracle.energy(f, ce64, ch_s, ci.COURANT_HALF_DT)
+        step(f, ce64, ch_s, per_step, omp=True)
+        energy(f, ce64, ch_s, ci.COURANT_HALF_DT)
     dt = time.perf_counter() - t0
     val = nx * ny * nzs * per_step * args.steps / dt / 1e9
     line = {"impl": "reference", "metric": "Gcell-updates/s", "value": round(val, 4), "unit": "Gcell-updates/s",
@@ -445,8 +474,9 @@ def main():
     ce, ch = sphere_coefs(w)
     fields = ci.random_fields(w["field_seed"] + rank, nx, ny, nz)
     stream = torch.cuda.Stream()
-    cav = Cavity(nx, ny, nz, ci.COURANT_HALF_DT, 1.0, ce, ch, w["storage"], stream)
-    cav.tune(**BENCH_TUNING)
+    cav = Cavity(nx, ny, nz, ci.COURANT_HALF_DT, 1.0, ce, ch, w["storage"], stream, order=w.get("order", 2))
+    tuning = tuning_of(w)
+    cav.tune(**tuning)
     cav.set_fields(fields)
 
     def barrier():
@@ -487,19 +517,19 @@ def main():
     # the fused kernels reads and writes every field once (and reads the material id once), however
     # many leapfrog steps it advances; the solve is `per` steps = per / spl launches.
     esz = 4 if w["storage"] == 0 else 2
-    spl = STEPS_PER_LAUNCH[BENCH_TUNING["kernel"]]
+    spl = STEPS_PER_LAUNCH[tuning["kernel"]]
     alg_bytes = cells * (12 * esz + ID_BYTES)
     launches = per / spl
     launch_s = statistics.mean(k_ms) / 1e3 / launches
     achieved = alg_bytes / launch_s / 1e9
     peaks = measured_peaks()
     peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
-    tr = MEASURED_TRAFFIC.get((args.workload, kernel_source_hash()))
+    tr = MEASURED_TRAFFIC.get((args.workload, kernel_source_hash(w)))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": alg_bytes, "mean_launch_us": round(launch_s * 1e6, 2),
-                "kernel": DOMINANT_KERNEL[BENCH_TUNING["kernel"]], "steps_per_launch": spl,
+                "kernel": dominant_kernel(w), "steps_per_launch": spl,
                 # the same time against one HBM sweep per step (12 x storage + 1 bytes per cell-update):
                 # temporal blocking moves spl steps per sweep, so this exceeds the physical fraction
                 "per_cell_update": {"bytes": 12 * esz + ID_BYTES,
@@ -538,9 +568,10 @@ def main():
                 "dtype": {0: "f32", 1: "f16-storage/f32-math", 2: "bf16-storage/f32-math"}[w["storage"]],
                 "data": "synthetic",
                 "config": {"workload": args.workload, "cells": [nx, ny, nz], "leapfrog_steps_per_bench_step": per,
-                           "coefficients": "32 dielectric spheres, 1-byte material id", "parallelism": f"replicas x{ws}",
-                           "l2": "inputs larger than L2 (6.4 GB of fields per step)",
-                           "tuning": BENCH_TUNING, "hbm_fraction_of_roofline": round(achieved / peak, 4)},
+                           "coefficients": f"{w['spheres']} dielectric spheres, 1-byte material id",
+                           "parallelism": f"replicas x{ws}", "spatial_order": w.get("order", 2),
+                           "l2": f"inputs larger than L2 ({6 * esz * cells / 1e9:.1f} GB of fields read and as many written per launch)",
+                           "tuning": tuning, "hbm_fraction_of_roofline": round(achieved / peak, 4)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(args.steps * (launches + 2))}
         print(json.dumps(line), flush=True)

@@ -193,7 +193,7 @@ FDTD_API int fdtd_get_order(const fdtd_ctx *ctx);
  * fdtd_steps_done are unchanged.  The choice is kept per (nx, ny, nz, storage, coefficient
  * kind, spatial order) for the life of the process: a later call for the same shape applies it
  * without trials.  Contexts with per-position coefficient arrays keep the unfused kernel; with
- * order 4 the candidates are the fused fourth-order kernel with 4, 8, 16-row tiles and 4 or 6
+ * order 4 the candidates are the fused fourth-order kernel with 4, 8, 16-row tiles and 5 or 7
  * ring slots.  out
  * (may be NULL) receives the chosen tuning, ms_per_step (may be NULL) its time per step.
  * Requires fdtd_set_fields; synchronises the stream. */

@@ -324,7 +324,8 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0) {
     else
         s.tile_y = (t.tile_y == 8 || t.tile_y == 12) ? t.tile_y : 12;
     const int min_st = kind == 2 ? 4 : 3;
-    s.stages = (t.stages >= min_st && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : kind == 1 ? 6 : 5);
+    // default ring depths: measured best at 512^3 (the fourth-order kernel keeps three units resident)
+    s.stages = (t.stages >= min_st && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : kind == 1 ? 6 : 7);
     auto smem = [&](int st) {
         return kind == 0 ? fused_smem_bytes(storage, s.tile_y, st)
                : kind == 1 ? fused2_smem_bytes(storage, s.tile_y, st)
@@ -1018,7 +1019,7 @@ std::vector<fdtd_tuning> tune_candidates(bool batch, int order = 2) {
     std::vector<fdtd_tuning> v;
     if (order == 4) {   // the fused fourth-order kernel's tile heights and ring depths
         for (int ty : {4, 8, 16})
-            for (int st : {4, 6}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, st, 1});
+            for (int st : {5, 7}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, st, 1});
         return v;
     }
     for (int ty : {4, 8, 16}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, 4, 1});

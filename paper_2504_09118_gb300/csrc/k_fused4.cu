@@ -343,9 +343,9 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
                     const float2 dxEz = d4(make_float2(ez_l, ez_0.x), ez_0, make_float2(ez_0.y, ez_r.x), ez_r, wax_h, wbx_h);
                     const float2 dxEy = d4(make_float2(ey_l, eyw1.x), eyw1, make_float2(eyw1.y, ey_r.x), ey_r, wax_h, wbx_h);
                     // each bracket is -(curl E): H + ch * bracket
-                    hx = fma2(chx, sub2(dzEy, dyEz), hx);
-                    hy = fma2(chy, sub2(dxEz, dzEx), hy);
-                    hz = fma2(chz, sub2(dyEx, dxEy), hz);
+                    hx = fma2o(chx, sub2o(dzEy, dyEz), hx);
+                    hy = fma2o(chy, sub2o(dxEz, dzEx), hy);
+                    hz = fma2o(chz, sub2o(dyEx, dxEy), hz);
                     const bool a0 = vrow && v0, a1 = vrow && v1;
                     hx = make_float2(a0 ? hx.x : 0.f, a1 ? hx.y : 0.f);
                     hy = make_float2(a0 ? hy.x : 0.f, a1 ? hy.y : 0.f);
@@ -383,8 +383,8 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
                     const float2 dyEz = d4(ez_m1, ez_0, ez_p1, ez_p2, wy_a, wy_b);
                     const float2 dyEx = d4(ex_m1, ex_0, ex_p1, ex_p2, wy_a, wy_b);
                     const float2 dxEy = d4(make_float2(ey_l, eyw1.x), eyw1, make_float2(eyw1.y, ey_r.x), ey_r, wax_h, wbx_h);
-                    hx = fma2(chx, sub2(dzEy, dyEz), hx);
-                    hz = fma2(chz, sub2(dyEx, dxEy), hz);
+                    hx = fma2o(chx, sub2o(dzEy, dyEz), hx);
+                    hz = fma2o(chz, sub2o(dyEx, dxEy), hz);
                     const bool a0 = vrow && v0, a1 = vrow && v1;
                     const int o = (y + 2) * HP4 + x + 2;
                     *reinterpret_cast<float2 *>(hn + o) = make_float2(a0 ? hx.x : 0.f, a1 ? hx.y : 0.f);
@@ -448,9 +448,9 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
                 const float2 dxHz = d4(hz_l, make_float2(hz_l.y, hz_0.x), hz_0, make_float2(hz_0.y, hz_r), wax_e, wbx_e);
                 const float2 dxHy = d4(hy_l, make_float2(hy_l.y, hyw2.x), hyw2, make_float2(hyw2.y, hy_r), wax_e, wbx_e);
                 const float2 dyHx = d4(hx_m2, hx_m1, hxw2, hx_p1, wy_a, wy_b);
-                const float2 ex = fma2(cex, sub2(dyHz, dzHy), exw0);
-                const float2 ey = fma2(cey, sub2(dzHx, dxHz), eyw0);
-                const float2 ez = fma2(cez, sub2(dxHy, dyHx), ez_prev);
+                const float2 ex = fma2o(cex, sub2o(dyHz, dzHy), exw0);
+                const float2 ey = fma2o(cey, sub2o(dzHx, dxHz), eyw0);
+                const float2 ez = fma2o(cez, sub2o(dxHy, dyHx), ez_prev);
                 const long long g = (long long)e * plane + (long long)gj * pitch + gi;
                 if (gj < ny && gi < nx && store_ok(P.status, g, 2, plane * nz)) {
                     Pair<T>::st(dst[0] + g, ex.x, ex.y);

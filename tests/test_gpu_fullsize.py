@@ -145,3 +145,58 @@ def test_384_precision_1000_steps(storage):
     print(f"storage {storage}: rel-L2 vs FP32 GPU {err:.3e} (estimate {est:.3e}); energy drift {(w1 - w0) / w0:.3e}")
     assert err <= 3 * est
     assert abs(w1 - w0) / w0 <= 3 * est
+
+
+def test_512_fourth_order_sampled_parity_invariants_and_bitwise():
+    """The fourth-order workload at full size in the bench's launch configuration: sampled sub-boxes
+    against the oracle's step4 after 3 steps (a value then depends on inputs within 4 cells per step),
+    the scheme's energy and divergences over 200 steps, PEC bits, and the fused kernel bit-identical to
+    the unfused one."""
+    import oracle
+    from paper_2504_09118_gb300 import Cavity
+    w = bench.WORKLOADS["order4_512"]
+    n = w["n"]
+    ce, ch = bench.sphere_coefs(w)
+    f = ci.random_fields(w["field_seed"], *n)
+    s = 3
+    with Cavity(*n, DT, 1.0, ce, ch, order=4) as cav:
+        cav.tune(**w["tuning"])
+        cav.set_fields(f)
+        w0 = cav.energy()
+        d0 = cav.divergence()
+        cav.step(s)
+        g = cav.get_fields()
+        N = n[0]
+        R = 22
+        for (cx, cy, cz) in [(0, 0, 0), (N, N, N), (N // 2, N // 2, N // 2), (63, 200, 17), (511, 64, 130)]:
+            a = [max(0, c - R) for c in (cx, cy, cz)]
+            b = [min(N, c + R) for c in (cx, cy, cz)]
+            sub = oracle.as_f64([_sub(x, a, b) for x in f])
+            sce = [_sub(x, a, b).astype(np.float64) for x in ce]
+            oracle.pec_e(sub)
+            oracle.step4(sub, sce, ch, s)
+            m = 4 * s + 2
+            sl = tuple(slice(m if lo > 0 else 0, (hi - lo + 1) - m if hi < N else hi - lo + 1)
+                       for lo, hi in ((a[2], b[2]), (a[1], b[1]), (a[0], b[0])))
+            for c, name in enumerate(ci.COMPONENTS):
+                got = _sub(g[c], a, b)[sl].astype(np.float64)
+                ref = sub[c][sl]
+                mask = ci.extent_mask(name, b[0] - a[0], b[1] - a[1], b[2] - a[2])[sl]
+                err = np.linalg.norm(got[mask] - ref[mask]) / max(np.linalg.norm(ref[mask]), 1e-30)
+                assert err <= REL_L2_F32, (name, (cx, cy, cz), err)
+        cav.step(200 - s)
+        w1 = cav.energy()
+        d1 = cav.divergence()
+        assert abs(w1 - w0) / w0 <= ENERGY_DRIFT_F32, (w0, w1)
+        assert abs(d1[0] - d0[0]) / d0[0] <= 1e-5 and abs(d1[1] - d0[1]) / d0[1] <= 1e-5
+        fused = cav.get_fields()
+        for c, name in enumerate(("Ex", "Ey", "Ez")):
+            assert np.all(fused[c][ci.tangential_e_mask(name, *n)] == 0.0)
+    del g
+    with Cavity(*n, DT, 1.0, ce, ch, order=4) as cav:
+        cav.tune(kernel=1)
+        cav.set_fields(f)
+        cav.step(200)
+        unfused = cav.get_fields()
+    for name, x, y in zip(ci.COMPONENTS, fused, unfused):
+        assert np.array_equal(x, y), name
