@@ -347,9 +347,9 @@ def run_serve(args, w):
         shape = (r.nz + 1, r.ny + 1, r.nx + 1)
         return [torch.rand(shape, generator=gen, device="cuda") * 2 - 1 for _ in range(6)]
 
-    def make_server():
+    def make_server(retune=False):
         return Server(ci.COURANT_HALF_DT, hbm_budget_bytes=int(w["budget_gb"] * (1 << 30)), max_slots=1024, K=16,
-                      tuning=SERVE_TUNING, result="energy", fields_fn=fields_fn)
+                      tuning=SERVE_TUNING, result="energy", fields_fn=fields_fn, retune=retune)
 
     # untimed warm-up: a short stream of the same recipe (another seed) through a server of its own, so
     # that library load, pool growth, tensor maps and graph captures are not charged to the timed stream
@@ -363,6 +363,21 @@ def run_serve(args, w):
     with ClockSampler(0, args.clocks_csv) as clk:
         st = srv.run(reqs)
     srv.close()
+    # the same stream with online re-tuning (size-bucket model in the library; the warm-up stream, served
+    # the same way first, leaves the model with the buckets it met)
+    online = None
+    if args.serve_retune:
+        if warm:
+            srv = make_server(retune=True)
+            srv.run([Request(q["id"], q["arrival_s"], q["nx"], q["ny"], q["nz"], q["steps"], q["bf16"]) for q in warm])
+            srv.close()
+        srv = make_server(retune=True)
+        st_r = srv.run([Request(q["id"], q["arrival_s"], q["nx"], q["ny"], q["nz"], q["steps"], q["bf16"])
+                        for q in stream])
+        online = {"gcells": round(st_r.gcells, 3), "p50_s": round(st_r.p50_s, 4), "p99_s": round(st_r.p99_s, 4),
+                  "wall_s": round(st_r.wall_s, 3), "retunes": {k: (round(v, 3) if isinstance(v, float) else v)
+                                                               for k, v in srv.retunes.items()}}
+        srv.close()
     nseq = min(len(stream), args.serve_seq_requests)
     seq_reqs = [Request(q["id"], q["arrival_s"], q["nx"], q["ny"], q["nz"], q["steps"], q["bf16"])
                 for q in stream[:nseq]]
@@ -379,7 +394,8 @@ def run_serve(args, w):
                         "offered_gcells": round(st.cell_updates / max(r["arrival_s"] for r in stream) / 1e9, 2)},
             "sequential": {"requests": sq.n, "gcells": round(sq.gcells, 3), "p50_s": round(sq.p50_s, 4),
                            "p99_s": round(sq.p99_s, 4), "closed_loop": True},
-            "served_vs_sequential": round(st.gcells / sq.gcells, 3), "clocks": clk.summary()}
+            "served_vs_sequential": round(st.gcells / sq.gcells, 3), "online_retune": online,
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -443,6 +459,8 @@ def main():
     ap.add_argument("--clocks-csv", default=None)
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-seq-requests", type=int, default=150)
+    ap.add_argument("--serve-retune", action="store_true",
+                    help="serve the stream a second time with online re-tuning (fdtd_batch_retune)")
     ap.add_argument("--precision-steps", type=int, default=0)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]

@@ -280,6 +280,17 @@ FDTD_API int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t);
  * members change).  out / ms_per_step may be NULL.  Synchronises the batch stream. */
 FDTD_API int fdtd_batch_autotune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double *ms_per_step);
 
+/* fdtd_batch_retune - online re-tuning from a size-bucket model, for a batch whose members change
+ * (continuous batching).  The bucket of a batch is (storage, floor(log2 C)) with C the total cell
+ * count of its running members (those with steps left; all members when none has).
+ * The first call for a bucket runs fdtd_batch_autotune on the batch as it is (same trials, same state
+ * restoration) and keeps the choice for the life of the process; a later call whose batch falls in a
+ * bucket already timed applies that choice without trials (and without touching the batch when the
+ * choice is the current tuning).  out / ms_per_step (the bucket's timed ms per step) / timed (1 when
+ * this call ran the trials, 0 when it used the model) may be NULL.  Errors as fdtd_batch_autotune;
+ * synchronises the batch stream only when it times. */
+FDTD_API int fdtd_batch_retune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double *ms_per_step, int *timed);
+
 /* fdtd_batch_size - number of members (-1 for NULL). */
 FDTD_API int fdtd_batch_size(const fdtd_batch *b);
 

@@ -31,7 +31,7 @@ EXPORTS = (
     "fdtd_batch_size", "fdtd_batch_sync", "fdtd_batch_destroy", "fdtd_batch_last_error",
     "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static", "fdtd_batch_set_steps",
     "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune", "fdtd_set_sources", "fdtd_set_probes",
-    "fdtd_get_probes", "fdtd_set_order", "fdtd_get_order",
+    "fdtd_get_probes", "fdtd_set_order", "fdtd_get_order", "fdtd_batch_retune",
 )
 
 
@@ -106,6 +106,8 @@ def lib() -> ctypes.CDLL:
             L.fdtd_set_probes.argtypes = [vp, i, vp, vp, i]
             L.fdtd_get_probes.argtypes = [vp, vp, ctypes.POINTER(i)]
             L.fdtd_set_order.argtypes = [vp, i]
+            L.fdtd_batch_retune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d),
+                                            ctypes.POINTER(i)]
             L.fdtd_get_order.argtypes = [vp]
             _LIB = L
         return _LIB
@@ -379,6 +381,15 @@ def fdtd_batch_autotune(b, trial_steps: int = 16) -> tuple[dict, float]:
     ms = ctypes.c_double()
     _bcheck(b, lib().fdtd_batch_autotune(b, int(trial_steps), ctypes.byref(t), ctypes.byref(ms)))
     return _tuning_dict(t), float(ms.value)
+
+
+def fdtd_batch_retune(b, trial_steps: int = 16) -> tuple[dict, float, bool]:
+    """Online re-tuning from the size-bucket model: (tuning, bucket ms per step, whether trials ran)."""
+    t = fdtd_tuning()
+    ms = ctypes.c_double()
+    timed = ctypes.c_int()
+    _bcheck(b, lib().fdtd_batch_retune(b, int(trial_steps), ctypes.byref(t), ctypes.byref(ms), ctypes.byref(timed)))
+    return _tuning_dict(t), float(ms.value), bool(timed.value)
 
 
 def fdtd_batch_set_steps(b, ctx, nsteps: int) -> None:

@@ -1772,6 +1772,72 @@ int fdtd_batch_autotune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double
     return FDTD_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Online re-tuning: a size-bucket model of batch tunings.  A bucket is (storage, floor(log2 of the
+// running members' total cells)); the first batch seen in a bucket is timed by fdtd_batch_autotune,
+// later ones take the bucket's choice without trials.
+namespace {
+
+std::mutex g_btune_mu;
+std::map<std::pair<int, int>, std::pair<fdtd_tuning, double>> g_btune_cache;
+
+int floor_log2(long long v) {
+    int r = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+bool same_tuning(const fdtd_tuning &a, const fdtd_tuning &b) {
+    return a.kernel == b.kernel && a.tile_y == b.tile_y && a.zchunk == b.zchunk && a.ctas_per_sm == b.ctas_per_sm &&
+           a.stages == b.stages && a.use_graph == b.use_graph;
+}
+
+}  // namespace
+
+int fdtd_batch_retune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double *ms_per_step, int *timed) {
+    if (!b) return FDTD_ERR_ARG;
+    if (b->members.empty()) return bfail(b, FDTD_ERR_STATE, "retune: the batch has no members");
+    long long cells = 0, running = 0;
+    for (const auto &mb : b->members)
+        if (mb.stop > b->step) {
+            cells += (long long)mb.c->nx * mb.c->ny * mb.c->nz;
+            ++running;
+        }
+    if (running == 0)   // every member has taken its steps: bucket by all of them
+        for (const auto &mb : b->members) {
+            cells += (long long)mb.c->nx * mb.c->ny * mb.c->nz;
+            ++running;
+        }
+    const auto key = std::make_pair(b->storage, floor_log2(cells));
+    fdtd_tuning t{};
+    double ms = -1.0;
+    bool hit = false;
+    {
+        std::lock_guard<std::mutex> g(g_btune_mu);
+        auto it = g_btune_cache.find(key);
+        if (it != g_btune_cache.end()) {
+            t = it->second.first;
+            ms = it->second.second;
+            hit = true;
+        }
+    }
+    if (hit) {
+        if (!same_tuning(t, b->tuning))
+            if (int rc = fdtd_batch_set_tuning(b, &t)) return rc;
+    } else {
+        if (int rc = fdtd_batch_autotune(b, trial_steps, &t, &ms)) return rc;
+        std::lock_guard<std::mutex> g(g_btune_mu);
+        g_btune_cache[key] = {t, ms};
+    }
+    if (out) *out = t;
+    if (ms_per_step) *ms_per_step = ms;
+    if (timed) *timed = hit ? 0 : 1;
+    return FDTD_OK;
+}
+
 int fdtd_batch_sync(fdtd_batch *b) {
     if (!b) return FDTD_ERR_ARG;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "sync");

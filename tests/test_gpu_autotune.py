@@ -85,3 +85,34 @@ def test_batch_autotune_keeps_members():
     for c, *_ in solo + mem:
         c.close()
     solo7.close()
+
+
+def test_batch_retune_uses_the_size_bucket_model():
+    """The first retune of a size bucket times the candidates on the live members (state restored); the
+    next call in the same bucket applies the model's choice without trials; results stay bit-exact."""
+    import torch
+    from paper_2504_09118_gb300 import binding
+    s = torch.cuda.Stream()
+    solo = make_members(0, s, seed=31)
+    for c, *_ in solo:
+        c.tune(kernel=2, tile_y=8)
+        c.step(3 + 29)
+    ref = [c.get_fields() for c, *_ in solo]
+    mem = make_members(0, s, seed=31)
+    b = binding.fdtd_batch_create(0, s)
+    try:
+        for c, *_ in mem:
+            binding.fdtd_batch_add(b, c.handle)
+        binding.fdtd_batch_step(b, 3)
+        t1, ms1, _ = binding.fdtd_batch_retune(b, 16)
+        assert t1["kernel"] in (2, 3) and ms1 > 0
+        t2, ms2, timed2 = binding.fdtd_batch_retune(b, 16)
+        assert not timed2 and t2 == t1 and ms2 == ms1
+        assert binding.fdtd_batch_steps_done(b) == 3
+        binding.fdtd_batch_step(b, 29)
+        for (c, *_), r in zip(mem, ref):
+            binding.fdtd_batch_remove(b, c.handle)
+            for x, y in zip(c.get_fields(), r):
+                assert np.array_equal(x, y)
+    finally:
+        binding.fdtd_batch_destroy(b)

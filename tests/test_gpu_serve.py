@@ -70,3 +70,21 @@ def test_sequential_baseline_same_results():
         ref = solo(r)
         for a, b in zip(r.result, ref):
             assert np.array_equal(a, b)
+
+
+def test_online_retune_keeps_results():
+    """With online re-tuning the batch's kernel may change between chunks; FP32 results of both fused
+    kernels agree bit for bit, so every result still equals its solo run."""
+    from paper_2504_09118_gb300.serve import Server
+    reqs = [r for r in stream_requests(30, 3) if r.storage == 0]
+    srv = Server(DT, result="fields", K=16, tuning={"kernel": 3, "tile_y": 12}, retune=True)
+    try:
+        st = srv.run(reqs)
+    finally:
+        srv.close()
+    assert st.n == len(reqs)
+    assert srv.retunes["timed"] + srv.retunes["model"] >= 1
+    for r in reqs:
+        ref = solo(r, 2)
+        for a, b in zip(r.result, ref):
+            assert np.array_equal(a, b), r.id
