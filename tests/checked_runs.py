@@ -14,6 +14,8 @@ DT = ci.COURANT_HALF_DT
 DIMS = [(1, 3, 2), (7, 9, 11), (61, 13, 5), (64, 8, 3), (65, 17, 9), (121, 40, 7), (130, 67, 12), (2, 70, 5)]
 TUNINGS = [dict(kernel=1), dict(kernel=2, tile_y=4), dict(kernel=2, tile_y=16, zchunk=3),
            dict(kernel=3, tile_y=8), dict(kernel=3, tile_y=12, zchunk=2, stages=3)]
+TUNINGS4 = [dict(kernel=1), dict(kernel=2, tile_y=4, stages=4), dict(kernel=2, tile_y=8, zchunk=3),
+            dict(kernel=2, tile_y=16, stages=5)]
 
 
 def run_all() -> dict:
@@ -32,6 +34,19 @@ def run_all() -> dict:
                     cav.step(7)
                     for c, a in enumerate(cav.get_fields()):
                         out[f"c{d_i}_s{storage}_t{t_i}_{c}"] = a
+    # the fourth-order kernels: every tile height, a short z-chunk, the unfused path
+    for d_i, dims in enumerate(DIMS):
+        sph = ci.sphere_list(d_i, 3, dims, 2.0, max(2.5, min(dims) / 3)) if min(dims) >= 8 else None
+        ce, ch = ci.sphere_coefficients(sph, *dims, DT) if sph else (None, None)
+        f = ci.random_fields(70 + d_i, *dims)
+        for storage in (0, 2):
+            for t_i, t in enumerate(TUNINGS4):
+                with Cavity(*dims, DT, 1.0, ce, ch, storage, order=4) as cav:
+                    cav.tune(**t)
+                    cav.set_fields(f)
+                    cav.step(7)
+                    for c, a in enumerate(cav.get_fields()):
+                        out[f"o4_c{d_i}_s{storage}_t{t_i}_{c}"] = a
     # a batch of members with their own step counts, both kernels
     s = torch.cuda.Stream()
     for kernel in (2, 3):

@@ -200,3 +200,31 @@ def test_512_fourth_order_sampled_parity_invariants_and_bitwise():
         unfused = cav.get_fields()
     for name, x, y in zip(ci.COMPONENTS, fused, unfused):
         assert np.array_equal(x, y), name
+
+
+def test_128_crop_fourth_order_vs_oracle():
+    """The 128^3 crop of the 512^3 sphere layout, 200 fourth-order steps in the bench's fourth-order
+    launch configuration, element-wise against the FP64 oracle's step4."""
+    import oracle
+    from paper_2504_09118_gb300 import Cavity
+    w = bench.WORKLOADS["order4_512"]
+    sph = ci.sphere_list(w["sphere_seed"], w["spheres"], w["n"], 8.0, 40.0)
+    n = (128, 128, 128)
+    ce, ch = ci.sphere_coefficients(sph, *n, DT)
+    f = ci.random_fields(w["field_seed"] + 19, *n)
+    with Cavity(*n, DT, 1.0, ce, ch, order=4) as cav:
+        cav.tune(**w["tuning"])
+        cav.set_fields(f)
+        w0 = cav.energy()
+        cav.step(200)
+        w1 = cav.energy()
+        got = cav.get_fields()
+    ref = oracle.as_f64(f)
+    oracle.step4(ref, [c.astype(np.float64) for c in ce], ch, 200, omp=True)
+    norm = float(np.sqrt(sum(np.sum(r ** 2) for r in ref)))
+    for c, name in enumerate(ci.COMPONENTS):
+        m = ci.extent_mask(name, *n)
+        d = np.linalg.norm(got[c][m].astype(np.float64) - ref[c][m])
+        r = np.linalg.norm(ref[c][m])
+        assert d / max(r, 1e-30 * norm) <= REL_L2_F32, (name, d / r)
+    assert abs(w1 - w0) / w0 <= ENERGY_DRIFT_F32
