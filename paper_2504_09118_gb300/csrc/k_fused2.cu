@@ -18,9 +18,9 @@
 // from small shared planes (H1 and H2: Hx, Hz of the row above; E1: Ex, Ez of the row
 // below, double-buffered in z); z neighbours stay in registers.
 //
-// Per z-plane iteration j: [H1(j)] bar [E1(j)] bar [H2(j-1)] bar [E2(j-1) + stores], the
-// last phase running into the next plane's H1 (they share no data).  A producer warp
-// streams plane units (six field boxes with a 2-cell halo in y, id box) through an
+// Per z-plane iteration j: [H1(j)] bar [E1(j)] [H2(j-1)] bar [E2(j-1) + stores], the last phase
+// running into the next plane's H1 (they share no data); H2(j-1) reads no E1(j) of another warp, so
+// E1 and H2 need no barrier between them.  A producer warp streams plane units (six field boxes with a 2-cell halo in y, id box) through an
 // S-slot TMA ring exactly as the one-step kernel does; waits are bounded and a shared
 // abort flag ends the CTA together (see k_fused.cu).
 #include "fused_common.cuh"
@@ -330,7 +330,10 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                     }
                 }
             }
-            asm volatile("bar.sync 1, %0;" ::"r"(NCT) : "memory");
+            // No barrier here: phase 3 reads only this lane's E1(k), its warp's E1(k-1) (shuffles) and the
+            // row below's E1(k-1), written in the previous iteration (e1prv, the other buffer).  The
+            // write-after-read hazards are covered by the remaining barriers: E1(k+1) overwrites e1prv's
+            // buffer after the phase-3 -> 4 barrier of this iteration and the phase-1 -> 2 barrier of the next.
 
             // ---------------- phase 3: H2(k-1) = H1(k-1) - ch curl E1 (plane k-1, z+1 from plane k)
             float2 h2x = zero2, h2y = zero2, h2z = zero2;
