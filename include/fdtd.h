@@ -71,7 +71,7 @@ enum fdtd_status {
 
 /* Step kernels (fdtd_tuning.kernel). */
 enum fdtd_kernel {
-    FDTD_KERNEL_AUTO = 0,    /* TEMPORAL with 12-row tiles where it applies (else FUSED; SIMPLE for
+    FDTD_KERNEL_AUTO = 0,    /* TEMPORAL with 16-row tiles where it applies (else FUSED; SIMPLE for
                                 per-position coefficient arrays); fdtd_autotune picks by timing */
     FDTD_KERNEL_SIMPLE = 1,  /* two launches per step (H, then E), one thread per cell; unfused baseline */
     FDTD_KERNEL_FUSED = 2,   /* one TMA-pipelined launch per step: H then E fused in a z-march */
@@ -81,7 +81,7 @@ enum fdtd_kernel {
 /* Launch configuration of the step kernel; zero fields take the default. */
 typedef struct fdtd_tuning {
     int kernel;       /* enum fdtd_kernel */
-    int tile_y;       /* fused: cells per tile along y (FUSED: 4, 8 or 16; TEMPORAL: 8 or 12; AUTO: any
+    int tile_y;       /* fused: cells per tile along y (FUSED: 4, 8 or 16; TEMPORAL: 8, 12 or 16; AUTO: any
                          of these, each kernel taking its default when the value is not one of its
                          own); x tile is 64 cells (TEMPORAL: 60 for FP32, 56 for 16-bit storage) */
     int zchunk;       /* fused: planes per tile along z (>= 1); 0 = choose for load balance */
@@ -186,7 +186,7 @@ FDTD_API int fdtd_get_order(const fdtd_ctx *ctx);
 
 /* fdtd_autotune - choose the step kernel and launch shape by timing candidates on this
  * context's own state: the one-step kernel with 4, 8, 16-row tiles and the two-step kernel with
- * 8, 12-row tiles and 4 or 6 ring slots (graphs on).  Each candidate runs trial_steps steps
+ * 8, 12, 16-row tiles and 4 or 6 ring slots (graphs on).  Each candidate runs trial_steps steps
  * (rounded up to a multiple of 16; <= 0: 16) after one untimed run of the same length, timed
  * with CUDA events on the context's stream.  The fields are copied aside first (one extra copy
  * of the active arrays, freed before return) and restored afterwards, so the state and
@@ -274,7 +274,7 @@ FDTD_API int fdtd_batch_step(fdtd_batch *b, int nsteps);
 FDTD_API int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t);
 
 /* fdtd_batch_autotune - fdtd_autotune for a batch over its current members: the one-step kernel
- * with 4, 8, 16-row tiles and the two-step kernel with 8, 12-row tiles, each timed over
+ * with 4, 8, 16-row tiles and the two-step kernel with 8, 12, 16-row tiles, each timed over
  * trial_steps batch steps (rounded up to a multiple of 16; <= 0: 16) after an untimed run.
  * Members' fields, step counts and the batch clock are restored afterwards.  Not cached (the
  * members change).  out / ms_per_step may be NULL.  Synchronises the batch stream. */

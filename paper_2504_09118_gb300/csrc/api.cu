@@ -322,7 +322,7 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0) {
     if (kind != 1)
         s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 16) ? t.tile_y : 8;
     else
-        s.tile_y = (t.tile_y == 8 || t.tile_y == 12) ? t.tile_y : 12;
+        s.tile_y = (t.tile_y == 8 || t.tile_y == 12 || t.tile_y == 16) ? t.tile_y : 16;
     const int min_st = kind == 2 ? 4 : 3;
     // default ring depths: measured best at 512^3 (the fourth-order kernel keeps three units resident)
     s.stages = (t.stages >= min_st && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : kind == 1 ? 6 : 7);
@@ -975,11 +975,12 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
     if (n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
     if (n.kernel == FDTD_KERNEL_TEMPORAL && c->order != 2)
         return fail(c, FDTD_ERR_ARG, "the two-step kernel runs the second-order scheme only");
-    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16, ty_two = n.tile_y == 8 || n.tile_y == 12;
+    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16,
+               ty_two = n.tile_y == 8 || n.tile_y == 12 || n.tile_y == 16;
     if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL ? ty_two
                       : n.kernel == FDTD_KERNEL_AUTO   ? (ty_one || ty_two)
                                                        : ty_one))
-        return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (8 or 12 for the two-step kernel)");
+        return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (8, 12 or 16 for the two-step kernel)");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return fail(c, FDTD_ERR_ARG, "stages must be in [3, 8]");
     if (n.stages == 3 && c->order == 4) return fail(c, FDTD_ERR_ARG, "the fourth-order kernel needs stages >= 4");
     if (n.zchunk < 0 || n.ctas_per_sm < 0) return fail(c, FDTD_ERR_ARG, "negative tuning value");
@@ -1023,7 +1024,7 @@ std::vector<fdtd_tuning> tune_candidates(bool batch, int order = 2) {
         return v;
     }
     for (int ty : {4, 8, 16}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, 4, 1});
-    for (int ty : {8, 12})
+    for (int ty : {8, 12, 16})
         for (int st : {4, 6}) {
             if (batch && st != 4) continue;
             v.push_back(fdtd_tuning{FDTD_KERNEL_TEMPORAL, ty, 0, 0, st, 1});
@@ -1533,7 +1534,8 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t) {
     if (t) n = *t;
     if (n.kernel == FDTD_KERNEL_SIMPLE || n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL)
         return bfail(b, FDTD_ERR_ARG, "batches use the fused kernels (FUSED or TEMPORAL)");
-    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16, ty_two = n.tile_y == 8 || n.tile_y == 12;
+    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16,
+               ty_two = n.tile_y == 8 || n.tile_y == 12 || n.tile_y == 16;
     if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL ? ty_two
                       : n.kernel == FDTD_KERNEL_AUTO   ? (ty_one || ty_two)
                                                        : ty_one))

@@ -65,7 +65,7 @@ def test_two_step_equals_one_step_bitwise_f32(dims, mat):
         assert_bitwise(a, b)
 
 
-@pytest.mark.parametrize("tile_y", [8, 12])
+@pytest.mark.parametrize("tile_y", [8, 12, 16])
 @pytest.mark.parametrize("stages", [3, 5, 8])
 @pytest.mark.parametrize("zchunk", [0, 1, 2, 7])
 def test_two_step_tuning_grid(tile_y, stages, zchunk):
@@ -163,7 +163,7 @@ def test_two_step_pec_and_far_faces(storage):
 def test_two_step_tuning_rejects_bad_tile():
     from paper_2504_09118_gb300 import Cavity, FdtdError
     with Cavity(8, 8, 8, DT, 1.0, None, None, 0) as cav:
-        for bad in (4, 10, 16):
+        for bad in (4, 10, 20):
             with pytest.raises(FdtdError):
                 cav.tune(kernel=3, tile_y=bad)
         cav.tune(kernel=3, tile_y=12)
