@@ -52,10 +52,10 @@ WORKLOADS = {
     "precision": dict(kind="precision", n=(384, 384, 384), steps=1000, sphere_seed=3, field_seed=4, spheres=32),
     # the fourth-order (2,4) scheme on the single512 cavity (fused fourth-order kernel, one step per launch)
     "order4_512": dict(n=(512, 512, 512), steps=200, storage=0, sphere_seed=1, field_seed=2, spheres=32, order=4,
-                       tuning=dict(kernel=2, tile_y=8, stages=7, zchunk=0, ctas_per_sm=0, use_graph=1)),
+                       tuning=dict(kernel=2, tile_y=12, stages=5, zchunk=0, ctas_per_sm=0, use_graph=1)),
     # small case of the same for ncu captures
     "order4_256": dict(n=(256, 256, 256), steps=20, storage=0, sphere_seed=1, field_seed=2, spheres=8, order=4,
-                       tuning=dict(kernel=2, tile_y=8, stages=7, zchunk=0, ctas_per_sm=0, use_graph=1)),
+                       tuning=dict(kernel=2, tile_y=12, stages=5, zchunk=0, ctas_per_sm=0, use_graph=1)),
 }
 # Launch configuration the bench times (the full-size parity test uses the same): the two-step
 # temporal-blocking kernel, 60 x 16-cell tiles (FP32), 4-slot TMA ring (what fits beside 16-row
@@ -75,7 +75,7 @@ MEASURED_TRAFFIC = {
     ("single512", "eaf5af25216c7bd7"): 7.24e9,
     # ncu on the 256^3 case of the same kernel and launch shape (profiles/fused4_step_256cube_f32_full.md),
     # scaled by the cell count (x 8): traffic grows in proportion to the cells
-    ("order4_512", "437a80be2782445b"): 6.35e9,
+    ("order4_512", "0e56f782532f783a"): 6.38e9,
 }
 
 

@@ -172,7 +172,7 @@ FDTD_API int fdtd_set_tuning(fdtd_ctx *ctx, const fdtd_tuning *t);
  * mirrored evenly and B = H/ch oddly past a wall), the invariants of this scheme.
  *
  * Kernels with order 4: FUSED (and AUTO) run the fused fourth-order kernel (one launch per step;
- * tile_y 4, 8 or 16; stages 4..8), SIMPLE the unfused one (also the path for per-position
+ * tile_y 4, 8, 12 or 16, default 12; stages 4..8, default the deepest ring that fits), SIMPLE the unfused one (also the path for per-position
  * coefficient arrays); TEMPORAL is not available.  Returns FDTD_ERR_UNSTABLE when the scheme's
  * Courant bound fails (order 4: max sqrt(3 ce ch) * 7/6 > 1, as the difference's symbol reaches
  * c1 - c2 = 7/6), FDTD_ERR_ARG for another order or a TEMPORAL / stages = 3 tuning, FDTD_ERR_STATE
@@ -193,8 +193,8 @@ FDTD_API int fdtd_get_order(const fdtd_ctx *ctx);
  * fdtd_steps_done are unchanged.  The choice is kept per (nx, ny, nz, storage, coefficient
  * kind, spatial order) for the life of the process: a later call for the same shape applies it
  * without trials.  Contexts with per-position coefficient arrays keep the unfused kernel; with
- * order 4 the candidates are the fused fourth-order kernel with 4, 8, 16-row tiles and 5 or 7
- * ring slots.  out
+ * order 4 the candidates are the fused fourth-order kernel with 4, 8, 12, 16-row tiles and the
+ * deepest ring that fits or 4 slots.  out
  * (may be NULL) receives the chosen tuning, ms_per_step (may be NULL) its time per step.
  * Requires fdtd_set_fields; synchronises the stream. */
 FDTD_API int fdtd_autotune(fdtd_ctx *ctx, int trial_steps, fdtd_tuning *out, double *ms_per_step);

@@ -319,13 +319,16 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0) {
     static std::map<int, int> occ_cache;   // (kind, storage, tile_y, stages) -> max CTAs per SM
     Shape s;
     s.kind = kind;
-    if (kind != 1)
+    if (kind == 2)
+        s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 12 || t.tile_y == 16) ? t.tile_y : 12;
+    else if (kind == 0)
         s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 16) ? t.tile_y : 8;
     else
         s.tile_y = (t.tile_y == 8 || t.tile_y == 12 || t.tile_y == 16) ? t.tile_y : 16;
     const int min_st = kind == 2 ? 4 : 3;
-    // default ring depths: measured best at 512^3 (the fourth-order kernel keeps three units resident)
-    s.stages = (t.stages >= min_st && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : kind == 1 ? 6 : 7);
+    // default ring depths: measured best at 512^3; the fourth-order kernel (three units resident) takes
+    // the deepest ring that fits, which measured best for each of its tile heights
+    s.stages = (t.stages >= min_st && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : kind == 1 ? 6 : 8);
     auto smem = [&](int st) {
         return kind == 0 ? fused_smem_bytes(storage, s.tile_y, st)
                : kind == 1 ? fused2_smem_bytes(storage, s.tile_y, st)
@@ -975,12 +978,13 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
     if (n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
     if (n.kernel == FDTD_KERNEL_TEMPORAL && c->order != 2)
         return fail(c, FDTD_ERR_ARG, "the two-step kernel runs the second-order scheme only");
-    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16,
+    // one-step kernels: 4, 8 or 16 rows (the fourth-order kernel also 12); two-step kernel: 8, 12 or 16
+    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16 || (c->order == 4 && n.tile_y == 12),
                ty_two = n.tile_y == 8 || n.tile_y == 12 || n.tile_y == 16;
     if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL ? ty_two
                       : n.kernel == FDTD_KERNEL_AUTO   ? (ty_one || ty_two)
                                                        : ty_one))
-        return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (8, 12 or 16 for the two-step kernel)");
+        return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (fourth order: also 12; two-step kernel: 8, 12 or 16)");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return fail(c, FDTD_ERR_ARG, "stages must be in [3, 8]");
     if (n.stages == 3 && c->order == 4) return fail(c, FDTD_ERR_ARG, "the fourth-order kernel needs stages >= 4");
     if (n.zchunk < 0 || n.ctas_per_sm < 0) return fail(c, FDTD_ERR_ARG, "negative tuning value");
@@ -1018,9 +1022,9 @@ namespace {
 
 std::vector<fdtd_tuning> tune_candidates(bool batch, int order = 2) {
     std::vector<fdtd_tuning> v;
-    if (order == 4) {   // the fused fourth-order kernel's tile heights and ring depths
-        for (int ty : {4, 8, 16})
-            for (int st : {5, 7}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, st, 1});
+    if (order == 4) {   // the fused fourth-order kernel's tile heights, deepest ring that fits (0) or 4 slots
+        for (int ty : {4, 8, 12, 16})
+            for (int st : {0, 4}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, st, 1});
         return v;
     }
     for (int ty : {4, 8, 16}) v.push_back(fdtd_tuning{FDTD_KERNEL_FUSED, ty, 0, 0, 4, 1});

@@ -506,14 +506,17 @@ cudaError_t occupancy4_typed(int stages, int *n) {
         if (storage == 0) {                                                                        \
             if (tile_y == 4) { using T = float; constexpr int TY = 4; __VA_ARGS__; }               \
             else if (tile_y == 8) { using T = float; constexpr int TY = 8; __VA_ARGS__; }          \
+            else if (tile_y == 12) { using T = float; constexpr int TY = 12; __VA_ARGS__; }          \
             else if (tile_y == 16) { using T = float; constexpr int TY = 16; __VA_ARGS__; }        \
         } else if (storage == 1) {                                                                 \
             if (tile_y == 4) { using T = __half; constexpr int TY = 4; __VA_ARGS__; }              \
             else if (tile_y == 8) { using T = __half; constexpr int TY = 8; __VA_ARGS__; }         \
+            else if (tile_y == 12) { using T = __half; constexpr int TY = 12; __VA_ARGS__; }         \
             else if (tile_y == 16) { using T = __half; constexpr int TY = 16; __VA_ARGS__; }       \
         } else if (storage == 2) {                                                                 \
             if (tile_y == 4) { using T = __nv_bfloat16; constexpr int TY = 4; __VA_ARGS__; }       \
             else if (tile_y == 8) { using T = __nv_bfloat16; constexpr int TY = 8; __VA_ARGS__; }  \
+            else if (tile_y == 12) { using T = __nv_bfloat16; constexpr int TY = 12; __VA_ARGS__; }  \
             else if (tile_y == 16) { using T = __nv_bfloat16; constexpr int TY = 16; __VA_ARGS__; } \
         }                                                                                          \
     } while (0)

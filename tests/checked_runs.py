@@ -15,7 +15,7 @@ DIMS = [(1, 3, 2), (7, 9, 11), (61, 13, 5), (64, 8, 3), (65, 17, 9), (121, 40, 7
 TUNINGS = [dict(kernel=1), dict(kernel=2, tile_y=4), dict(kernel=2, tile_y=16, zchunk=3),
            dict(kernel=3, tile_y=8), dict(kernel=3, tile_y=12, zchunk=2, stages=3), dict(kernel=3, tile_y=16)]
 TUNINGS4 = [dict(kernel=1), dict(kernel=2, tile_y=4, stages=4), dict(kernel=2, tile_y=8, zchunk=3),
-            dict(kernel=2, tile_y=16, stages=5)]
+            dict(kernel=2, tile_y=12), dict(kernel=2, tile_y=16, stages=5)]
 
 
 def run_all() -> dict:

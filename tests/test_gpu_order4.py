@@ -17,6 +17,7 @@ TUNINGS = {
     "fused8": dict(kernel=2, tile_y=8, stages=5),
     "fused4": dict(kernel=2, tile_y=4, stages=4),
     "fused16": dict(kernel=2, tile_y=16, stages=4),
+    "fused12": dict(kernel=2, tile_y=12, stages=5),
     "fused8_s8_graph": dict(kernel=2, tile_y=8, stages=8, use_graph=1),
     "auto": dict(kernel=0),
 }
@@ -69,7 +70,7 @@ def test_random_vacuum_parity(dims, steps, tuning):
         assert abs(w1 - w0) / w0 <= ENERGY_DRIFT_F32
 
 
-@pytest.mark.parametrize("tuning", ["simple", "fused8", "fused16", "auto"])
+@pytest.mark.parametrize("tuning", ["simple", "fused8", "fused12", "fused16", "auto"])
 def test_sphere_dielectric_parity(tuning):
     dims = (70, 53, 41)
     sph = ci.sphere_list(41, 6, dims, 4.0, 15.0)
@@ -81,7 +82,7 @@ def test_sphere_dielectric_parity(tuning):
     assert abs(w1 - w0) / w0 <= ENERGY_DRIFT_F32
 
 
-@pytest.mark.parametrize("tuning", ["simple", "fused8", "fused4", "fused16"])
+@pytest.mark.parametrize("tuning", ["simple", "fused8", "fused4", "fused12", "fused16"])
 def test_nonuniform_ch_table_parity(tuning):
     dims = (67, 21, 13)
     ce, ch = table_coefficients(43, dims)
@@ -116,7 +117,7 @@ def test_fused_bitwise_equals_unfused(coef, dims):
         ce, ch = table_coefficients(48, dims)
     f = ci.random_fields(49, *dims)
     a = run4(f, dims, ce, ch, steps=11, tuning=TUNINGS["simple"])[0]
-    for name in ("fused8", "fused4", "fused16"):
+    for name in ("fused8", "fused4", "fused12", "fused16"):
         b = run4(f, dims, ce, ch, steps=11, tuning=TUNINGS[name])[0]
         for c in range(6):
             assert np.array_equal(a[c], b[c]), (name, ci.COMPONENTS[c])
@@ -239,7 +240,7 @@ def test_autotune_restores_state():
     with Cavity(*dims, DT, 1.0, order=4) as cav:
         cav.set_fields(f)
         tuning, ms = cav.autotune(16)
-        assert tuning["kernel"] == 2 and tuning["tile_y"] in (4, 8, 16) and ms > 0
+        assert tuning["kernel"] == 2 and tuning["tile_y"] in (4, 8, 12, 16) and ms > 0
         assert cav.steps_done == 0
         assert all(np.array_equal(a, b) for a, b in zip(cav.get_fields(), f))
         cav.step(12)
