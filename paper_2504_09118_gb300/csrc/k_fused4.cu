@@ -25,7 +25,8 @@
 // the cavity (the images are in the weights); with three buffers one named barrier per plane
 // orders every H write before the E phase that reads it and after the E phase that read the
 // buffer's previous plane.  Every wait is bounded (globaltimer); the first to run out raises a
-// shared abort flag and the CTA ends as k_fused.cu's does.
+// shared abort flag and the CTA ends as k_fused.cu's does (fdtd_debug_inject_timeout exercises this:
+// CTA 0 withholds its first unit and its waits give up after the requested time).
 //
 // Bytes per cell and step: the 49 B (FP32) / 25 B (16-bit) of the second-order fused kernel; halo
 // rows, columns and planes are re-read from L2.
@@ -59,6 +60,7 @@ struct Fused4Params {
     int stages;
     int slot_bytes;
     const int *first;   // per-CTA tile ranges (NULL: round-robin)
+    int inject_timeout_us;   // >0: CTA 0 never issues its first unit; its waits give up after this many us
 };
 
 __host__ __device__ constexpr int al4(int v, int a) { return (v + a - 1) / a * a; }
@@ -112,6 +114,8 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
     const int t_begin = P.first ? __ldg(P.first + blockIdx.x) : (int)blockIdx.x;
     const int t_end = P.first ? __ldg(P.first + blockIdx.x + 1) : P.ntiles;
     const int t_step = P.first ? 1 : (int)gridDim.x;
+    const bool inject = P.inject_timeout_us > 0 && blockIdx.x == 0;
+    const uint64_t lim = inject ? (uint64_t)P.inject_timeout_us * 1000ull : kWaitLimitNs4;
 
     if (threadIdx.x == 0) {
         *abort_flag = 0;
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
             int u0 = 0, u1 = 0;   // planes of the tile's first and last unit
             for (int u = 0;; ++u) {
                 if (issued >= S) {
-                    const bool w = mbar_wait_abortable(&empty[s], rnd ^ 1u, kWaitLimitNs4, abort_flag, 0);
+                    const bool w = mbar_wait_abortable(&empty[s], rnd ^ 1u, lim, abort_flag, 0);
                     if (!__all_sync(0xffffffffu, w)) {
                         ok = false;
                         break;
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
                     u1 = rec->kz1 + 2;
                 }
                 const int kk = u0 + u;
-                if (lane == 0) {
+                if (lane == 0 && !(inject && issued == 0)) {
                     const int src_copy = P.parity ^ rec->parity_off;
                     const bool has_id = rec->mode == COEF_ID8;
                     unsigned char *dst = slots + s * SB;
@@ -180,8 +184,10 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
         }
         if (!ok && lane == 0) {
             atomicOr(P.status, STATUS_TIMEOUT);
-            for (int u = issued > S ? issued - S : 0; u < issued; ++u)
+            for (int u = issued > S ? issued - S : 0; u < issued; ++u) {
+                if (inject && u == 0) continue;   // never issued
                 mbar_wait_bounded(&full[u % S], (u / S) & 1, kWaitLimitNs4);
+            }
         }
         return;
     }
@@ -201,7 +207,7 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
     auto ids_of = [&](int s) { return slots + s * SB + al4(6 * FB, 128); };
     auto at = [&](const T *base, int f, int bx, int by) { return base + f * FE + by * BX + bx; };
     auto wait_next = [&]() -> const T * {
-        const bool ok = mbar_wait_abortable(&full[ws], wpar, kWaitLimitNs4, abort_flag, 0);
+        const bool ok = mbar_wait_abortable(&full[ws], wpar, lim, abort_flag, 0);
         const T *r = ok ? slot(ws) : nullptr;
         if (++ws == S) {
             ws = 0;
@@ -488,6 +494,7 @@ cudaError_t launch4_typed(const FusedLaunch &L, cudaStream_t s) {
     P.stages = L.stages;
     P.slot_bytes = slot_bytes4<T, TY>();
     P.first = L.first;
+    P.inject_timeout_us = L.inject_timeout_us;
     kern<<<L.grid, block_threads4<TY>(), smem, s>>>(P);
     return cudaGetLastError();
 }

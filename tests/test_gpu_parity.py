@@ -161,11 +161,12 @@ def test_device_pointer_roundtrip():
         assert np.array_equal(a.cpu().numpy(), b)
 
 
-def test_injected_timeout_is_reported_and_context_recovers():
+@pytest.mark.parametrize("order", [2, 4])
+def test_injected_timeout_is_reported_and_context_recovers(order):
     from paper_2504_09118_gb300 import Cavity, FdtdError, binding
     dims = (64, 32, 40)
     f = ci.random_fields(14, *dims)
-    with Cavity(*dims, DT) as cav:
+    with Cavity(*dims, DT, order=order) as cav:
         cav.set_fields(f)
         binding.fdtd_debug_inject_timeout(cav.handle, 20000)   # 20 ms
         cav.step(1)
