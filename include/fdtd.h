@@ -315,8 +315,8 @@ FDTD_API const char *fdtd_batch_last_error(const fdtd_batch *b);
 FDTD_API int fdtd_debug_inject_timeout(fdtd_ctx *ctx, int limit_us);
 
 /*
- * fdtd_energy_static - the energy W of fdtd_energy, computed from caller-owned
- * device arrays by a path that allocates no device memory.  (The paper has no
+ * fdtd_energy_static - the energy W of fdtd_energy (second-order scheme, Eq. 2), computed from
+ * caller-owned device arrays by a path that allocates no device memory.  (The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc
  * where they need the energy, e.g. inside work they capture into a CUDA graph,
  * under a fixed pre-reserved memory budget, or in a loop that cannot afford
