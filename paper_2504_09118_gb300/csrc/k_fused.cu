@@ -259,9 +259,9 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
         }
         const float4 *table = stab;
         const int dstc = (P.parity ^ rec->parity_off) ^ 1;
-        T *dst[6];
-#pragma unroll
-        for (int f = 0; f < 6; ++f) dst[f] = static_cast<T *>(rec->dst[dstc][f]);
+        // the six arrays of a copy lie in one allocation, plane * nz elements apart
+        T *const dst0 = static_cast<T *>(rec->dst[dstc][0]);
+        const long long fstride = plane * nz;
         const float ce_s0 = rec->ce[0], ce_s1 = rec->ce[1], ce_s2 = rec->ce[2];
         const float ch_s0 = rec->ch[0], ch_s1 = rec->ch[1], ch_s2 = rec->ch[2];
         const int gj = y0 + y;
@@ -345,9 +345,9 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     *reinterpret_cast<float2 *>(hn + 2 * HC + o) = hz;
                     const long long g = (long long)k * plane + (long long)gj * pitch + gi;
                     if (!prologue && gj < ny && gi < nx && store_ok(P.status, g, 2, plane * nz)) {
-                        Pair<T>::st(dst[3] + g, hx.x, hx.y);
-                        Pair<T>::st(dst[4] + g, hy.x, hy.y);
-                        Pair<T>::st(dst[5] + g, hz.x, hz.y);
+                        Pair<T>::st(dst0 + g + 3 * fstride, hx.x, hx.y);
+                        Pair<T>::st(dst0 + g + 4 * fstride, hy.x, hy.y);
+                        Pair<T>::st(dst0 + g + 5 * fstride, hz.x, hz.y);
                     }
                 }
             } else if (ok && !prologue) {
@@ -403,9 +403,9 @@ __global__ void __launch_bounds__(block_threads<TY>(), (TY <= 8 ? 2 : 1)) fused_
                     ez = fma2(cez, sub2(sub2(hy, hy_xm2), sub2(hx, hx_ym)), ez);
                     const long long g = (long long)k * plane + (long long)gj * pitch + gi;
                     if (gj < ny && gi < nx && store_ok(P.status, g, 2, plane * nz)) {
-                        Pair<T>::st(dst[0] + g, ex.x, ex.y);
-                        Pair<T>::st(dst[1] + g, ey.x, ey.y);
-                        Pair<T>::st(dst[2] + g, ez.x, ez.y);
+                        Pair<T>::st(dst0 + g, ex.x, ex.y);
+                        Pair<T>::st(dst0 + g + 1 * fstride, ey.x, ey.y);
+                        Pair<T>::st(dst0 + g + 2 * fstride, ez.x, ez.y);
                     }
                 }
                 hpx = hx;
