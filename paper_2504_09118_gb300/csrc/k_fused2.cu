@@ -259,7 +259,8 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 sb = 0;
                 pb ^= 1u;
             }
-            ok = wait_full(sa, pa) && wait_full(sb, pb);
+            // unit k (slot sa) was waited for as the next unit of the previous plane, or at the tile start
+            ok = wait_full(sb, pb);
             ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the phases below shuffle across lanes
             const T *A = reinterpret_cast<const T *>(slots + sa * SB);
             const T *B = reinterpret_cast<const T *>(slots + sb * SB);
