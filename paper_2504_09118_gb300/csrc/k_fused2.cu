@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 h1x_ = Pair<T>::ld(at(A, 3, bx, by));
                 h1y_ = Pair<T>::ld(at(A, 4, bx, by));
                 h1z_ = Pair<T>::ld(at(A, 5, bx, by));
-                if (id_mode) idpair = ida[by * G::IBX + idoff + 2 * lane] | (ida[by * G::IBX + idoff + 2 * lane + 1] << 8);
+                // idoff is even (x0 and the 16-byte id box origin are), so the lane's two ids are one aligned u16
+                if (id_mode) idpair = *reinterpret_cast<const uint16_t *>(ida + by * G::IBX + idoff + 2 * lane);
                 float4 ca, cb;
                 coef(idpair, 1, ca, cb);
                 const float2 ez_x1 = make_float2(e0z.y, ez_x2), ey_x1 = make_float2(e0y.y, ey_x2);
