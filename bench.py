@@ -61,9 +61,10 @@ WORKLOADS = {
 # temporal-blocking kernel, 60 x 16-cell tiles (FP32), 4-slot TMA ring (what fits beside 16-row
 # planes), graphs of 8 launches.
 BENCH_TUNING = dict(kernel=3, tile_y=16, stages=4, zchunk=0, ctas_per_sm=0, use_graph=1)
-# Batches of the serving loop: two-step launches, 12-row tiles (what fdtd_batch_autotune picks for the
-# batch workload; the serving mix changes every chunk, so it is fixed rather than re-tuned).
-SERVE_TUNING = dict(kernel=3, tile_y=12, stages=4)
+# Batches of the serving loop: two-step launches, 16-row tiles (what fdtd_batch_autotune picks for the
+# batch workload, and measured best on the serving stream; the mix changes every chunk, so it is fixed
+# rather than re-tuned).
+SERVE_TUNING = dict(kernel=3, tile_y=16, stages=4)
 STEPS_PER_LAUNCH = {1: 0.5, 2: 1, 3: 2}   # leapfrog steps per launch of each kernel kind (SIMPLE: H and E launches)
 DOMINANT_KERNEL = {1: "simple_h_kernel/simple_e_kernel", 2: "fused_step_kernel", 3: "fused2_step_kernel"}
 ID_BYTES = 1  # material id per cell
@@ -348,9 +349,11 @@ def run_serve(args, w):
         shape = (r.nz + 1, r.ny + 1, r.nx + 1)
         return [torch.rand(shape, generator=gen, device="cuda") * 2 - 1 for _ in range(6)]
 
+    tuning = json.loads(args.serve_tuning) if args.serve_tuning else SERVE_TUNING
+
     def make_server(retune=False):
         return Server(ci.COURANT_HALF_DT, hbm_budget_bytes=int(w["budget_gb"] * (1 << 30)), max_slots=1024, K=16,
-                      tuning=SERVE_TUNING, result="energy", fields_fn=fields_fn, retune=retune)
+                      tuning=tuning, result="energy", fields_fn=fields_fn, retune=retune)
 
     # untimed warm-up: a short stream of the same recipe (another seed) through a server of its own, so
     # that library load, pool growth, tensor maps and graph captures are not charged to the timed stream
@@ -388,7 +391,7 @@ def run_serve(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 or bf16-storage per request", "data": "synthetic",
             "config": {"workload": "serve", "requests": st.n, "rate_hz": w["rate"], "budget_gb": w["budget_gb"],
-                       "graph_steps": 16, "tuning": SERVE_TUNING, "max_slots": 1024,
+                       "graph_steps": 16, "tuning": tuning, "max_slots": 1024,
                        "warmup_requests": len(warm)},
             "serving": {"p50_s": round(st.p50_s, 4), "p99_s": round(st.p99_s, 4), "mean_s": round(st.mean_s, 4),
                         "wall_s": round(st.wall_s, 3), "max_active": st.max_active,
@@ -460,6 +463,8 @@ def main():
     ap.add_argument("--clocks-csv", default=None)
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-seq-requests", type=int, default=150)
+    ap.add_argument("--serve-tuning", default=None,
+                    help="JSON tuning of the serving batches (default: SERVE_TUNING)")
     ap.add_argument("--serve-retune", action="store_true",
                     help="serve the stream a second time with online re-tuning (fdtd_batch_retune)")
     ap.add_argument("--precision-steps", type=int, default=0)
@@ -592,6 +597,9 @@ def main():
                            "l2": f"inputs larger than L2 ({6 * esz * cells / 1e9:.1f} GB of fields read and as many written per launch)",
                            "tuning": tuning, "hbm_fraction_of_roofline": round(achieved / peak, 4)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                # per bench step (one solve of `per` leapfrog steps, device time of the step launches)
+                "solve_ms": {"best": round(min(k_ms), 3), "median": round(statistics.median(k_ms), 3),
+                             "n": len(k_ms)},
                 "gpu_launches": int(args.steps * (launches + 2))}
         print(json.dumps(line), flush=True)
     cav.close()
