@@ -120,6 +120,20 @@ FDTD_API int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, doub
  */
 FDTD_API int fdtd_set_fields(fdtd_ctx *ctx, const float *const f[6], int on_device);
 
+/* fdtd_prefetch_fields - start copying the next fields from host memory while the context computes.
+ * f[6]: host arrays, canonical layout as fdtd_set_fields (page-locked memory for the copy to overlap
+ * the context's kernels: pageable memory is copied but not overlapped).  The six arrays are copied into
+ * a device area owned by the context (6 x (nx+1)(ny+1)(nz+1) floats, allocated at the first call) on a
+ * second stream; the call returns without waiting.  They must stay valid and unchanged until the
+ * matching fdtd_set_fields_prefetched returns.  FDTD_ERR_STATE while an earlier prefetch has not been
+ * loaded.  Lets a caller overlap the host-to-device load of its next solve with the current one. */
+FDTD_API int fdtd_prefetch_fields(fdtd_ctx *ctx, const float *const f[6]);
+
+/* fdtd_set_fields_prefetched - fdtd_set_fields from the arrays of the last fdtd_prefetch_fields (waits
+ * for their copy on the GPU, not on the host, then loads them as fdtd_set_fields does from device
+ * arrays).  FDTD_ERR_STATE when no prefetch is pending or the context is a batch member. */
+FDTD_API int fdtd_set_fields_prefetched(fdtd_ctx *ctx);
+
 /*
  * fdtd_step - advance nsteps >= 0 leapfrog steps (Listing 1 order), asynchronously
  * on the context's stream.  Launch errors are returned here; device-side errors

@@ -31,7 +31,8 @@ EXPORTS = (
     "fdtd_batch_size", "fdtd_batch_sync", "fdtd_batch_destroy", "fdtd_batch_last_error",
     "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static", "fdtd_batch_set_steps",
     "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune", "fdtd_set_sources", "fdtd_set_probes",
-    "fdtd_get_probes", "fdtd_set_order", "fdtd_get_order", "fdtd_batch_retune",
+    "fdtd_get_probes", "fdtd_set_order", "fdtd_get_order", "fdtd_batch_retune", "fdtd_prefetch_fields",
+    "fdtd_set_fields_prefetched",
 )
 
 
@@ -106,6 +107,8 @@ def lib() -> ctypes.CDLL:
             L.fdtd_set_probes.argtypes = [vp, i, vp, vp, i]
             L.fdtd_get_probes.argtypes = [vp, vp, ctypes.POINTER(i)]
             L.fdtd_set_order.argtypes = [vp, i]
+            L.fdtd_prefetch_fields.argtypes = [vp, vp]
+            L.fdtd_set_fields_prefetched.argtypes = [vp]
             L.fdtd_batch_retune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d),
                                             ctypes.POINTER(i)]
             L.fdtd_get_order.argtypes = [vp]
@@ -196,6 +199,19 @@ def fdtd_set_fields(ctx, fields, on_device: int = 0, dims=None) -> None:
     ptrs, keep = _field_ptrs(fields, (nz + 1, ny + 1, nx + 1), bool(on_device), False)
     _check(ctx, lib().fdtd_set_fields(ctx, ctypes.cast(_ptr_array(ptrs), ctypes.c_void_p), int(on_device)))
     del keep
+
+
+def fdtd_prefetch_fields(ctx, fields, dims=None):
+    """Start the host-to-device copy of the next fields; returns the host arrays the copy reads, which
+    the caller must keep alive and unchanged until fdtd_set_fields_prefetched."""
+    nx, ny, nz = dims if dims is not None else _dims_of(fields)
+    ptrs, keep = _field_ptrs(fields, (nz + 1, ny + 1, nx + 1), False, False)
+    _check(ctx, lib().fdtd_prefetch_fields(ctx, ctypes.cast(_ptr_array(ptrs), ctypes.c_void_p)))
+    return keep
+
+
+def fdtd_set_fields_prefetched(ctx) -> None:
+    _check(ctx, lib().fdtd_set_fields_prefetched(ctx))
 
 
 def fdtd_get_fields(ctx, fields, on_device: int = 0, dims=None) -> None:

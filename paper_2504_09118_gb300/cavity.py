@@ -33,6 +33,15 @@ class Cavity:
     def set_fields(self, fields, on_device=False):
         B.fdtd_set_fields(self.handle, fields, int(on_device), dims=self.dims)
 
+    def prefetch_fields(self, fields):
+        """Start copying the next fields from host memory (pinned for overlap) while the cavity computes;
+        load them with set_fields_prefetched.  The arrays are kept referenced until then."""
+        self._prefetch_keep = B.fdtd_prefetch_fields(self.handle, fields, dims=self.dims)
+
+    def set_fields_prefetched(self):
+        B.fdtd_set_fields_prefetched(self.handle)
+        self._prefetch_keep = None
+
     def get_fields(self, out=None, on_device=False):
         if out is None:
             out = [np.empty(self.shape, dtype=np.float32) for _ in range(6)]

@@ -87,6 +87,11 @@ struct fdtd_ctx {
     float *d_stage2 = nullptr;   // second staging buffer: host loads copy one field while packing another
     cudaStream_t copy_stream = nullptr;   // host-to-device copies of fdtd_set_fields (lazy)
     cudaEvent_t staged[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr};
+    // fdtd_prefetch_fields: six canonical arrays copied from the host on the copy stream while the
+    // context computes; fdtd_set_fields_prefetched loads them (lazy)
+    float *d_prefetch = nullptr;
+    cudaEvent_t prefetched = nullptr, prefetch_free = nullptr;
+    bool prefetch_pending = false;
     unsigned *d_max = nullptr;
     CUtensorMap *d_maps = nullptr;          // kMapSets x kMapsPerCavity
     std::vector<CUtensorMap> host_maps[kMapSets];
@@ -939,6 +944,7 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
 void fdtd_destroy(fdtd_ctx *c) {
     if (!c) return;
     if (c->batch) fdtd_batch_remove(c->batch, c);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);   // a prefetch may still be copying
     cudaStreamSynchronize(c->stream);
     drop_graphs(c->graphs);
     cudaStream_t st = c->stream;
@@ -956,6 +962,7 @@ void fdtd_destroy(fdtd_ctx *c) {
                     (void *)c->d_probe_comp, (void *)c->d_probe_off, (void *)c->d_probe_buf, (void *)c->d_xclock})
         pool_free(p, st);
     pool_free(c->d_stage2, st);
+    pool_free(c->d_prefetch, st);
     cudaStreamSynchronize(st);
     if (c->copy_stream) {
         cudaStreamSynchronize(c->copy_stream);
@@ -965,6 +972,8 @@ void fdtd_destroy(fdtd_ctx *c) {
         if (c->staged[b]) cudaEventDestroy(c->staged[b]);
         if (c->packed[b]) cudaEventDestroy(c->packed[b]);
     }
+    if (c->prefetched) cudaEventDestroy(c->prefetched);
+    if (c->prefetch_free) cudaEventDestroy(c->prefetch_free);
     delete c;
 }
 
@@ -1200,6 +1209,43 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
     c->steps = 0;
     c->has_fields = true;
     return check_status(c, c->d_status, c->stream);
+}
+
+int fdtd_prefetch_fields(fdtd_ctx *c, const float *const f[6]) {
+    if (!c || !f) return fail(c, FDTD_ERR_ARG, "NULL argument");
+    for (int q = 0; q < 6; ++q)
+        if (!f[q]) return fail(c, FDTD_ERR_ARG, "field %d is NULL", q);
+    if (c->prefetch_pending) return fail(c, FDTD_ERR_STATE, "a prefetch is pending: load it first");
+    if (int rc = ensure_stage2(c)) return rc;   // the copy stream
+    const size_t n = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+    if (!c->d_prefetch) {
+        CK(c, dmalloc(c, (void **)&c->d_prefetch, 6 * n * sizeof(float)));
+        CK(c, cudaEventCreateWithFlags(&c->prefetched, cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->prefetch_free, cudaEventDisableTiming));
+        CK(c, cudaEventRecord(c->prefetch_free, c->stream));   // after the allocation on the context stream
+    }
+    // the previous prefetch's arrays must have been packed before they are overwritten
+    CK(c, cudaStreamWaitEvent(c->copy_stream, c->prefetch_free, 0));
+    for (int q = 0; q < 6; ++q)
+        CK(c, cudaMemcpyAsync(c->d_prefetch + q * n, f[q], n * sizeof(float), cudaMemcpyHostToDevice,
+                              c->copy_stream));
+    CK(c, cudaEventRecord(c->prefetched, c->copy_stream));
+    c->prefetch_pending = true;
+    return FDTD_OK;
+}
+
+int fdtd_set_fields_prefetched(fdtd_ctx *c) {
+    if (!c) return FDTD_ERR_ARG;
+    if (!c->prefetch_pending) return fail(c, FDTD_ERR_STATE, "no prefetch pending");
+    if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
+    CK(c, cudaStreamWaitEvent(c->stream, c->prefetched, 0));
+    const size_t n = (size_t)(c->nx + 1) * (c->ny + 1) * (c->nz + 1);
+    const float *src[6];
+    for (int q = 0; q < 6; ++q) src[q] = c->d_prefetch + q * n;
+    c->prefetch_pending = false;
+    const int rc = fdtd_set_fields(c, src, 1);
+    CK(c, cudaEventRecord(c->prefetch_free, c->stream));
+    return rc;
 }
 
 int fdtd_get_fields(fdtd_ctx *c, float *const f[6], int on_device) {

@@ -192,3 +192,34 @@ def test_error_paths_gpu():
     with pytest.raises(FdtdError) as ei:
         Cavity(8, 8, 8, 0.7)                   # violates Courant
     assert ei.value.code == binding.FDTD_ERR_UNSTABLE
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_prefetched_fields_load_like_set_fields(storage):
+    """fdtd_prefetch_fields + fdtd_set_fields_prefetched give the same state as fdtd_set_fields, also
+    when the copy runs while the context steps; misuse is reported."""
+    import torch
+    from paper_2504_09118_gb300 import Cavity, FdtdError
+    dims = (70, 41, 33)
+    f0 = ci.random_fields(15, *dims)
+    f1 = ci.random_fields(16, *dims)
+    pinned = [torch.from_numpy(a).pin_memory().numpy() for a in f1]
+    with Cavity(*dims, DT, 1.0, None, None, storage) as ref:
+        ref.set_fields(f1)
+        ref.step(9)
+        want = ref.get_fields()
+    with Cavity(*dims, DT, 1.0, None, None, storage) as cav:
+        with pytest.raises(FdtdError):
+            cav.set_fields_prefetched()              # nothing prefetched
+        cav.set_fields(f0)
+        cav.prefetch_fields(pinned)                  # copied while the current state steps
+        cav.step(40)
+        with pytest.raises(FdtdError):
+            cav.prefetch_fields(pinned)              # the first one is not loaded yet
+        cav.set_fields_prefetched()
+        assert cav.steps_done == 0
+        cav.step(9)
+        got = cav.get_fields()
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b)
+        cav.prefetch_fields(f1)                      # pageable arrays work too; destroy with one pending
