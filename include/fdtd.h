@@ -31,7 +31,8 @@
  *   on output.  Field arrays are passed as f[6] = {Ex, Ey, Ez, Hx, Hy, Hz}.
  *
  * Errors: every int-returning call returns FDTD_OK (0) or a negative status
- * and never aborts.  A failed call leaves a message in fdtd_last_error(ctx).
+ * and never aborts.  The main calls mark their extent with NVTX ranges named after them (visible to
+ * Nsight tools; no cost without one).  A failed call leaves a message in fdtd_last_error(ctx).
  * Device-side errors (a bounded wait that ran out) are latched in a device
  * status word and reported by the next call that synchronises the stream.
  *
@@ -327,6 +328,12 @@ FDTD_API const char *fdtd_batch_last_error(const fdtd_batch *b);
  * context stays usable (its fields are undefined until the next set_fields).
  * Fault injection on the host side of a wait: no GPU fault is involved. */
 FDTD_API int fdtd_debug_inject_timeout(fdtd_ctx *ctx, int limit_us);
+
+/* fdtd_debug_fail_alloc - host-side fault injection for allocation failures: after `after` further
+ * successful device allocations by the library (any context or batch), the next one fails once as if
+ * the device were out of memory (the call that made it returns FDTD_ERR_OOM and releases what it had
+ * taken); after < 0 disarms.  No GPU fault is involved.  Process-wide. */
+FDTD_API int fdtd_debug_fail_alloc(int after);
 
 /*
  * fdtd_energy_static - the energy W of fdtd_energy (second-order scheme, Eq. 2), computed from

@@ -32,7 +32,7 @@ EXPORTS = (
     "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static", "fdtd_batch_set_steps",
     "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune", "fdtd_set_sources", "fdtd_set_probes",
     "fdtd_get_probes", "fdtd_set_order", "fdtd_get_order", "fdtd_batch_retune", "fdtd_prefetch_fields",
-    "fdtd_set_fields_prefetched",
+    "fdtd_set_fields_prefetched", "fdtd_debug_fail_alloc",
 )
 
 
@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
             L.fdtd_get_probes.argtypes = [vp, vp, ctypes.POINTER(i)]
             L.fdtd_set_order.argtypes = [vp, i]
             L.fdtd_prefetch_fields.argtypes = [vp, vp]
+            L.fdtd_debug_fail_alloc.argtypes = [i]
             L.fdtd_set_fields_prefetched.argtypes = [vp]
             L.fdtd_batch_retune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d),
                                             ctypes.POINTER(i)]
@@ -208,6 +209,11 @@ def fdtd_prefetch_fields(ctx, fields, dims=None):
     ptrs, keep = _field_ptrs(fields, (nz + 1, ny + 1, nx + 1), False, False)
     _check(ctx, lib().fdtd_prefetch_fields(ctx, ctypes.cast(_ptr_array(ptrs), ctypes.c_void_p)))
     return keep
+
+
+def fdtd_debug_fail_alloc(after: int) -> None:
+    """Make the library's device allocation after `after` more successes fail once (-1 disarms)."""
+    lib().fdtd_debug_fail_alloc(int(after))
 
 
 def fdtd_set_fields_prefetched(ctx) -> None:

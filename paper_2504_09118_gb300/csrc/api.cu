@@ -3,7 +3,10 @@
 // reductions, CUDA-graph replay and batches of cavities.
 #include <cudaTypedefs.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -20,6 +23,17 @@
 
 #include "../../include/fdtd.h"
 #include "launch.h"
+
+namespace {
+// NVTX range over a library call (visible in Nsight Systems / Compute timelines; header-only NVTX3,
+// a no-op unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 using namespace fdtd;
 
@@ -204,7 +218,18 @@ cudaMemPool_t lib_pool() {
     return pool;
 }
 
+// Host-side fault injection (fdtd_debug_fail_alloc): the allocation that counts this down to zero fails.
+std::atomic<int> g_fail_alloc_in{-1};
+
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    for (int n = g_fail_alloc_in.load(); n >= 0;)
+        if (g_fail_alloc_in.compare_exchange_weak(n, n - 1)) {
+            if (n == 0) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
     cudaMemPool_t pool = lib_pool();
     if (!pool) return cudaErrorMemoryAllocation;
     return cudaMallocFromPoolAsync(p, bytes, pool, s);
@@ -1056,6 +1081,7 @@ std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<fdtd_tuning, d
 }  // namespace
 
 int fdtd_autotune(fdtd_ctx *c, int trial_steps, fdtd_tuning *out, double *ms_per_step) {
+    NvtxRange nvtx_range("fdtd_autotune");
     if (!c) return FDTD_ERR_ARG;
     if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
     if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; tune the batch");
@@ -1130,6 +1156,7 @@ int fdtd_autotune(fdtd_ctx *c, int trial_steps, fdtd_tuning *out, double *ms_per
 }
 
 int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
+    NvtxRange nvtx_range("fdtd_set_fields");
     if (!c || !f) return fail(c, FDTD_ERR_ARG, "NULL argument");
     for (int q = 0; q < 6; ++q)
         if (!f[q]) return fail(c, FDTD_ERR_ARG, "field %d is NULL", q);
@@ -1212,6 +1239,7 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
 }
 
 int fdtd_prefetch_fields(fdtd_ctx *c, const float *const f[6]) {
+    NvtxRange nvtx_range("fdtd_prefetch_fields");
     if (!c || !f) return fail(c, FDTD_ERR_ARG, "NULL argument");
     for (int q = 0; q < 6; ++q)
         if (!f[q]) return fail(c, FDTD_ERR_ARG, "field %d is NULL", q);
@@ -1235,6 +1263,7 @@ int fdtd_prefetch_fields(fdtd_ctx *c, const float *const f[6]) {
 }
 
 int fdtd_set_fields_prefetched(fdtd_ctx *c) {
+    NvtxRange nvtx_range("fdtd_set_fields_prefetched");
     if (!c) return FDTD_ERR_ARG;
     if (!c->prefetch_pending) return fail(c, FDTD_ERR_STATE, "no prefetch pending");
     if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; remove it first");
@@ -1249,6 +1278,7 @@ int fdtd_set_fields_prefetched(fdtd_ctx *c) {
 }
 
 int fdtd_get_fields(fdtd_ctx *c, float *const f[6], int on_device) {
+    NvtxRange nvtx_range("fdtd_get_fields");
     if (!c || !f) return fail(c, FDTD_ERR_ARG, "NULL argument");
     for (int q = 0; q < 6; ++q)
         if (!f[q]) return fail(c, FDTD_ERR_ARG, "field %d is NULL", q);
@@ -1267,6 +1297,7 @@ int fdtd_get_fields(fdtd_ctx *c, float *const f[6], int on_device) {
 }
 
 int fdtd_step(fdtd_ctx *c, int nsteps) {
+    NvtxRange nvtx_range("fdtd_step");
     if (!c) return FDTD_ERR_ARG;
     if (nsteps < 0) return fail(c, FDTD_ERR_ARG, "nsteps < 0");
     if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
@@ -1459,6 +1490,7 @@ static int run_reductions(fdtd_ctx *c, int what, double out[3]) {
 }
 
 int fdtd_energy(fdtd_ctx *c, double *W) {
+    NvtxRange nvtx_range("fdtd_energy");
     if (!c || !W) return fail(c, FDTD_ERR_ARG, "NULL argument");
     double o[3];
     if (int rc = run_reductions(c, 0, o)) return rc;
@@ -1467,11 +1499,17 @@ int fdtd_energy(fdtd_ctx *c, double *W) {
 }
 
 int fdtd_divergence(fdtd_ctx *c, double *de, double *dh) {
+    NvtxRange nvtx_range("fdtd_divergence");
     if (!c || !de || !dh) return fail(c, FDTD_ERR_ARG, "NULL argument");
     double o[3];
     if (int rc = run_reductions(c, 1, o)) return rc;
     *de = std::sqrt(o[1]);
     *dh = std::sqrt(o[2]);
+    return FDTD_OK;
+}
+
+int fdtd_debug_fail_alloc(int after) {
+    g_fail_alloc_in.store(after < 0 ? -1 : after);
     return FDTD_OK;
 }
 
@@ -1690,6 +1728,7 @@ static void batch_account(fdtd_batch *b, int nsteps) {
 }
 
 int fdtd_batch_step(fdtd_batch *b, int nsteps) {
+    NvtxRange nvtx_range("fdtd_batch_step");
     if (!b || nsteps < 0) return bfail(b, FDTD_ERR_ARG, "bad argument");
     if (b->members.empty() || nsteps == 0) return FDTD_OK;
     if (int rc = batch_rebuild(b)) return rc;
@@ -1748,6 +1787,7 @@ int fdtd_batch_step(fdtd_batch *b, int nsteps) {
 }
 
 int fdtd_batch_autotune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double *ms_per_step) {
+    NvtxRange nvtx_range("fdtd_batch_autotune");
     if (!b) return FDTD_ERR_ARG;
     if (b->members.empty()) return bfail(b, FDTD_ERR_STATE, "autotune: the batch has no members");
     const int n = trial_length(trial_steps);

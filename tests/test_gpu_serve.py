@@ -88,3 +88,25 @@ def test_online_retune_keeps_results():
         ref = solo(r, 2)
         for a, b in zip(r.result, ref):
             assert np.array_equal(a, b), r.id
+
+
+def test_failed_request_is_retired_and_the_stream_goes_on():
+    """Host-side fault injection: one request's context allocation fails (as out of memory); the server
+    retires it with the error and every other request still equals its solo run."""
+    from paper_2504_09118_gb300 import binding
+    from paper_2504_09118_gb300.serve import Server
+    reqs = [r for r in stream_requests(12, 4) if r.storage == 0]
+    srv = Server(DT, result="fields", K=16, tuning={"kernel": 3, "tile_y": 16})
+    try:
+        binding.fdtd_debug_fail_alloc(6)       # a few allocations in: inside one request's context
+        st = srv.run(reqs)
+    finally:
+        binding.fdtd_debug_fail_alloc(-1)
+        srv.close()
+    failed = [r for r in reqs if r.error is not None]
+    assert st.failed == len(failed) == 1 and "OOM" in failed[0].error
+    assert st.n == len(reqs) - 1
+    for r in reqs:
+        if r.error is None:
+            for a, b in zip(r.result, solo(r, 2)):
+                assert np.array_equal(a, b), r.id
