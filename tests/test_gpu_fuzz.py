@@ -1,0 +1,63 @@
+"""Seeded fuzzing of the fused kernels' tiling: random sizes (down to one cell per axis), tile heights, ring
+depths, z-chunks, graph use, step counts and coefficient modes.  With FP32 storage every fused kernel
+computes the same operations per value as the unfused kernel of its order, so each run must equal the
+unfused run bit for bit; the unfused kernels are pinned to the oracle by the parity tests."""
+import numpy as np
+import pytest
+
+import cavity_inputs as ci
+from tests.gpu_util import DT
+
+pytestmark = pytest.mark.gpu
+
+N_CASES = 40
+
+
+def _case(seed):
+    rng = np.random.default_rng(seed)
+    order = int(rng.choice([2, 4]))
+    dims = (int(rng.integers(1, 141)), int(rng.integers(1, 71)), int(rng.integers(1, 41)))
+    steps = int(rng.integers(1, 14))
+    coef = str(rng.choice(["vacuum", "spheres", "table"]))
+    if order == 2:
+        kernel = int(rng.choice([2, 3]))
+        tile_y = int(rng.choice([4, 8, 16] if kernel == 2 else [8, 12, 16]))
+        stages = int(rng.integers(3, 9))
+    else:
+        kernel = 2
+        tile_y = int(rng.choice([4, 8, 12, 16]))
+        stages = int(rng.integers(4, 9))
+    zchunk = int(rng.choice([0, 0, int(rng.integers(1, 9))]))
+    use_graph = int(rng.integers(0, 2))
+    return order, dims, steps, coef, dict(kernel=kernel, tile_y=tile_y, stages=stages, zchunk=zchunk,
+                                          use_graph=use_graph)
+
+
+def _coefs(coef, dims, seed):
+    if coef == "spheres" and min(dims) >= 4:
+        sph = ci.sphere_list(seed, 3, dims, 1.0, max(1.5, min(dims) / 3))
+        return ci.sphere_coefficients(sph, *dims, DT)
+    if coef == "table":
+        nx, ny, nz = dims
+        rng = np.random.default_rng(seed)
+        tup = DT * rng.uniform(0.5, 1.0, (4, 6))
+        idx = rng.integers(0, 4, (nz + 1, ny + 1, nx + 1))
+        return [tup[idx, c].astype(np.float32) for c in range(3)], [tup[idx, 3 + c].astype(np.float32) for c in range(3)]
+    return None, None
+
+
+@pytest.mark.parametrize("seed", range(N_CASES))
+def test_fused_tilings_equal_unfused(seed):
+    from paper_2504_09118_gb300 import Cavity
+    order, dims, steps, coef, tuning = _case(1000 + seed)
+    ce, ch = _coefs(coef, dims, 2000 + seed)
+    f = ci.random_fields(3000 + seed, *dims)
+    out = []
+    for t in (dict(kernel=1), tuning):
+        with Cavity(*dims, DT, 1.0, ce, ch, order=order) as cav:
+            cav.tune(**t)
+            cav.set_fields(f)
+            cav.step(steps)
+            out.append(cav.get_fields())
+    for a, b, name in zip(out[0], out[1], ci.COMPONENTS):
+        assert np.array_equal(a, b), (order, dims, steps, coef, tuning, name)
