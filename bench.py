@@ -70,13 +70,11 @@ DOMINANT_KERNEL = {1: "simple_h_kernel/simple_e_kernel", 2: "fused_step_kernel",
 ID_BYTES = 1  # material id per cell
 
 # DRAM traffic per fused launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the
-# SHA-256 of the kernel source it was measured on; ignored (reported null) once the source changes.
+# SHA-256 of the kernel source and the device headers it includes, as measured; ignored (reported null)
+# once any of them changes.
 MEASURED_TRAFFIC = {
     # ncu, 512^3 bench configuration, mean of three launches (profiles/fused2_step_512cube_f32_launches.md)
-    ("single512", "d331badc31c6cd62"): 7.39e9,
-    # ncu on the 256^3 case of the same kernel and launch shape (profiles/fused4_step_256cube_f32_full.md),
-    # scaled by the cell count (x 8): traffic grows in proportion to the cells
-    ("order4_512", "7720c4e0bb6569b3"): 6.38e9,
+    ("single512", "fa00a1b7df30a467"): 7.10e9,
 }
 
 
@@ -97,8 +95,11 @@ def kernel_source_hash(w=None) -> str:
         src = "k_order4.cu" if k == 1 else "k_fused4.cu"
     else:
         src = {2: "k_fused.cu", 3: "k_fused2.cu"}.get(k, "k_simple.cu")
-    p = os.path.join(ROOT, "paper_2504_09118_gb300", "csrc", src)
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    headers = ["fdtd_internal.cuh", "fused_common.cuh"] + (["order4.cuh"] if (w or {}).get("order", 2) == 4 else [])
+    h = hashlib.sha256()
+    for name in [src] + headers:
+        h.update(open(os.path.join(ROOT, "paper_2504_09118_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():

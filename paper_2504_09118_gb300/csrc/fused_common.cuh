@@ -75,12 +75,17 @@ __device__ __forceinline__ bool bar_sync_or(int id, int nthreads, bool pred) {
 // Two adjacent storage elements <-> two floats.  16-bit storage holds E scaled by s_E and
 // H scaled by s_H; the kernel computes in those scaled units (the ratio s_E/s_H is folded
 // into the coefficients of its tile records), so loads and stores are plain conversions.
+// st_cs stores with the streaming (evict-first) cache hint: a launch never re-reads what it
+// writes, so its outputs should not push the neighbouring tiles' halo rows out of L2.
 template <typename T> struct Pair;
 template <> struct Pair<float> {
     __device__ __forceinline__ static float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
     __device__ __forceinline__ static float ld1(const float *p) { return *p; }
     __device__ __forceinline__ static void st(float *p, float a, float b) {
         *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
+    __device__ __forceinline__ static void st_cs(float *p, float a, float b) {
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
     }
 };
 template <> struct Pair<__half> {
@@ -91,6 +96,9 @@ template <> struct Pair<__half> {
     __device__ __forceinline__ static void st(__half *p, float a, float b) {
         *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
     }
+    __device__ __forceinline__ static void st_cs(__half *p, float a, float b) {
+        __stcs(reinterpret_cast<__half2 *>(p), __floats2half2_rn(a, b));
+    }
 };
 template <> struct Pair<__nv_bfloat16> {
     __device__ __forceinline__ static float2 ld(const __nv_bfloat16 *p) {
@@ -99,6 +107,9 @@ template <> struct Pair<__nv_bfloat16> {
     __device__ __forceinline__ static float ld1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     __device__ __forceinline__ static void st(__nv_bfloat16 *p, float a, float b) {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+    }
+    __device__ __forceinline__ static void st_cs(__nv_bfloat16 *p, float a, float b) {
+        __stcs(reinterpret_cast<__nv_bfloat162 *>(p), __floats2bfloat162_rn(a, b));
     }
 };
 

@@ -324,12 +324,12 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 if (level1_only && out_row && out_a && k >= kz0 && k < kz1) {   // one step: (H1, E1) is the result
                     const long long g = (long long)k * plane + (long long)gj * pitch + gi;
                     if (store_ok(P.status, g, 2, plane * nz)) {
-                        Pair<T>::st(dst0 + g, e1x.x, e1x.y);
-                        Pair<T>::st(dst0 + g + 1 * fstride, e1y.x, e1y.y);
-                        Pair<T>::st(dst0 + g + 2 * fstride, e1z.x, e1z.y);
-                        Pair<T>::st(dst0 + g + 3 * fstride, h1x_.x, h1x_.y);
-                        Pair<T>::st(dst0 + g + 4 * fstride, h1y_.x, h1y_.y);
-                        Pair<T>::st(dst0 + g + 5 * fstride, h1z_.x, h1z_.y);
+                        Pair<T>::st_cs(dst0 + g, e1x.x, e1x.y);
+                        Pair<T>::st_cs(dst0 + g + 1 * fstride, e1y.x, e1y.y);
+                        Pair<T>::st_cs(dst0 + g + 2 * fstride, e1z.x, e1z.y);
+                        Pair<T>::st_cs(dst0 + g + 3 * fstride, h1x_.x, h1x_.y);
+                        Pair<T>::st_cs(dst0 + g + 4 * fstride, h1y_.x, h1y_.y);
+                        Pair<T>::st_cs(dst0 + g + 5 * fstride, h1z_.x, h1z_.y);
                     }
                 }
             }
@@ -375,12 +375,12 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 const float2 e2z = fma2(cez, sub2(sub2(h2y, make_float2(h2y_xm, h2y.x)), sub2(h2x, hx_ym)), e1pz);
                 const long long g = (long long)kk * plane + (long long)gj * pitch + gi;
                 if (out_a && store_ok(P.status, g, 2, plane * nz)) {
-                    Pair<T>::st(dst0 + g, e2x.x, e2x.y);
-                    Pair<T>::st(dst0 + g + 1 * fstride, e2y.x, e2y.y);
-                    Pair<T>::st(dst0 + g + 2 * fstride, e2z.x, e2z.y);
-                    Pair<T>::st(dst0 + g + 3 * fstride, h2x.x, h2x.y);
-                    Pair<T>::st(dst0 + g + 4 * fstride, h2y.x, h2y.y);
-                    Pair<T>::st(dst0 + g + 5 * fstride, h2z.x, h2z.y);
+                    Pair<T>::st_cs(dst0 + g, e2x.x, e2x.y);
+                    Pair<T>::st_cs(dst0 + g + 1 * fstride, e2y.x, e2y.y);
+                    Pair<T>::st_cs(dst0 + g + 2 * fstride, e2z.x, e2z.y);
+                    Pair<T>::st_cs(dst0 + g + 3 * fstride, h2x.x, h2x.y);
+                    Pair<T>::st_cs(dst0 + g + 4 * fstride, h2y.x, h2y.y);
+                    Pair<T>::st_cs(dst0 + g + 5 * fstride, h2z.x, h2z.y);
                 }
             }
             // ---------------- carry the z neighbours to the next plane

@@ -363,9 +363,9 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
                     *reinterpret_cast<float2 *>(hn + 2 * HC + o) = hz;
                     const long long g = (long long)p * plane + (long long)gj * pitch + gi;
                     if (p >= kz0 && p < kz1 && a0 && store_ok(P.status, g, 2, plane * nz)) {
-                        Pair<T>::st(dst0 + g + 3 * fstride, hx.x, hx.y);
-                        Pair<T>::st(dst0 + g + 4 * fstride, hy.x, hy.y);
-                        Pair<T>::st(dst0 + g + 5 * fstride, hz.x, hz.y);
+                        Pair<T>::st_cs(dst0 + g + 3 * fstride, hx.x, hx.y);
+                        Pair<T>::st_cs(dst0 + g + 4 * fstride, hy.x, hy.y);
+                        Pair<T>::st_cs(dst0 + g + 5 * fstride, hz.x, hz.y);
                     }
                     hx_n = hx;
                     hy_n = hy;
@@ -460,9 +460,9 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
                 const float2 ez = fma2o(cez, sub2o(dxHy, dyHx), ez_prev);
                 const long long g = (long long)e * plane + (long long)gj * pitch + gi;
                 if (gj < ny && gi < nx && store_ok(P.status, g, 2, plane * nz)) {
-                    Pair<T>::st(dst0 + g, ex.x, ex.y);
-                    Pair<T>::st(dst0 + g + 1 * fstride, ey.x, ey.y);
-                    Pair<T>::st(dst0 + g + 2 * fstride, ez.x, ez.y);
+                    Pair<T>::st_cs(dst0 + g, ex.x, ex.y);
+                    Pair<T>::st_cs(dst0 + g + 1 * fstride, ey.x, ey.y);
+                    Pair<T>::st_cs(dst0 + g + 2 * fstride, ez.x, ez.y);
                 }
             }
             // ---------------- slide the z windows
