@@ -16,7 +16,7 @@
  *   - the per-component update written as a plain triple loop (Listing 2),
  *     with fields updated in place (Sec. 3, in-place bufferisation).
  *
- * Readings where the paper is silent or garbled (each also listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - Listing 2's index range reads one past equal-sized arrays; the arrays
  *     here have the staggered Yee extents implied by Listing 3's slice shapes.
  *   - Eq. 1 prints dH/dt = +(1/mu) curl E, while Eq. 2 and Listing 2 carry
