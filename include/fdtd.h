@@ -335,6 +335,23 @@ FDTD_API int fdtd_debug_inject_timeout(fdtd_ctx *ctx, int limit_us);
  * taken); after < 0 disarms.  No GPU fault is involved.  Process-wide. */
 FDTD_API int fdtd_debug_fail_alloc(int after);
 
+/* fdtd_debug_tile_plan - host only (no GPU, no context): the work split that the fused kernels use for
+ * one cavity with one persistent CTA per SM.  The cavity is cut into `cols` columns (x-y tiles) over nz
+ * planes; a tile is a column over a z-chunk and costs (chunk length + prologue) plane-times, prologue
+ * being the planes that prime the z recurrence (1 for the one-step kernel, 3 for the two-step kernel,
+ * 4 for the fourth-order kernel).  zchunk > 0 fixes the chunk length (the last chunk takes the rest);
+ * zchunk = 0 picks, among n equal chunks (n = 1..64) and n chunks of one length followed by the rest in
+ * 1-4 pieces, the plan with the shortest makespan of greedy list scheduling over min(ctas, cols * nz)
+ * CTAs.  Tiles are listed chunk-major, columns in order within a chunk, and each goes to the CTA that
+ * becomes free first (lowest index on ties).
+ *   chunks[0 .. *nchunks)  chunk lengths in z order (capacity max_chunks, caller-owned)
+ *   *makespan              plane-times of the busiest CTA
+ *   cta_of_tile            NULL, or *nchunks * cols entries (caller-owned): the CTA of each listed tile
+ * Returns FDTD_ERR_ARG for non-positive sizes, a negative prologue or zchunk, a capacity below the
+ * plan's chunk count, or more than 2^26 tiles with cta_of_tile given. */
+FDTD_API int fdtd_debug_tile_plan(long long cols, int nz, int ctas, int prologue, int zchunk, int *chunks,
+                                  int max_chunks, int *nchunks, long long *makespan, int *cta_of_tile);
+
 /*
  * fdtd_energy_static - the energy W of fdtd_energy (second-order scheme, Eq. 2), computed from
  * caller-owned device arrays by a path that allocates no device memory.  (The paper has no

@@ -32,7 +32,7 @@ EXPORTS = (
     "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static", "fdtd_batch_set_steps",
     "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune", "fdtd_set_sources", "fdtd_set_probes",
     "fdtd_get_probes", "fdtd_set_order", "fdtd_get_order", "fdtd_batch_retune", "fdtd_prefetch_fields",
-    "fdtd_set_fields_prefetched", "fdtd_debug_fail_alloc",
+    "fdtd_set_fields_prefetched", "fdtd_debug_fail_alloc", "fdtd_debug_tile_plan",
 )
 
 
@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
             L.fdtd_set_order.argtypes = [vp, i]
             L.fdtd_prefetch_fields.argtypes = [vp, vp]
             L.fdtd_debug_fail_alloc.argtypes = [i]
+            L.fdtd_debug_tile_plan.argtypes = [ll, i, i, i, i, vp, i, ctypes.POINTER(i), ctypes.POINTER(ll), vp]
             L.fdtd_set_fields_prefetched.argtypes = [vp]
             L.fdtd_batch_retune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d),
                                             ctypes.POINTER(i)]
@@ -214,6 +215,27 @@ def fdtd_prefetch_fields(ctx, fields, dims=None):
 def fdtd_debug_fail_alloc(after: int) -> None:
     """Make the library's device allocation after `after` more successes fail once (-1 disarms)."""
     lib().fdtd_debug_fail_alloc(int(after))
+
+
+def fdtd_debug_tile_plan(cols: int, nz: int, ctas: int, prologue: int, zchunk: int = 0,
+                         assignment: bool = True) -> tuple[list[int], int, np.ndarray | None]:
+    """Host-only work split of one cavity: (chunk lengths, makespan in plane-times, CTA of each listed
+    tile or None).  Needs no GPU."""
+    cap = max(128, -(-int(nz) // int(zchunk))) if zchunk > 0 else 128   # the search tries at most 68 chunks
+    chunks = np.zeros(cap, np.int32)
+    n, ms = ctypes.c_int(0), ctypes.c_longlong(0)
+    call = lambda out: lib().fdtd_debug_tile_plan(int(cols), int(nz), int(ctas), int(prologue), int(zchunk),
+                                                  chunks.ctypes.data, cap, ctypes.byref(n), ctypes.byref(ms), out)
+    rc = call(None)
+    if rc != FDTD_OK:
+        raise FdtdError(rc, "fdtd_debug_tile_plan: invalid arguments")
+    cta = None
+    if assignment:
+        cta = np.full(n.value * int(cols), -1, np.int32)
+        rc = call(cta.ctypes.data)
+        if rc != FDTD_OK:
+            raise FdtdError(rc, "fdtd_debug_tile_plan: invalid arguments")
+    return [int(x) for x in chunks[:n.value]], int(ms.value), cta
 
 
 def fdtd_set_fields_prefetched(ctx) -> None:

@@ -1513,6 +1513,42 @@ int fdtd_debug_fail_alloc(int after) {
     return FDTD_OK;
 }
 
+int fdtd_debug_tile_plan(long long cols, int nz, int ctas, int prologue, int zchunk, int *chunks, int max_chunks,
+                         int *nchunks, long long *makespan, int *cta_of_tile) {
+    if (cols < 1 || nz < 1 || ctas < 1 || prologue < 0 || zchunk < 0 || !chunks || !nchunks || !makespan)
+        return FDTD_ERR_ARG;
+    // the same sequence as build_tiles with one CTA per SM: plan for G CTAs, list chunk-major, assign greedily
+    const int G = (int)std::min<long long>(ctas, cols * nz);
+    const std::vector<int> plan = plan_chunks(cols, nz, G, prologue, zchunk);
+    if ((int)plan.size() > max_chunks) return FDTD_ERR_ARG;
+    const long long ntiles = cols * (long long)plan.size();
+    if (cta_of_tile && ntiles > (1ll << 26)) return FDTD_ERR_ARG;
+    for (size_t q = 0; q < plan.size(); ++q) chunks[q] = plan[q];
+    *nchunks = (int)plan.size();
+    *makespan = simulate_plan(plan, cols, G, prologue);
+    if (cta_of_tile) {
+        std::vector<TileRec> listed;
+        listed.reserve((size_t)ntiles);
+        int z0 = 0;
+        for (int len : plan) {
+            for (long long col = 0; col < cols; ++col) {
+                TileRec t{};
+                t.x0 = (int)listed.size();   // the listing index, to map the regrouped records back
+                t.kz0 = z0;
+                t.kz1 = z0 + len;
+                listed.push_back(t);
+            }
+            z0 += len;
+        }
+        std::vector<int> first;
+        const int grid = (int)std::min<long long>(ntiles, G);
+        const std::vector<TileRec> v = assign_tiles(listed, grid, prologue, first);
+        for (int b = 0; b < grid; ++b)
+            for (int q = first[b]; q < first[b + 1]; ++q) cta_of_tile[v[q].x0] = b;
+    }
+    return FDTD_OK;
+}
+
 int fdtd_debug_inject_timeout(fdtd_ctx *c, int limit_us) {
     if (!c) return FDTD_ERR_ARG;
     if (limit_us < 1 || limit_us > 1000000) return fail(c, FDTD_ERR_ARG, "limit_us must be in [1, 1e6]");
