@@ -224,6 +224,7 @@ def cpu_baseline(w, budget_s: float = 12.0):
     step(g, ci.COURANT_HALF_DT, ci.COURANT_HALF_DT, s1, omp=False)
     d1 = time.perf_counter() - t0
     return {"value": round(rate, 4), "unit": "Gcell-updates/s", "cores": oracle.threads(True), "kind": "oracle",
+            "affinity_cores": len(os.sched_getaffinity(0)),
             "sample": f"{nx}x{ny}x{nzs} slab of the {w['n'][0]}x{w['n'][1]}x{w['n'][2]} workload "
                       f"(same sphere layout), FP64 OpenMP oracle (order {w.get('order', 2)}), {steps} steps "
                       f"in {dt:.1f} s",
@@ -264,7 +265,7 @@ def run_reference(args, w, wname):
             "config": {"workload": wname, "cells": [nx, ny, nz], "sample_cells": [nx, ny, nzs],
                        "leapfrog_steps_per_bench_step": per_step},
             "cpu_baseline": {"value": round(val, 4), "unit": "Gcell-updates/s", "cores": oracle.threads(True),
-                             "kind": "oracle", "sample": f"{nx}x{ny}x{nzs} slab, {per_step} FP64 steps + energy per bench step"},
+                             "affinity_cores": len(os.sched_getaffinity(0)), "kind": "oracle", "sample": f"{nx}x{ny}x{nzs} slab, {per_step} FP64 steps + energy per bench step"},
             "e2e": {"value": round(val, 4), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
