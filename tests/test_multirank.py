@@ -8,6 +8,9 @@
 3. The same for the fourth-order scheme: two ghost planes per side (E: two above, one below before the H
    update; H: two below, one above before the E update), wall images along x, y and at the global z walls;
    gathered, equal to the one-slab restatement bit for bit and to the oracle's step4 to rounding.
+4. Temporal blocking across ranks (T = 2): two ghost planes of all six fields per side, exchanged once per
+   two steps, both steps then taken locally; gathered, equal to the single-domain restatement bit for bit,
+   and dropping one exchange shows.
 """
 import os
 import socket
@@ -333,3 +336,81 @@ def test_zslab_fourth_order_matches_single_domain_and_oracle(tmp_path, dims, ste
         m = ci.extent_mask(name, nx, ny, nz)
         assert np.array_equal(got[c][m], whole[c][m]), name
         assert np.max(np.abs(got[c][m] - orc[c][m])) <= 1e-13, name
+
+
+# ------------------------------------------------------------------ 4. z-slabs with temporal blocking (T = 2)
+# The two-step kernel's counterpart across ranks: each rank keeps two ghost planes of all six fields on each
+# side, exchanges them once per two steps, and then takes both steps locally, recomputing the ghost planes
+# it needs (their outermost values go stale, which the owned planes never read: two steps reach two planes).
+def _local_step(loc, ce, ch, g0, nz):
+    """One step on local planes 0 .. P-1 (global g0 + p), each value updated wherever the local arrays
+    hold its inputs; E on the global z walls and cell-centred components at the node plane nz are never
+    written.  Per value the arithmetic of the whole-array restatement of Eq. 2."""
+    Ex, Ey, Ez, Hx, Hy, Hz = loc
+    cex, cey, cez = ce
+    chx, chy, chz = ch
+    P = Ex.shape[0]
+    ny, nx = Ex.shape[1] - 1, Ex.shape[2] - 1
+    cell = [p for p in range(P) if g0 + p < nz]                          # Hx, Hy, Ez planes that exist
+    hc = np.array([p for p in cell if p + 1 < P], int)                  # Hx, Hy: need E at p + 1
+    Hx[hc, :ny, :] -= chx[hc, :ny, :] * ((Ez[hc, 1:, :] - Ez[hc, :ny, :]) - (Ey[hc + 1, :ny, :] - Ey[hc, :ny, :]))
+    Hy[hc, :, :nx] -= chy[hc, :, :nx] * ((Ex[hc + 1, :, :nx] - Ex[hc, :, :nx]) - (Ez[hc, :, 1:] - Ez[hc, :, :nx]))
+    Hz[:, :ny, :nx] -= chz[:, :ny, :nx] * ((Ey[:, :ny, 1:] - Ey[:, :ny, :nx]) - (Ex[:, 1:, :nx] - Ex[:, :ny, :nx]))
+    en = np.array([p for p in range(1, P) if 0 < g0 + p < nz], int)     # Ex, Ey: need H at p - 1; not walls
+    Ex[en, 1:ny, :nx] += cex[en, 1:ny, :nx] * ((Hz[en, 1:ny, :nx] - Hz[en, :ny - 1, :nx]) - (Hy[en, 1:ny, :nx] - Hy[en - 1, 1:ny, :nx]))
+    Ey[en, :ny, 1:nx] += cey[en, :ny, 1:nx] * ((Hx[en, :ny, 1:nx] - Hx[en - 1, :ny, 1:nx]) - (Hz[en, :ny, 1:nx] - Hz[en, :ny, :nx - 1]))
+    ez = np.array(cell, int)
+    Ez[ez, 1:ny, 1:nx] += cez[ez, 1:ny, 1:nx] * ((Hy[ez, 1:ny, 1:nx] - Hy[ez, 1:ny, :nx - 1]) - (Hx[ez, 1:ny, 1:nx] - Hx[ez, :ny - 1, 1:nx]))
+
+
+def _slabs_t2(rank, dims, pairs, seed, out_dir, skip_pair):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    sh = (nz + 1, ny + 1, nx + 1)
+    ce = [rng.uniform(0.2, 0.28, sh) for _ in range(3)]
+    ch = [rng.uniform(0.2, 0.28, sh) for _ in range(3)]
+    f = [np.asarray(a, np.float64) for a in ci.random_fields(seed, nx, ny, nz)]
+    k0, k1 = _owned(nz, rank)
+    own_hi = k1 + (1 if rank == WORLD - 1 else 0)      # owned planes [k0, own_hi)
+    lo, hi = max(k0 - 2, 0), min(own_hi + 1, nz)        # local planes lo .. hi
+    loc = [a[lo:hi + 1].copy() for a in f]
+    lce = [a[lo:hi + 1] for a in ce]
+    lch = [a[lo:hi + 1] for a in ch]
+    exchanges = 0
+    for pair in range(pairs):
+        if pair != skip_pair:
+            # two owned planes go to each neighbour: the first two down, the last two up
+            up = np.stack([a[k1 - 2 - lo:k1 - lo] for a in loc])
+            down = np.stack([a[k0 - lo:k0 + 2 - lo] for a in loc])
+            below, above = _swap(rank, WORLD, up, down)
+            if below is not None:
+                for a, b in zip(loc, below):
+                    a[k0 - 2 - lo:k0 - lo] = b
+            if above is not None:
+                for a, b in zip(loc, above):
+                    a[k1 - lo:hi + 1 - lo] = b[:hi + 1 - k1]
+            exchanges += 1
+        _local_step(loc, lce, lch, lo, nz)
+        _local_step(loc, lce, lch, lo, nz)
+    np.save(os.path.join(out_dir, f"t2slab{rank}.npy"), np.stack([a[k0 - lo:own_hi - lo] for a in loc]))
+    assert exchanges == pairs - (1 if 0 <= skip_pair < pairs else 0)
+
+
+@pytest.mark.parametrize("dims,pairs", [((9, 7, 10), 3), ((6, 11, 9), 5)])
+def test_zslab_two_step_halo_matches_single_domain(tmp_path, dims, pairs):
+    from tests.test_oracle_pins import numpy_step
+    nx, ny, nz = dims
+    seed = 8
+    rng = np.random.default_rng(seed)
+    sh = (nz + 1, ny + 1, nx + 1)
+    ce = [rng.uniform(0.2, 0.28, sh) for _ in range(3)]
+    ch = [rng.uniform(0.2, 0.28, sh) for _ in range(3)]
+    ref = [np.asarray(a, np.float64) for a in ci.random_fields(seed, nx, ny, nz)]
+    for _ in range(2 * pairs):
+        numpy_step(ref, ce, ch)
+    for skip in (-1, 1):      # -1: every exchange; 1: the second pair's exchange dropped, which must show
+        _run(_slabs_t2, dims, pairs, seed, str(tmp_path), skip)
+        got = np.concatenate([np.load(tmp_path / f"t2slab{r}.npy") for r in range(WORLD)], axis=1)
+        same = all(np.array_equal(got[c][ci.extent_mask(n, nx, ny, nz)], ref[c][ci.extent_mask(n, nx, ny, nz)])
+                   for c, n in enumerate(ci.COMPONENTS))
+        assert same == (skip < 0)
