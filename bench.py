@@ -68,12 +68,13 @@ SERVE_TUNING = dict(kernel=3, tile_y=16, stages=4)
 STEPS_PER_LAUNCH = {1: 0.5, 2: 1, 3: 2}   # leapfrog steps per launch of each kernel kind (SIMPLE: H and E launches)
 DOMINANT_KERNEL = {1: "simple_h_kernel/simple_e_kernel", 2: "fused_step_kernel", 3: "fused2_step_kernel"}
 ID_BYTES = 1  # material id per cell
+NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e nominal bandwidth (context beside the measured copy peak)
 
 # DRAM traffic per fused launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the
 # SHA-256 of the kernel source and the device headers it includes, as measured; ignored (reported null)
 # once any of them changes.
 MEASURED_TRAFFIC = {
-    # ncu, 512^3 bench configuration, mean of three launches (profiles/fused2_step_512cube_f32_launches.md)
+    # ncu, 512^3 bench configuration, mean of three launches of the two-step kernel
     ("single512", "fa00a1b7df30a467"): 7.10e9,
 }
 
@@ -271,7 +272,8 @@ def run_reference(args, w, wname):
 
 
 def run_batch(args, w):
-    """Batched persistent launches vs plain one-launch-per-step stepping of each cavity alone."""
+    """Batched persistent launches vs plain one-launch-per-step stepping of each cavity alone.
+    Returns the leg's results (its own timed region and clock summary)."""
     import torch
     from paper_2504_09118_gb300 import Cavity, binding
     torch.cuda.set_device(0)
@@ -325,21 +327,24 @@ def run_batch(args, w):
     plain = cells * plain_steps / (p0.elapsed_time(p1) / 1e3) / 1e9
     for m in members:
         m.close()
-    line = {"metric": "Gcell-updates/s", "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": 1,
+    return {"metric": "Gcell-updates/s", "value": round(value, 3), "unit": "Gcell-updates/s",
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch256", "cavities": len(members), "cells": cells,
+                       "sides": f"iid U{{{w['lo']}..{w['hi']}}} per axis, vacuum or spheres (p = 1/2), seed {w['seed']}",
                        "leapfrog_steps_per_bench_step": per, "graph_steps": 16,
                        "autotuned": tuning, "autotune_s": round(t_tune, 3)},
-            "plain_one_launch_per_step": round(plain, 3), "batched_vs_plain": round(value / plain, 3),
+            "plain_one_launch_per_step": round(plain, 3), "plain_steps": plain_steps,
+            "batched_vs_plain": round(value / plain, 3),
             "clocks": clk.summary(),
             # each launch (one step, or two with the two-step kernel) is followed by the clock kernel
             "gpu_launches": 2 * args.steps * per // (2 if tuning["kernel"] == 3 else 1)}
-    print(json.dumps(line), flush=True)
 
 
 def run_serve(args, w):
-    """Continuous-batching server on a Poisson stream vs the same stream served one request at a time."""
+    """Continuous-batching server on a Poisson stream vs plain one-request-at-a-time stepping (the
+    sequential baseline runs closed-loop over a stated prefix of the same stream).  Returns the leg's
+    results."""
     import torch
     from paper_2504_09118_gb300.serve import Request, Server, serve_sequential
     torch.cuda.set_device(0)
@@ -387,51 +392,55 @@ def run_serve(args, w):
     nseq = min(len(stream), args.serve_seq_requests)
     seq_reqs = [Request(q["id"], q["arrival_s"], q["nx"], q["ny"], q["nz"], q["steps"], q["bf16"])
                 for q in stream[:nseq]]
-    sq = serve_sequential(seq_reqs, ci.COURANT_HALF_DT, result="energy", fields_fn=fields_fn)
-    line = {"metric": "Gcell-updates/s", "value": round(st.gcells, 3), "unit": "Gcell-updates/s", "n_gpus": 1,
-            "steps": st.n, "warmup": len(warm), "ms_per_step": round(1e3 * st.wall_s / st.n, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    with ClockSampler(0, None) as clk_seq:
+        sq = serve_sequential(seq_reqs, ci.COURANT_HALF_DT, result="energy", fields_fn=fields_fn)
+    offered = st.cell_updates / max(r["arrival_s"] for r in stream) / 1e9
+    return {"metric": "Gcell-updates/s", "value": round(st.gcells, 3), "unit": "Gcell-updates/s",
+            "requests": st.n, "failed": st.failed, "ms_per_request": round(1e3 * st.wall_s / max(st.n, 1), 3),
             "dtype": "f32 or bf16-storage per request", "data": "synthetic",
-            "config": {"workload": "serve", "requests": st.n, "rate_hz": w["rate"], "budget_gb": w["budget_gb"],
-                       "graph_steps": 16, "tuning": tuning, "max_slots": 1024,
-                       "warmup_requests": len(warm)},
+            "config": {"workload": "serve", "requests": len(stream), "rate_hz": w["rate"],
+                       "sides": "log-uniform 16-256 per axis", "steps": "U{100..2000}", "bf16": "Bernoulli(1/2)",
+                       "budget_gb": w["budget_gb"], "graph_steps": 16, "tuning": tuning, "max_slots": 1024,
+                       "warmup_requests": len(warm), "seed": w["seed"]},
             "serving": {"p50_s": round(st.p50_s, 4), "p99_s": round(st.p99_s, 4), "mean_s": round(st.mean_s, 4),
                         "wall_s": round(st.wall_s, 3), "max_active": st.max_active,
-                        "offered_gcells": round(st.cell_updates / max(r["arrival_s"] for r in stream) / 1e9, 2)},
+                        "offered_gcells": round(offered, 2)},
             "sequential": {"requests": sq.n, "gcells": round(sq.gcells, 3), "p50_s": round(sq.p50_s, 4),
-                           "p99_s": round(sq.p99_s, 4), "closed_loop": True},
+                           "p99_s": round(sq.p99_s, 4), "wall_s": round(sq.wall_s, 3), "closed_loop": True,
+                           "sample": f"the first {sq.n} requests of the same stream, one at a time, one plain "
+                                     f"launch per step, each started as soon as the previous one finished",
+                           "clocks": clk_seq.summary()},
             "served_vs_sequential": round(st.gcells / sq.gcells, 3), "online_retune": online,
             "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
 
 
 def run_precision(args, w):
-    """Storage precision study: rel-L2 per field and energy drift of FP32/FP16/BF16 GPU runs against
-    the FP64 oracle (OpenMP build on the host cores) and the FP32 GPU run, same seeded input."""
+    """Storage precision (FP32 arithmetic): the same seeded 384^3 sphere cavity stepped 1000 times with
+    FP32, FP16 and BF16 storage; per-field rel-L2 of the 16-bit runs against the FP32 run and every run's
+    energy drift (the library's FP64 energy).  The FP32 run itself is held to the FP64 oracle by the
+    full-size parity tests.  Returns the leg's results."""
     import torch
-    import oracle
     from paper_2504_09118_gb300 import Cavity
     torch.cuda.set_device(0)
     nx, ny, nz = w["n"]
     steps = args.precision_steps or w["steps"]
     ce, ch = sphere_coefs(w)
     f = ci.random_fields(w["field_seed"], nx, ny, nz)
-    runs = {}
-    for st, name in ((0, "f32"), (1, "f16"), (2, "bf16")):
-        with Cavity(nx, ny, nz, ci.COURANT_HALF_DT, 1.0, ce, ch, st) as cav:
-            cav.tune(**BENCH_TUNING)
-            cav.set_fields(f)
-            w0 = cav.energy()
-            cav.step(steps)
-            w1 = cav.energy()
-            runs[name] = (cav.get_fields(), w0, w1)
-    t0 = time.perf_counter()
-    ref = oracle.as_f64(f)
-    ce64 = [c.astype(np.float64) for c in ce]
-    W0 = oracle.energy(ref, ce64, ch, ci.COURANT_HALF_DT)
-    oracle.step(ref, ce64, ch, steps, omp=True)
-    W1 = oracle.energy(ref, ce64, ch, ci.COURANT_HALF_DT)
-    t_or = time.perf_counter() - t0
+    runs, times = {}, {}
+    stream = torch.cuda.Stream()
+    with ClockSampler(0, None) as clk:
+        for st, name in ((0, "f32"), (1, "f16"), (2, "bf16")):
+            with Cavity(nx, ny, nz, ci.COURANT_HALF_DT, 1.0, ce, ch, st, stream) as cav:
+                cav.tune(**BENCH_TUNING)
+                cav.set_fields(f)
+                w0 = cav.energy()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                cav.step(steps)
+                e1.record(stream)
+                w1 = cav.energy()
+                times[name] = e0.elapsed_time(e1) / steps
+                runs[name] = (cav.get_fields(), w0, w1)
 
     def rel(a, b):
         out = {}
@@ -443,14 +452,16 @@ def run_precision(args, w):
 
     res = {}
     for name, (g, w0, w1) in runs.items():
-        res[name] = {"rel_l2_vs_oracle": rel(g, ref), "energy_drift": (w1 - w0) / w0,
-                     "energy_vs_oracle_final": (w1 - W1) / W1}
+        res[name] = {"energy_drift": (w1 - w0) / w0, "ms_per_step": round(times[name], 4),
+                     "gcells": round(nx * ny * nz / times[name] / 1e6, 2)}
         if name != "f32":
             res[name]["rel_l2_vs_f32_gpu"] = rel(g, runs["f32"][0])
-    line = {"metric": "rel-L2 and energy drift", "workload": "precision", "cells": [nx, ny, nz], "steps": steps,
-            "oracle": {"energy_drift": (W1 - W0) / W0, "seconds": round(t_or, 1), "threads": oracle.threads(True)},
-            "storage": res}
-    print(json.dumps(line), flush=True)
+    return {"metric": "rel-L2 vs the FP32 run, energy drift", "cells": [nx, ny, nz], "steps": steps,
+            "config": {"workload": "precision384", "spheres": w["spheres"], "seeds": [w["sphere_seed"], w["field_seed"]],
+                       "tuning": BENCH_TUNING, "scale": "one power-of-two scale per field (E, H), round to nearest even"},
+            "storage": res, "clocks": clk.summary(),
+            "oracle_parity": "tests/test_gpu_fullsize.py::test_384_precision_1000_steps_vs_oracle (FP64 oracle, "
+                             "per field)"}
 
 
 def main():
@@ -463,23 +474,26 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clocks-csv", default=None)
-    ap.add_argument("--serve-requests", type=int, default=1500)
-    ap.add_argument("--serve-seq-requests", type=int, default=150)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-seq-requests", type=int, default=1000,
+                    help="closed-loop prefix of the stream served by the sequential baseline")
     ap.add_argument("--serve-tuning", default=None,
                     help="JSON tuning of the serving batches (default: SERVE_TUNING)")
     ap.add_argument("--serve-retune", action="store_true",
                     help="serve the stream a second time with online re-tuning (fdtd_batch_retune)")
     ap.add_argument("--precision-steps", type=int, default=0)
+    ap.add_argument("--legs", default="batched,served,precision",
+                    help="comma-separated legs nested in the single-cavity line at N = 1 (batched: 256 uneven "
+                         "cavities; served: the 10k-request Poisson stream; precision: 384^3 FP16/BF16); '' for none")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.impl == "ours" and w.get("kind") == "batch":
-        run_batch(args, w)
-        return
-    if args.impl == "ours" and w.get("kind") == "serve":
-        run_serve(args, w)
-        return
-    if args.impl == "ours" and w.get("kind") == "precision":
-        run_precision(args, w)
+    standalone = {"batch": ("batched", run_batch), "serve": ("served", run_serve),
+                  "precision": ("precision", run_precision)}
+    if args.impl == "ours" and w.get("kind") in standalone:
+        name, fn = standalone[w["kind"]]
+        leg = fn(args, w)
+        leg.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "leg": name})
+        print(json.dumps(leg), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, w, args.workload)
@@ -553,6 +567,7 @@ def main():
     tr = MEASURED_TRAFFIC.get((args.workload, kernel_source_hash(w)))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr,
+                "frac_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "peak_nominal": NOMINAL_HBM_GBS,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": alg_bytes, "mean_launch_us": round(launch_s * 1e6, 2),
                 "kernel": dominant_kernel(w), "steps_per_launch": spl,
@@ -594,6 +609,18 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
+    cav.close()
+    # the other workloads of the method, each with its own timed region and clock record (one GPU only:
+    # under torchrun every rank would hold its GPU while rank 0 alone ran them)
+    legs = {}
+    if ws == 1 and args.workload == "single512":
+        wanted = [x.strip() for x in args.legs.split(",") if x.strip()]
+        for name, wname, fn in (("batched", "batch256", run_batch), ("precision", "precision", run_precision),
+                                ("served", "serve", run_serve)):
+            if name in wanted:
+                t0 = time.perf_counter()
+                legs[name] = fn(args, WORKLOADS[wname])
+                legs[name]["leg_wall_s"] = round(time.perf_counter() - t0, 1)
     if rank == 0:
         line = {"metric": "Gcell-updates/s", "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
@@ -610,8 +637,8 @@ def main():
                 "solve_ms": {"best": round(min(k_ms), 3), "median": round(statistics.median(k_ms), 3),
                              "n": len(k_ms)},
                 "gpu_launches": int(args.steps * (launches + 2))}
+        line.update(legs)
         print(json.dumps(line), flush=True)
-    cav.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

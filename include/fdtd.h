@@ -93,6 +93,9 @@ typedef struct fdtd_tuning {
 
 /*
  * fdtd_create - allocate a cavity of nx*ny*nz cells on the current device.
+ * Defines the grid and coefficients of Sec. 2, Eq. 2: ce = dt/(eps dx) multiplies curl H in the E
+ * update, ch = dt/(mu dx) multiplies curl E in the H update; the box walls are PEC as in the
+ * benchmark cavity of Sec. 4.
  *   dt, dx      time step and cell size (> 0).
  *   ce[3]       host canonical arrays of dt/(eps*dx) at the Ex, Ey, Ez
  *               positions, or NULL for vacuum (dt/dx everywhere).
@@ -112,6 +115,9 @@ FDTD_API int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, doub
 
 /*
  * fdtd_set_fields - load the state (H^{n-1/2}, E^n) and reset the step counter.
+ * The six staggered components of Sec. 2, Eq. 2 at their Yee positions; H is taken half a step
+ * behind E because a step of Sec. 2.1, Listing 1 updates H first (Eq. 2 labels the same state
+ * (E^{n+1/2}, H^{n+1}); the two labellings differ only by a half-step shift of the clock).
  *   f[6]       canonical FP32 arrays; host pointers when on_device == 0, CUDA
  *              device pointers when on_device == 1.  Read during the call only, on the
  *              context's stream: device data written on another stream must be complete
@@ -136,14 +142,18 @@ FDTD_API int fdtd_prefetch_fields(fdtd_ctx *ctx, const float *const f[6]);
 FDTD_API int fdtd_set_fields_prefetched(fdtd_ctx *ctx);
 
 /*
- * fdtd_step - advance nsteps >= 0 leapfrog steps (Listing 1 order), asynchronously
- * on the context's stream.  Launch errors are returned here; device-side errors
+ * fdtd_step - advance nsteps >= 0 leapfrog steps, asynchronously on the context's stream.
+ * One step is Sec. 2.1, Listing 1: the H update of Sec. 2, Eq. 2 (H -= ch curl E, with the minus
+ * sign of Faraday's law), the H boundary handling (nothing to do on a PEC box: normal H on a face
+ * sees zero curl), the E update of Eq. 2 (E += ce curl H), the E boundary handling (tangential E
+ * on the faces stays 0).  Results equal those of that sequence up to FP32 rounding order.  Launch errors are returned here; device-side errors
  * at the next synchronising call.
  */
 FDTD_API int fdtd_step(fdtd_ctx *ctx, int nsteps);
 
 /*
- * fdtd_get_fields - write the current state into f[6] (canonical FP32; host or
+ * fdtd_get_fields - the state (H^{n-1/2}, E^n) of Sec. 2, Eq. 2 after the steps taken,
+ * written into f[6] (canonical FP32; host or
  * device pointers as on_device says; device buffers are written on the context's
  * stream, so other streams must be done with them).  Entries outside each extent are 0.
  * Synchronises the stream; returns a latched device error if one occurred.
@@ -155,6 +165,9 @@ FDTD_API int fdtd_get_fields(fdtd_ctx *ctx, float *const f[6], int on_device);
  *   W^n = 1/2 sum eps |E^n|^2 + 1/2 sum mu H^{n-1/2} . H^{n+1/2},
  *   eps = dt/(ce dx), mu = dt/(ch dx), cell volume 1, with H^{n+1/2} formed on the
  *   fly.  It is the invariant of the Eq. 2 leapfrog on a lossless PEC cavity.
+ * The paper defines no energy: this is the quadratic form the leapfrog conserves exactly (the
+ * plain 1/2 sum eps E^2 + mu H^2 with both at one time level is not conserved), chosen as the
+ * check of a lossless run.  Every term is formed and summed in FP64 from the stored values.
  * Synchronises the stream.
  */
 FDTD_API int fdtd_energy(fdtd_ctx *ctx, double *W);
@@ -163,7 +176,9 @@ FDTD_API int fdtd_energy(fdtd_ctx *ctx, double *W);
  * fdtd_divergence - L2 norms (FP64) of the discrete divergences:
  *   divE at interior nodes: sum_c E_c/ce_c (node) - E_c/ce_c (node - e_c);
  *   divH at every cell:     sum_c H_c/ch_c (cell + e_c) - H_c/ch_c (cell).
- * Both are invariant under exact Yee stepping.  Synchronises the stream.
+ * Both are invariant under exact Yee stepping (the discrete divergence of a discrete curl is
+ * zero).  The paper defines neither; they are the second invariant checked on a lossless run.
+ * Every term is formed and summed in FP64 from the stored values.  Synchronises the stream.
  */
 FDTD_API int fdtd_divergence(fdtd_ctx *ctx, double *divE_l2, double *divH_l2);
 
@@ -353,7 +368,7 @@ FDTD_API int fdtd_debug_tile_plan(long long cols, int nz, int ctas, int prologue
                                   int max_chunks, int *nchunks, long long *makespan, int *cta_of_tile);
 
 /*
- * fdtd_energy_static - the energy W of fdtd_energy (second-order scheme, Eq. 2), computed from
+ * fdtd_energy_static - the same energy W as fdtd_energy (second-order scheme), computed from
  * caller-owned device arrays by a path that allocates no device memory.  (The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc
  * where they need the energy, e.g. inside work they capture into a CUDA graph,
@@ -371,8 +386,10 @@ FDTD_API int fdtd_debug_tile_plan(long long cols, int nz, int ctas, int prologue
  * plane), shared by every call: calls whose kernels overlap on the GPU race and
  * must be serialised by the caller.  The first call on a device looks up that
  * array's address (cudaGetSymbolAddress) and should come before any stream
- * capture.  Returns FDTD_ERR_ARG (message via fdtd_last_error(NULL)) for NULL
- * pointers, non-positive sizes or nz > 8191.
+ * capture; the address is looked up again when the device's current CUDA
+ * context is no longer the one it was found in (after a cudaDeviceReset).
+ * Returns FDTD_ERR_ARG (message via fdtd_last_error(NULL)) for NULL pointers,
+ * non-positive sizes, nz > 8191 or a z-plane of more than 2^31 points.
  */
 FDTD_API int fdtd_energy_static(int nx, int ny, int nz, double dt, double dx, const float *const f[6],
                                 const float *const ce[3], const float *const ch[3], double *W,

@@ -1,0 +1,214 @@
+// Internal definitions shared by the host-side translation units of libfdtd (the C ABI of
+// include/fdtd.h): the context and batch objects, the stream-ordered device pool, the launch
+// planner and the helpers the entry points share.  Not part of the ABI.
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include <nvtx3/nvToolsExt.h>
+
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <queue>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fdtd.h"
+#include "launch.h"
+
+namespace fdtd {
+
+namespace {
+// NVTX range over a library call (visible in Nsight Systems / Compute timelines; header-only NVTX3,
+// a no-op unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
+
+struct GraphKey {
+    int steps, parity, kind = 0;
+    bool operator<(const GraphKey &o) const {
+        if (kind != o.kind) return kind < o.kind;
+        return steps != o.steps ? steps < o.steps : parity < o.parity;
+    }
+};
+
+
+}  // namespace fdtd
+
+// The C ABI's opaque handles are global-namespace types; their members use the library's types.
+using namespace fdtd;
+
+struct fdtd_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    double dt = 0, dx = 0;
+    int storage = 0;
+    cudaStream_t stream = nullptr;
+    int pitch = 0;
+    size_t arr_elems = 0;
+    void *fields[2][6] = {};
+    float *face[3] = {}, *face_ch[3] = {};
+    int coef_mode = COEF_SCALAR;
+    float ce_s[3] = {}, ch_s[3] = {};
+    uint8_t *id = nullptr;
+    float *table = nullptr, *inv_table = nullptr;
+    float *table_fused = nullptr;     // table with the storage-scale ratios folded in (fused kernel)
+    std::vector<float> host_table;    // 8 floats per entry: ce xyz, pad, ch xyz, pad
+    int ntab = 0;
+    float *coef_full[6] = {};
+    float scale[6] = {1, 1, 1, 1, 1, 1};
+    int cur = 0;
+    long long steps = 0;
+    bool has_fields = false;
+    int *d_status = nullptr;
+    double *d_partial = nullptr, *d_out = nullptr;
+    float *d_stage = nullptr;    // canonical staging buffer for host transfers (lazy)
+    float *d_stage2 = nullptr;   // second staging buffer: host loads copy one field while packing another
+    cudaStream_t copy_stream = nullptr;   // host-to-device copies of fdtd_set_fields (lazy)
+    cudaEvent_t staged[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr};
+    // fdtd_prefetch_fields: six canonical arrays copied from the host on the copy stream while the
+    // context computes; fdtd_set_fields_prefetched loads them (lazy)
+    float *d_prefetch = nullptr;
+    cudaEvent_t prefetched = nullptr, prefetch_free = nullptr;
+    bool prefetch_pending = false;
+    unsigned *d_max = nullptr;
+    CUtensorMap *d_maps = nullptr;          // kMapSets x kMapsPerCavity
+    std::vector<CUtensorMap> host_maps[kMapSets];
+    int maps_by[kMapSets] = {0, 0, 0};      // box height each map set was encoded for (0: not yet)
+    CavityDesc *d_desc = nullptr;
+    struct TileList {
+        TileRec *d = nullptr;   // records, followed by the per-CTA range offsets
+        int *first = nullptr;   // inside the same allocation as d
+        int n = 0, grid = 0, key = 0;
+    } tl[3];                                // [0] one-step, [1] two-step, [2] fourth-order kernel
+    int order = 2;                          // spatial order of the differences (2: Eq. 2, 4: the (2,4) scheme)
+    double courant = 0.0;                   // max over cells of 3 ce ch (stable for order 2 when <= 1)
+    int ch_uniform = 1;
+    fdtd_tuning tuning{};
+    std::map<fdtd::GraphKey, cudaGraphExec_t> graphs;
+    int inject_us = 0;
+    // point currents and probes (fdtd_set_sources / fdtd_set_probes): run after every step
+    int nsrc = 0, wave_len = 0, nprobe = 0, probe_cap = 0;
+    long long probe_start = 0;         // step index of a probe buffer's first sample
+    int *d_src_comp = nullptr, *d_probe_comp = nullptr;
+    long long *d_src_off = nullptr, *d_probe_off = nullptr;
+    float *d_wave = nullptr, *d_probe_buf = nullptr;
+    long long *d_xclock = nullptr;     // device: steps taken since fdtd_set_fields (advanced by the extras launch)
+    long long bytes = 0;
+    fdtd_batch *batch = nullptr;
+    std::string err;
+};
+
+struct fdtd_batch {
+    struct Member {
+        fdtd_ctx *c;
+        int cur0;               // member's current copy when it joined
+        long long join;         // batch step clock at which it joined
+        long long join_launch;  // batch launch count at which it joined
+        long long stop;         // step clock at which it has taken all its steps (LLONG_MAX: no limit)
+        long long steps0;       // its step count when it joined
+        long long nlaunch;      // launches it took part in since joining (each flips its copy)
+    };
+    int storage = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<Member> members;
+    long long step = 0;              // step clock: steps enqueued so far (a two-step launch advances it by 2)
+    long long launches = 0;          // launches enqueued so far; the next launch has parity launches & 1
+    long long *d_step = nullptr;     // device copy of the step clock (advanced by a kernel after each launch)
+    fdtd_tuning tuning{};
+    TileRec *d_tiles = nullptr;
+    int tiles_cap = 0, ntiles = 0, grid = 0;
+    bool dirty = true;
+    int *d_status = nullptr;
+    cudaEvent_t done_ev = nullptr;   // recorded at member removal; the member's stream waits on it
+    // Completion marks: after each fdtd_batch_step call, an event and the clock it brings the batch
+    // to.  A removed member's stream waits only for the first mark at or past the clock at which the
+    // member took its last step (later launches skip it), not for everything enqueued since.
+    std::deque<std::pair<long long, cudaEvent_t>> marks;
+    std::vector<cudaEvent_t> free_marks;
+    std::map<fdtd::GraphKey, cudaGraphExec_t> graphs;
+    std::vector<cudaGraphExec_t> retired_graphs;   // destroyed at the next synchronisation point
+    std::string err;
+};
+
+namespace fdtd {
+
+// ---- errors (ctx.cu): the message goes to the context, or to fdtd_last_error(NULL) when c is NULL
+extern thread_local std::string g_create_error;
+int fail(fdtd_ctx *c, int code, const char *fmt, ...);
+int bfail(fdtd_batch *b, int code, const char *fmt, ...);
+
+#define CK(ctx, call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? FDTD_ERR_OOM : FDTD_ERR_CUDA, "%s: %s", #call, \
+                        cudaGetErrorString(e_));                                                        \
+    } while (0)
+
+// Device memory comes from a library-owned stream-ordered pool per device that keeps freed
+
+// ---- device and driver (ctx.cu)
+PFN_cuTensorMapEncodeTiled_v12000 get_encode();
+int num_sms();
+inline size_t esize(int storage) { return storage == FDTD_F32 ? 4 : 2; }
+
+// ---- stream-ordered device pool with host-side failure injection (pool.cu)
+extern std::atomic<int> g_fail_alloc_in;
+cudaMemPool_t lib_pool();
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
+cudaError_t dmalloc(fdtd_ctx *c, void **p, size_t bytes);
+
+// ---- context helpers (ctx.cu)
+CavityDesc make_desc(const fdtd_ctx *c, int parity_off);
+int upload_desc(fdtd_ctx *c);
+int encode_maps(fdtd_ctx *c, int set, int box_y);
+void drop_graphs(std::map<GraphKey, cudaGraphExec_t> &g);
+bool use_fused(const fdtd_ctx *c);
+bool use_temporal(const fdtd_ctx *c);
+int one_step_kind(const fdtd_ctx *c);
+int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind = 0);
+int check_status(fdtd_ctx *c, int *d_status, cudaStream_t s);
+int ensure_stage(fdtd_ctx *c);
+int ensure_stage2(fdtd_ctx *c);
+
+// ---- launch planning (plan.cu)
+struct Shape {
+    int kind;   // 0: one step per launch, 1: two steps per launch, 2: one fourth-order step
+    int tile_y, stages, ctas_per_sm;
+};
+Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0);
+int choose_zlen(long long cols, int nz, int grid, int zchunk, int prologue_planes);
+long long simulate_plan(const std::vector<int> &plan, long long cols, int G, int prologue);
+std::vector<int> plan_chunks(long long cols, int nz, int G, int prologue, int zchunk);
+TileRec base_rec(const fdtd_ctx *c, int parity_off, int set = 0);
+void append_tiles_plan(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y,
+                       const std::vector<int> &plan, int kind);
+void append_tiles(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y, int zlen, int kind = 0);
+std::vector<TileRec> assign_tiles(const std::vector<TileRec> &v, int G, int prologue, std::vector<int> &first);
+int build_tiles(fdtd_ctx *c, int kind);
+
+// ---- point currents and probes (extras_api.cu)
+bool extras_on(const fdtd_ctx *c);
+int launch_extras_after(fdtd_ctx *c, int copy);
+
+// ---- autotuning (autotune.cu)
+int trial_length(int trial_steps);
+std::vector<fdtd_tuning> tune_candidates(bool batch, int order = 2);
+
+}  // namespace fdtd

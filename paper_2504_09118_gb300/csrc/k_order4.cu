@@ -80,21 +80,12 @@ __global__ void simple4_e_kernel(const CavityDesc d, int copy) {
 
 constexpr int kRed4Threads = 256;
 
-// Kahan-compensated FP32 sum (Kahan 1965), folded into FP64 once per row.
-struct Kahan4 {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        const float y = __fsub_rn(v, c);
-        const float t = __fadd_rn(s, y);
-        c = __fsub_rn(__fsub_rn(t, s), y);
-        s = t;
-    }
-    __device__ __forceinline__ double take() {
-        const double r = (double)s - (double)c;
-        s = c = 0.f;
-        return r;
-    }
-};
+// The fourth-order difference in FP64 for the reductions, with the step's own weights (the FP32
+// values of c1, c2 and c1 + c2 the kernels use, exactly as doubles): the invariants of the discrete
+// scheme that is actually stepped.
+__device__ __forceinline__ double d4d(double a2, double a, double b, double b2, float wa, float wb) {
+    return (double)kC2 * (b2 - a2) + ((double)wb * b - (double)wa * a);
+}
 
 __device__ __forceinline__ double block_sum4(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -113,15 +104,33 @@ __device__ __forceinline__ double block_sum4(double v, double *sh) {
 //   WHAT == 1: sum of div4E^2 over interior nodes and of div4B^2 over cells, B = H/ch, with D = E/ce
 //   mirrored evenly and B oddly past a wall (the same folded weights as the step; B at index n is the
 //   constant far-face H).
+// Every term is formed in FP64 from the stored values (reciprocal coefficients in FP64) and summed
+// in FP64 in a fixed order.
 template <typename T, int WHAT>
 __global__ void __launch_bounds__(kRed4Threads) reduce4_kernel(const CavityDesc d, int copy, double *partial) {
     __shared__ double sh[kRed4Threads / 32];
+    __shared__ double itab[6 * kMaxTable];   // 1/ce xyz, 1/ch xyz per material id
     const int nx = d.nx, ny = d.ny, nz = d.nz;
     const long long P = d.pitch, Z = d.plane;
     double s0 = 0.0, s1 = 0.0;
-    Kahan4 k0, k1;
-    auto face_inv_ch = [&](int c, long long fi) -> float {
-        return d.coef_mode == COEF_SCALAR ? d.inv_ch[c] : 1.0f / d.face_ch[c][fi];
+    double isc[6];
+    for (int c = 0; c < 3; ++c) {
+        isc[c] = 1.0 / (double)d.ce[c];
+        isc[3 + c] = 1.0 / (double)d.ch[c];
+    }
+    if (d.coef_mode == COEF_ID8)
+        for (int e = threadIdx.x; e < 6 * d.ntab; e += kRed4Threads) {
+            const int m = e / 6, c = e % 6;
+            itab[e] = 1.0 / (double)d.table[8 * m + (c < 3 ? c : c + 1)];
+        }
+    __syncthreads();
+    auto IC = [&](int c, long long o) -> double {
+        if (d.coef_mode == COEF_ID8) return itab[6 * d.id[o] + c];
+        if (d.coef_mode == COEF_SCALAR) return isc[c];
+        return 1.0 / (double)d.coef[c][o];
+    };
+    auto face_inv_ch = [&](int c, long long fi) -> double {
+        return d.coef_mode == COEF_SCALAR ? isc[3 + c] : 1.0 / (double)d.face_ch[c][fi];
     };
     const int lane = threadIdx.x & 31;
     const long long nrows = (long long)ny * nz;
@@ -130,80 +139,75 @@ __global__ void __launch_bounds__(kRed4Threads) reduce4_kernel(const CavityDesc 
         const int j = (int)(r % ny), k = (int)(r / ny);
         for (int i = lane; i < nx; i += 32) {
             const long long o = (long long)k * Z + (long long)j * P + i;
-            auto F = [&](int f, int di, int dj, int dk) -> float {   // 0 outside the active range
+            auto F = [&](int f, int di, int dj, int dk) -> double {   // 0 outside the active range
                 const int a = i + di, b = j + dj, c = k + dk;
-                if (a < 0 || a >= nx || b < 0 || b >= ny || c < 0 || c >= nz) return 0.f;
-                return ld_field<T>(d, copy, f, o + dk * Z + dj * P + di);
+                if (a < 0 || a >= nx || b < 0 || b >= ny || c < 0 || c >= nz) return 0.0;
+                return (double)ld_field<T>(d, copy, f, o + dk * Z + dj * P + di);
             };
             if (WHAT == 0) {
                 const float wax = wa_h(i, nx), wbx = wb_h(i, nx), way = wa_h(j, ny), wby = wb_h(j, ny);
                 const float waz = wa_h(k, nz), wbz = wb_h(k, nz);
-                const float cx = __fsub_rn(d4(F(2, 0, -1, 0), F(2, 0, 0, 0), F(2, 0, 1, 0), F(2, 0, 2, 0), way, wby),
-                                           d4(F(1, 0, 0, -1), F(1, 0, 0, 0), F(1, 0, 0, 1), F(1, 0, 0, 2), waz, wbz));
-                const float cy = __fsub_rn(d4(F(0, 0, 0, -1), F(0, 0, 0, 0), F(0, 0, 0, 1), F(0, 0, 0, 2), waz, wbz),
-                                           d4(F(2, -1, 0, 0), F(2, 0, 0, 0), F(2, 1, 0, 0), F(2, 2, 0, 0), wax, wbx));
-                const float cz = __fsub_rn(d4(F(1, -1, 0, 0), F(1, 0, 0, 0), F(1, 1, 0, 0), F(1, 2, 0, 0), wax, wbx),
-                                           d4(F(0, 0, -1, 0), F(0, 0, 0, 0), F(0, 0, 1, 0), F(0, 0, 2, 0), way, wby));
-                const float ex = F(0, 0, 0, 0), ey = F(1, 0, 0, 0), ez = F(2, 0, 0, 0);
-                const float hx = F(3, 0, 0, 0), hy = F(4, 0, 0, 0), hz = F(5, 0, 0, 0);
-                const float e = ex * ex * ld_inv_coef(d, 0, o) + ey * ey * ld_inv_coef(d, 1, o) +
-                                ez * ez * ld_inv_coef(d, 2, o);
-                const float h = (hx * hx * ld_inv_coef(d, 3, o) - hx * cx) + (hy * hy * ld_inv_coef(d, 4, o) - hy * cy) +
-                                (hz * hz * ld_inv_coef(d, 5, o) - hz * cz);
-                k0.add(e);
-                k0.add(h);
+                const double cx = d4d(F(2, 0, -1, 0), F(2, 0, 0, 0), F(2, 0, 1, 0), F(2, 0, 2, 0), way, wby) -
+                                  d4d(F(1, 0, 0, -1), F(1, 0, 0, 0), F(1, 0, 0, 1), F(1, 0, 0, 2), waz, wbz);
+                const double cy = d4d(F(0, 0, 0, -1), F(0, 0, 0, 0), F(0, 0, 0, 1), F(0, 0, 0, 2), waz, wbz) -
+                                  d4d(F(2, -1, 0, 0), F(2, 0, 0, 0), F(2, 1, 0, 0), F(2, 2, 0, 0), wax, wbx);
+                const double cz = d4d(F(1, -1, 0, 0), F(1, 0, 0, 0), F(1, 1, 0, 0), F(1, 2, 0, 0), wax, wbx) -
+                                  d4d(F(0, 0, -1, 0), F(0, 0, 0, 0), F(0, 0, 1, 0), F(0, 0, 2, 0), way, wby);
+                const double ex = F(0, 0, 0, 0), ey = F(1, 0, 0, 0), ez = F(2, 0, 0, 0);
+                const double hx = F(3, 0, 0, 0), hy = F(4, 0, 0, 0), hz = F(5, 0, 0, 0);
+                const double e = ex * ex * IC(0, o) + ey * ey * IC(1, o) + ez * ez * IC(2, o);
+                const double h = hx * (hx * IC(3, o) - cx) + hy * (hy * IC(4, o) - cy) + hz * (hz * IC(5, o) - cz);
+                s0 += e + h;
             } else {
                 if (i >= 1 && j >= 1 && k >= 1) {
                     // D_a = E_a / ce_a; taps at E index -1 or n along a read 0 (folded even images)
-                    auto D = [&](int f, int di, int dj, int dk) -> float {
+                    auto D = [&](int f, int di, int dj, int dk) -> double {
                         const int a = i + di, b = j + dj, c = k + dk;
-                        if (a < 0 || a >= nx || b < 0 || b >= ny || c < 0 || c >= nz) return 0.f;
+                        if (a < 0 || a >= nx || b < 0 || b >= ny || c < 0 || c >= nz) return 0.0;
                         const long long q = o + dk * Z + dj * P + di;
-                        return ld_field<T>(d, copy, f, q) * ld_inv_coef(d, f, q);
+                        return (double)ld_field<T>(d, copy, f, q) * IC(f, q);
                     };
-                    const float de =
-                        d4(D(0, -2, 0, 0), D(0, -1, 0, 0), D(0, 0, 0, 0), D(0, 1, 0, 0), wa_e(i, nx), wb_e(i, nx)) +
-                        d4(D(1, 0, -2, 0), D(1, 0, -1, 0), D(1, 0, 0, 0), D(1, 0, 1, 0), wa_e(j, ny), wb_e(j, ny)) +
-                        d4(D(2, 0, 0, -2), D(2, 0, 0, -1), D(2, 0, 0, 0), D(2, 0, 0, 1), wa_e(k, nz), wb_e(k, nz));
-                    k0.add(de * de);
+                    const double de =
+                        d4d(D(0, -2, 0, 0), D(0, -1, 0, 0), D(0, 0, 0, 0), D(0, 1, 0, 0), wa_e(i, nx), wb_e(i, nx)) +
+                        d4d(D(1, 0, -2, 0), D(1, 0, -1, 0), D(1, 0, 0, 0), D(1, 0, 1, 0), wa_e(j, ny), wb_e(j, ny)) +
+                        d4d(D(2, 0, 0, -2), D(2, 0, 0, -1), D(2, 0, 0, 0), D(2, 0, 0, 1), wa_e(k, nz), wb_e(k, nz));
+                    s0 += de * de;
                 }
                 // B_a = H_a / ch_a at a node index along a: index n is the far face, beyond it 0
-                auto Bx = [&](int di) -> float {
+                auto Bx = [&](int di) -> double {
                     const int a = i + di;
-                    if (a < 0 || a > nx) return 0.f;
+                    if (a < 0 || a > nx) return 0.0;
                     if (a == nx) {
                         const long long fi = (long long)k * ny + j;
-                        return d.face[0][fi] * face_inv_ch(0, fi);
+                        return (double)d.face[0][fi] * face_inv_ch(0, fi);
                     }
-                    return ld_field<T>(d, copy, 3, o + di) * ld_inv_coef(d, 3, o + di);
+                    return (double)ld_field<T>(d, copy, 3, o + di) * IC(3, o + di);
                 };
-                auto By = [&](int dj) -> float {
+                auto By = [&](int dj) -> double {
                     const int b = j + dj;
-                    if (b < 0 || b > ny) return 0.f;
+                    if (b < 0 || b > ny) return 0.0;
                     if (b == ny) {
                         const long long fi = (long long)k * nx + i;
-                        return d.face[1][fi] * face_inv_ch(1, fi);
+                        return (double)d.face[1][fi] * face_inv_ch(1, fi);
                     }
-                    return ld_field<T>(d, copy, 4, o + dj * P) * ld_inv_coef(d, 4, o + dj * P);
+                    return (double)ld_field<T>(d, copy, 4, o + dj * P) * IC(4, o + dj * P);
                 };
-                auto Bz = [&](int dk) -> float {
+                auto Bz = [&](int dk) -> double {
                     const int c = k + dk;
-                    if (c < 0 || c > nz) return 0.f;
+                    if (c < 0 || c > nz) return 0.0;
                     if (c == nz) {
                         const long long fi = (long long)j * nx + i;
-                        return d.face[2][fi] * face_inv_ch(2, fi);
+                        return (double)d.face[2][fi] * face_inv_ch(2, fi);
                     }
-                    return ld_field<T>(d, copy, 5, o + dk * Z) * ld_inv_coef(d, 5, o + dk * Z);
+                    return (double)ld_field<T>(d, copy, 5, o + dk * Z) * IC(5, o + dk * Z);
                 };
                 // the image of B one past a wall is odd: the folded weights of a difference of E
-                const float dh = d4(Bx(-1), Bx(0), Bx(1), Bx(2), wa_h(i, nx), wb_h(i, nx)) +
-                                 d4(By(-1), By(0), By(1), By(2), wa_h(j, ny), wb_h(j, ny)) +
-                                 d4(Bz(-1), Bz(0), Bz(1), Bz(2), wa_h(k, nz), wb_h(k, nz));
-                k1.add(dh * dh);
+                const double dh = d4d(Bx(-1), Bx(0), Bx(1), Bx(2), wa_h(i, nx), wb_h(i, nx)) +
+                                  d4d(By(-1), By(0), By(1), By(2), wa_h(j, ny), wb_h(j, ny)) +
+                                  d4d(Bz(-1), Bz(0), Bz(1), Bz(2), wa_h(k, nz), wb_h(k, nz));
+                s1 += dh * dh;
             }
         }
-        s0 += k0.take();
-        s1 += k1.take();
     }
     if (WHAT == 0) {
         // constant far-face normal H: curl E vanishes there, so its energy term is H^2/ch
@@ -215,8 +219,8 @@ __global__ void __launch_bounds__(kRed4Threads) reduce4_kernel(const CavityDesc 
             if (n < nfx) { c = 0; fi = n; }
             else if (n < nfx + nfy) { c = 1; fi = n - nfx; }
             else { c = 2; fi = n - nfx - nfy; }
-            const float h = d.face[c][fi];
-            s0 += (double)(h * h * face_inv_ch(c, fi));
+            const double h = d.face[c][fi];
+            s0 += h * h * face_inv_ch(c, fi);
         }
     }
     const double a = block_sum4(s0, sh);

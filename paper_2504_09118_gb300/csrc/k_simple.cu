@@ -136,54 +136,61 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
-// FP32 sum with Kahan compensation (Kahan 1965): the rounding error of every addition is carried
-// into the next, so a lane's partial over one row is exact to a few units in the last place
-// however many cells it holds; partials are folded into FP64 once per row.
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        const float y = __fsub_rn(v, c);
-        const float t = __fadd_rn(s, y);
-        c = __fsub_rn(__fsub_rn(t, s), y);
-        s = t;
-    }
-    __device__ __forceinline__ double take() {
-        const double r = (double)s - (double)c;
-        s = c = 0.f;
-        return r;
+// Reciprocal coefficients in FP64 for the reductions: 1/ce (c = 0..2) and 1/ch (c = 3..5).
+// Material-id mode keeps a table of them in shared memory (filled by the block before use), scalar
+// mode six registers; per-position arrays divide per cell (that mode is rare and slow anyway).
+struct InvCoef64 {
+    const CavityDesc *d;
+    const double *tab;   // shared, 6 per id (COEF_ID8)
+    double sc[6];        // COEF_SCALAR
+    __device__ __forceinline__ double operator()(int c, long long o, int m) const {
+        if (d->coef_mode == COEF_ID8) return tab[6 * m + c];
+        if (d->coef_mode == COEF_SCALAR) return sc[c];
+        return 1.0 / (double)d->coef[c][o];
     }
 };
+
+// Fills tab (6 * ntab doubles, shared) and the scalar reciprocals; call with the whole block, then sync.
+__device__ __forceinline__ InvCoef64 make_inv_coef64(const CavityDesc &d, double *tab) {
+    InvCoef64 r;
+    r.d = &d;
+    r.tab = tab;
+    for (int c = 0; c < 3; ++c) {
+        r.sc[c] = 1.0 / (double)d.ce[c];
+        r.sc[3 + c] = 1.0 / (double)d.ch[c];
+    }
+    if (d.coef_mode == COEF_ID8)
+        for (int e = threadIdx.x; e < 6 * d.ntab; e += blockDim.x) {
+            const int m = e / 6, c = e % 6;
+            tab[e] = 1.0 / (double)d.table[8 * m + (c < 3 ? c : c + 1)];
+        }
+    return r;
+}
+
+// 1/ch in FP64 at far-face entry fi of face array c.
+__device__ __forceinline__ double face_inv_ch64(const CavityDesc &d, int c, long long fi) {
+    return d.coef_mode == COEF_SCALAR ? 1.0 / (double)d.ch[c] : 1.0 / (double)d.face_ch[c][fi];
+}
 
 // Per block, in a fixed order (warps over rows, lanes along x; far-face H appended):
 //   WHAT == 0: energy sum  E^2/ce + H^2/ch - H curl E   (W without the 1/2 dt/dx factor)
 //   WHAT == 1: sum of divE^2 over interior nodes and of divH^2 over cells.
-// Each cell's terms are formed in FP32 with precomputed reciprocal coefficients (relative
-// error of order 2^-23 per term, unbiased), summed per lane and row with Kahan compensation,
-// and accumulated in FP64 (GB300's FP64 rate is a small fraction of its FP32 rate, so FP64
-// work is kept to one addition per lane and row).
+// Every term is formed in FP64 from the stored values (converted exactly to double: the curl
+// differences of two stored values are then exact, the reciprocal coefficients are FP64) and summed
+// in FP64, per lane and then per block in a fixed order, so the result is deterministic.
 template <typename T, int WHAT>
 __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const CavityDesc d, int copy, double *partial) {
     __shared__ double sh[kRedThreads / 32];
-    __shared__ float itab[8 * kMaxTable];   // reciprocal coefficient table (material-id mode)
+    __shared__ double itab[6 * kMaxTable];
     const int nx = d.nx, ny = d.ny, nz = d.nz;
     const long long P = d.pitch, Z = d.plane;
     double s0 = 0.0, s1 = 0.0;
-    Kahan k0, k1;
     const bool ids = d.coef_mode == COEF_ID8;
-    if (ids)
-        for (int e = threadIdx.x; e < 8 * d.ntab; e += kRedThreads) itab[e] = d.inv_table[e];
+    const InvCoef64 IC = make_inv_coef64(d, itab);
     __syncthreads();
-    auto F = [&](int f, long long o) -> float { return ld_field<T>(d, copy, f, o); };
-    // 1/ce (c = 0..2) or 1/ch (c = 3..5) at offset o; `m` is the cell's material id in id mode
-    auto ICm = [&](int c, long long o, int m) -> float {
-        if (ids) return itab[8 * m + (c < 3 ? c : c + 1)];
-        return ld_inv_coef(d, c, o);
-    };
-    auto IC = [&](int c, long long o) -> float { return ICm(c, o, ids ? d.id[o] : 0); };
-    auto face_inv_ch = [&](int c, long long fi) -> float {
-        return d.coef_mode == COEF_SCALAR ? d.inv_ch[c] : 1.0f / d.face_ch[c][fi];
-    };
-    // one warp per (j, k) row, lanes along x: coalesced loads and one division per row, not per cell
+    auto F = [&](int f, long long o) -> double { return (double)ld_field<T>(d, copy, f, o); };
+    auto ICo = [&](int c, long long o) -> double { return IC(c, o, ids ? d.id[o] : 0); };
+    // one warp per (j, k) row, lanes along x: coalesced loads
     const int lane = threadIdx.x & 31;
     const long long nrows = (long long)ny * nz;
     const long long nwarps = ((long long)gridDim.x * kRedThreads) >> 5;
@@ -191,39 +198,34 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const CavityDesc d,
         const int j = (int)(r % ny), k = (int)(r / ny);
         for (int i = lane; i < nx; i += 32) {
             const long long o = (long long)k * Z + (long long)j * P + i;
-            const float ex = F(0, o), ey = F(1, o), ez = F(2, o), hx = F(3, o), hy = F(4, o), hz = F(5, o);
+            const double ex = F(0, o), ey = F(1, o), ez = F(2, o), hx = F(3, o), hy = F(4, o), hz = F(5, o);
             const int m = ids ? d.id[o] : 0;
             if (WHAT == 0) {
-                const float ex_j1 = j + 1 < ny ? F(0, o + P) : 0.f, ex_k1 = k + 1 < nz ? F(0, o + Z) : 0.f;
-                const float ey_i1 = i + 1 < nx ? F(1, o + 1) : 0.f, ey_k1 = k + 1 < nz ? F(1, o + Z) : 0.f;
-                const float ez_i1 = i + 1 < nx ? F(2, o + 1) : 0.f, ez_j1 = j + 1 < ny ? F(2, o + P) : 0.f;
-                const float cx = (ez_j1 - ez) - (ey_k1 - ey);
-                const float cy = (ex_k1 - ex) - (ez_i1 - ez);
-                const float cz = (ey_i1 - ey) - (ex_j1 - ex);
-                const float e = ex * ex * ICm(0, o, m) + ey * ey * ICm(1, o, m) + ez * ez * ICm(2, o, m);
-                const float h = (hx * hx * ICm(3, o, m) - hx * cx) + (hy * hy * ICm(4, o, m) - hy * cy) +
-                                (hz * hz * ICm(5, o, m) - hz * cz);
-                k0.add(e);
-                k0.add(h);
+                const double ex_j1 = j + 1 < ny ? F(0, o + P) : 0.0, ex_k1 = k + 1 < nz ? F(0, o + Z) : 0.0;
+                const double ey_i1 = i + 1 < nx ? F(1, o + 1) : 0.0, ey_k1 = k + 1 < nz ? F(1, o + Z) : 0.0;
+                const double ez_i1 = i + 1 < nx ? F(2, o + 1) : 0.0, ez_j1 = j + 1 < ny ? F(2, o + P) : 0.0;
+                const double cx = (ez_j1 - ez) - (ey_k1 - ey);
+                const double cy = (ex_k1 - ex) - (ez_i1 - ez);
+                const double cz = (ey_i1 - ey) - (ex_j1 - ex);
+                const double e = ex * ex * IC(0, o, m) + ey * ey * IC(1, o, m) + ez * ez * IC(2, o, m);
+                const double h = hx * (hx * IC(3, o, m) - cx) + hy * (hy * IC(4, o, m) - cy) +
+                                 hz * (hz * IC(5, o, m) - cz);
+                s0 += e + h;
             } else {
                 if (i >= 1 && j >= 1 && k >= 1) {
-                    const float de = (ex * ICm(0, o, m) - F(0, o - 1) * IC(0, o - 1)) +
-                                     (ey * ICm(1, o, m) - F(1, o - P) * IC(1, o - P)) +
-                                     (ez * ICm(2, o, m) - F(2, o - Z) * IC(2, o - Z));
-                    k0.add(de * de);
+                    const double de = (ex * IC(0, o, m) - F(0, o - 1) * ICo(0, o - 1)) +
+                                      (ey * IC(1, o, m) - F(1, o - P) * ICo(1, o - P)) +
+                                      (ez * IC(2, o, m) - F(2, o - Z) * ICo(2, o - Z));
+                    s0 += de * de;
                 }
-                const float bx1 = i + 1 < nx ? F(3, o + 1) * IC(3, o + 1)
-                                             : d.face[0][(long long)k * ny + j] * face_inv_ch(0, (long long)k * ny + j);
-                const float by1 = j + 1 < ny ? F(4, o + P) * IC(4, o + P)
-                                             : d.face[1][(long long)k * nx + i] * face_inv_ch(1, (long long)k * nx + i);
-                const float bz1 = k + 1 < nz ? F(5, o + Z) * IC(5, o + Z)
-                                             : d.face[2][(long long)j * nx + i] * face_inv_ch(2, (long long)j * nx + i);
-                const float dh = (bx1 - hx * ICm(3, o, m)) + (by1 - hy * ICm(4, o, m)) + (bz1 - hz * ICm(5, o, m));
-                k1.add(dh * dh);
+                const long long fx = (long long)k * ny + j, fy = (long long)k * nx + i, fz = (long long)j * nx + i;
+                const double bx1 = i + 1 < nx ? F(3, o + 1) * ICo(3, o + 1) : d.face[0][fx] * face_inv_ch64(d, 0, fx);
+                const double by1 = j + 1 < ny ? F(4, o + P) * ICo(4, o + P) : d.face[1][fy] * face_inv_ch64(d, 1, fy);
+                const double bz1 = k + 1 < nz ? F(5, o + Z) * ICo(5, o + Z) : d.face[2][fz] * face_inv_ch64(d, 2, fz);
+                const double dh = (bx1 - hx * IC(3, o, m)) + (by1 - hy * IC(4, o, m)) + (bz1 - hz * IC(5, o, m));
+                s1 += dh * dh;
             }
         }
-        s0 += k0.take();
-        s1 += k1.take();
     }
     if (WHAT == 0) {
         // constant far-face normal H: curl E vanishes there, so its energy term is H^2/ch
@@ -235,8 +237,8 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const CavityDesc d,
             if (n < nfx) { c = 0; fi = n; }
             else if (n < nfx + nfy) { c = 1; fi = n - nfx; }
             else { c = 2; fi = n - nfx - nfy; }
-            const float h = d.face[c][fi];
-            s0 += (double)(h * h * face_inv_ch(c, fi));
+            const double h = d.face[c][fi];
+            s0 += h * h * face_inv_ch64(d, c, fi);
         }
     }
     const double a = block_sum(s0, sh);

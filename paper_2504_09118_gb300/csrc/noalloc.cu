@@ -20,6 +20,12 @@
 // The host side resolves the array's device address with cudaGetSymbolAddress
 // once per device, with that device current, on the first call made on that
 // device; that first call should therefore come before any stream capture.
+// The address is remembered together with the CUDA context it belongs to: when
+// the current context of the device is a different one (the primary context
+// was reset with cudaDeviceReset and made again, which reloads the library's
+// device code), the address is looked up again before the kernel is launched.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 #include <string>
 
@@ -28,7 +34,7 @@
 
 namespace fdtd {
 
-void set_last_error(const char *msg);   // api.cu: message returned by fdtd_last_error(NULL)
+void set_last_error(const char *msg);   // ctx.cu: message returned by fdtd_last_error(NULL)
 
 namespace {
 
@@ -105,19 +111,43 @@ __global__ void __launch_bounds__(kThreads) energy_final_kernel(const double *pa
 
 std::mutex g_mu;
 double *g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};   // the context each cached address belongs to
 
-// Device address of g_energy_partial on the current device (resolved once per device).
+// cuCtxGetCurrent from the driver (through the runtime's entry-point query, so the library links
+// against no driver library); NULL when the driver does not offer it.
+PFN_cuCtxGetCurrent_v4000 ctx_get_current() {
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    });
+    return fn;
+}
+
+// Device address of g_energy_partial on the current device: resolved on the first call made on a
+// device, and again whenever the device's current context is not the one it was resolved in.
 cudaError_t scratch_address(double **out, int *dev_out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    CUcontext cur = nullptr;
+    auto get = ctx_get_current();
+    if (!get || get(&cur) != CUDA_SUCCESS) return cudaErrorUnknown;
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!cur || !g_scratch_addr[dev] || g_scratch_ctx[dev] != cur) {
+        // no context current yet on this thread (cudaGetSymbolAddress makes the device's primary
+        // context current), or another context than the cached address belongs to
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_energy_partial);
         if (e != cudaSuccess) return e;
+        if (get(&cur) != CUDA_SUCCESS || !cur) return cudaErrorUnknown;
         g_scratch_addr[dev] = static_cast<double *>(p);
+        g_scratch_ctx[dev] = cur;
     }
     *out = g_scratch_addr[dev];
     *dev_out = dev;
@@ -141,11 +171,11 @@ extern "C" int fdtd_energy_static(int nx, int ny, int nz, double dt, double dx, 
         if (!f[c]) return fail_static(FDTD_ERR_ARG, "fdtd_energy_static: a field pointer is NULL");
     if (nx < 1 || ny < 1 || nz < 1)
         return fail_static(FDTD_ERR_ARG, "fdtd_energy_static: cell counts must be >= 1");
-    if (nz + 1 > kStaticPlanes)
+    if ((long long)nz + 1 > kStaticPlanes)
         return fail_static(FDTD_ERR_ARG, "fdtd_energy_static: nz = " + std::to_string(nz) +
                                              " exceeds the static scratch limit of " +
                                              std::to_string(kStaticPlanes - 1) + " planes");
-    if ((long long)(nx + 1) * (ny + 1) > (1ll << 31))
+    if (((long long)nx + 1) * ((long long)ny + 1) > (1ll << 31))
         return fail_static(FDTD_ERR_ARG, "fdtd_energy_static: a z-plane has more than 2^31 points");
     if (!(dt > 0) || !(dx > 0)) return fail_static(FDTD_ERR_ARG, "fdtd_energy_static: dt and dx must be positive");
     const bool have_ce = ce && ce[0] && ce[1] && ce[2];

@@ -100,6 +100,43 @@ def test_128_crop_of_the_512_layout_vs_oracle():
     assert abs(w1 - w0) / w0 <= ENERGY_DRIFT_F32
 
 
+def _oracle_invariants(fields, ce, ch):
+    import oracle
+    f64 = oracle.as_f64(fields)
+    ce64 = [c.astype(np.float64) for c in ce]
+    w = oracle.energy(f64, ce64, ch, DT)
+    de, dh = oracle.divergence(f64, ce64, ch)
+    return w, math.sqrt(float(np.sum(de * de))), math.sqrt(float(np.sum(dh * dh)))
+
+
+@pytest.mark.parametrize("workload", ["single512", "precision384_f16"])
+def test_fullsize_reductions_match_oracle_on_the_stored_state(workload):
+    """The FP64 energy and divergence reductions at the bench sizes: on the loaded state and after 200
+    steps, the library's values equal the FP64 oracle's energy and divergence of exactly the state the
+    library holds (read back), to 1e-10 relative (the oracle sums its 10^8-10^9 terms serially in FP64,
+    which alone moves the sum by about 1e-12-1e-11).  This is the floor under every energy drift the
+    benchmarks quote (FP32 drifts of about 1e-9 over 200-1000 steps)."""
+    from paper_2504_09118_gb300 import Cavity
+    w = bench.WORKLOADS[workload]
+    n = w["n"]
+    ce, ch = bench.sphere_coefs(w)
+    f = ci.random_fields(w["field_seed"], *n)
+    with Cavity(*n, DT, 1.0, ce, ch, w["storage"]) as cav:
+        cav.tune(**bench.BENCH_TUNING)
+        cav.set_fields(f)
+        states = []
+        for steps in (0, 200):
+            cav.step(steps)
+            states.append((cav.energy(), cav.divergence(), cav.get_fields()))
+    for wg, (deg, dhg), g in states:
+        wo, deo, dho = _oracle_invariants(g, ce, ch)
+        assert abs(wg - wo) <= 1e-10 * abs(wo), (wg, wo)
+        assert abs(deg - deo) <= 1e-10 * deo, (deg, deo)
+        assert abs(dhg - dho) <= 1e-10 * dho, (dhg, dho)
+    if w["storage"] == 0:   # the FP32 run conserves the energy far below the contract bound
+        assert abs(states[1][0] - states[0][0]) / states[0][0] <= 1e-7
+
+
 def test_512_two_step_equals_one_step_bitwise():
     """The bench's launch configuration (two-step kernel) against the one-step kernel at full size."""
     from paper_2504_09118_gb300 import Cavity
@@ -118,33 +155,54 @@ def test_512_two_step_equals_one_step_bitwise():
         assert np.array_equal(x, y), name
 
 
-@pytest.mark.parametrize("storage", [1, 2])
-def test_384_precision_1000_steps(storage):
-    from paper_2504_09118_gb300 import Cavity
-    w = bench.WORKLOADS["precision384_f16" if storage == 1 else "precision384_bf16"]
+@pytest.fixture(scope="module")
+def precision384_oracle():
+    """The 384^3 sphere cavity of the precision workload after 1000 steps of the FP64 oracle (OpenMP
+    build on the host cores; about 2.5 minutes on 16 cores), from the FP32 input both sides start from."""
+    import oracle
+    w = bench.WORKLOADS["precision384_f16"]
     n, steps = w["n"], w["steps"]
     ce, ch = bench.sphere_coefs(w)
     f = ci.random_fields(w["field_seed"], *n)
-    with Cavity(*n, DT, 1.0, ce, ch, 0) as ref_cav:
-        ref_cav.tune(**bench.BENCH_TUNING)
-        ref_cav.set_fields(f)
-        ref_cav.step(steps)
-        ref = ref_cav.get_fields()
-    with Cavity(*n, DT, 1.0, ce, ch, storage) as cav:
+    ref = oracle.as_f64(f)
+    ce64 = [c.astype(np.float64) for c in ce]
+    w0 = oracle.energy(ref, ce64, ch, DT)
+    oracle.step(ref, ce64, ch, steps, omp=True)
+    return dict(n=n, steps=steps, ce=ce, ch=ch, f=f, ref=ref, drift=(oracle.energy(ref, ce64, ch, DT) - w0) / w0)
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_384_precision_1000_steps_vs_oracle(storage, precision384_oracle):
+    """configs' precision workload: 384^3, 32 dielectric spheres, 1000 steps in the bench's launch
+    configuration, per field against the FP64 oracle.  FP32 storage: rel-L2 <= 1e-4 per field and energy
+    drift <= 1e-5; FP16 / BF16 storage: per field within 3x the random-walk estimate
+    (u / sqrt(3)) sqrt(N + 1) of 16-bit rounding, and the energy drift within the same bound."""
+    from paper_2504_09118_gb300 import Cavity
+    P = precision384_oracle
+    n, steps, ref = P["n"], P["steps"], P["ref"]
+    assert abs(P["drift"]) <= 1e-11   # the oracle conserves the discrete energy to rounding
+    with Cavity(*n, DT, 1.0, P["ce"], P["ch"], storage) as cav:
         cav.tune(**bench.BENCH_TUNING)
-        cav.set_fields(f)
+        cav.set_fields(P["f"])
         w0 = cav.energy()
         cav.step(steps)
         w1 = cav.energy()
         got = cav.get_fields()
-    num = sum(float(np.sum((a.astype(np.float64) - b) ** 2)) for a, b in zip(got, ref))
-    den = sum(float(np.sum(b.astype(np.float64) ** 2)) for b in ref)
-    err = math.sqrt(num / den)
-    u = 2.0 ** -11 if storage == 1 else 2.0 ** -8
-    est = u / math.sqrt(3.0) * math.sqrt(steps + 1)
-    print(f"storage {storage}: rel-L2 vs FP32 GPU {err:.3e} (estimate {est:.3e}); energy drift {(w1 - w0) / w0:.3e}")
-    assert err <= 3 * est
-    assert abs(w1 - w0) / w0 <= 3 * est
+    errs = {}
+    for c, name in enumerate(ci.COMPONENTS):
+        m = ci.extent_mask(name, *n)
+        errs[name] = float(np.linalg.norm(got[c][m].astype(np.float64) - ref[c][m]) / np.linalg.norm(ref[c][m]))
+    drift = (w1 - w0) / w0
+    print(f"storage {storage}: per-field rel-L2 vs FP64 oracle " +
+          " ".join(f"{k} {v:.3e}" for k, v in errs.items()) + f"; energy drift {drift:.3e}")
+    if storage == 0:
+        assert max(errs.values()) <= REL_L2_F32, errs
+        assert abs(drift) <= ENERGY_DRIFT_F32
+    else:
+        u = 2.0 ** -11 if storage == 1 else 2.0 ** -8
+        est = u / math.sqrt(3.0) * math.sqrt(steps + 1)
+        assert max(errs.values()) <= 3 * est, (errs, est)
+        assert abs(drift) <= 3 * est
 
 
 def test_512_fourth_order_sampled_parity_invariants_and_bitwise():

@@ -81,3 +81,47 @@ def test_16bit_fused_independent_of_tiling(storage):
     b, *_ = run_gpu(f, dims, steps=12, storage=storage, tuning={"kernel": 2, "tile_y": 8, "zchunk": 5, "stages": 3})
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def _per_field(got, ref, dims):
+    nx, ny, nz = dims
+    norm = math.sqrt(sum(float(np.sum(np.asarray(r, np.float64) ** 2)) for r in ref))
+    own, state = {}, {}
+    for c, name in enumerate(ci.COMPONENTS):
+        m = ci.extent_mask(name, nx, ny, nz)
+        d = float(np.linalg.norm(np.asarray(got[c], np.float64)[m] - np.asarray(ref[c], np.float64)[m]))
+        own[name] = d / float(np.linalg.norm(np.asarray(ref[c], np.float64)[m]))
+        state[name] = d / norm
+    return own, state
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_16bit_per_field_errors_with_components_far_apart(storage):
+    """One storage scale per field (E, H), components 2^12 apart in magnitude, per-field errors against
+    the FP64 oracle.  (a) Random state with Ex and Hz scaled by 2^-12: the curl mixes the components
+    within a step, and every component, the small two included, stays within the random-walk bound of
+    its own norm.  (b) A z-invariant (Ez, Hx, Hy) field plus a 2^-12 perturbation, which keeps
+    (Ex, Ey, Hz) about 2^12 below the others for the whole run: relative to the state every component
+    is within the bound, the large ones also relative to their own norms.  The small ones carry
+    errors set by the rounding of the large ones they couple to, which a scale of their own would not
+    change (tests/test_storage_scale.py shows the same errors with per-component scales)."""
+    import oracle
+    from tests.test_storage_scale import tm_plus_small_state
+    dims = (40, 33, 21)
+    steps = 60
+    b = bound(storage, steps)
+    f = ci.random_fields(8, *dims)
+    for c in (0, 5):
+        f[c] = (f[c] * np.float32(2.0 ** -12)).astype(np.float32)
+    for case, fields in (("scaled", f), ("tm_plus_small", tm_plus_small_state(*dims, 9))):
+        ref = oracle.as_f64(fields)
+        oracle.step(ref, DT, DT, steps, omp=True)
+        got, w0, w1, *_ = run_gpu(fields, dims, steps=steps, storage=storage)
+        own, state = _per_field(got, ref, dims)
+        print(f"storage {storage} {case}: own-norm " + " ".join(f"{k} {v:.2e}" for k, v in own.items()) +
+              " | state-norm " + " ".join(f"{k} {v:.2e}" for k, v in state.items()))
+        assert max(state.values()) <= b, (case, state)
+        large = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz") if case == "scaled" else ("Ez", "Hx", "Hy")
+        for name in large:
+            assert own[name] <= b, (case, name, own[name])
+        assert abs(w1 - w0) / w0 <= b

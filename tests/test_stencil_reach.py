@@ -50,9 +50,9 @@ def test_reach_of_the_schemes(order, steps, expected):
 
 
 def test_box_heights_cover_the_reach_exactly():
-    src = open(os.path.join(ROOT, "paper_2504_09118_gb300", "csrc", "api.cu")).read()
+    src = open(os.path.join(ROOT, "paper_2504_09118_gb300", "csrc", "plan.cu")).read()
     m = re.search(r"encode_maps\(c, kind, s\.tile_y \+ \(kind == 0 \? (\d+) : kind == 1 \? (\d+) : (\d+)\)\)", src)
-    assert m, "box-height expression not found in api.cu"
+    assert m, "box-height expression not found in plan.cu"
     one_step, two_step, fourth = (int(g) for g in m.groups())
     assert one_step == 2 * reach(2, 1)[1]
     assert two_step == 2 * reach(2, 2)[1]
