@@ -40,8 +40,12 @@ import cavity_inputs as ci  # noqa: E402
 WORKLOADS = {
     # name: (nx, ny, nz, leapfrog steps per bench step, storage, sphere seed, field seed)
     "single512": dict(n=(512, 512, 512), steps=200, storage=0, sphere_seed=1, field_seed=2, spheres=32),
+    # the same cavity with 16-bit storage (FP32 arithmetic)
+    "single512_f16": dict(n=(512, 512, 512), steps=200, storage=1, sphere_seed=1, field_seed=2, spheres=32),
+    "single512_bf16": dict(n=(512, 512, 512), steps=200, storage=2, sphere_seed=1, field_seed=2, spheres=32),
     # small case for ncu captures (fields 0.8 GB > L2, a few launches)
     "single256": dict(n=(256, 256, 256), steps=20, storage=0, sphere_seed=1, field_seed=2, spheres=8),
+    "single256_f16": dict(n=(256, 256, 256), steps=20, storage=1, sphere_seed=1, field_seed=2, spheres=8),
     "precision384_f16": dict(n=(384, 384, 384), steps=1000, storage=1, sphere_seed=3, field_seed=4, spheres=32),
     "precision384_bf16": dict(n=(384, 384, 384), steps=1000, storage=2, sphere_seed=3, field_seed=4, spheres=32),
     # 256 independent cavities, sides iid U{16..96}, vacuum or spheres (p = 1/2), 500 steps per bench step
@@ -65,8 +69,9 @@ BENCH_TUNING = dict(kernel=3, tile_y=16, stages=4, zchunk=0, ctas_per_sm=0, use_
 # batch workload, and measured best on the serving stream; the mix changes every chunk, so it is fixed
 # rather than re-tuned).
 SERVE_TUNING = dict(kernel=3, tile_y=16, stages=4)
-STEPS_PER_LAUNCH = {1: 0.5, 2: 1, 3: 2}   # leapfrog steps per launch of each kernel kind (SIMPLE: H and E launches)
-DOMINANT_KERNEL = {1: "simple_h_kernel/simple_e_kernel", 2: "fused_step_kernel", 3: "fused2_step_kernel"}
+STEPS_PER_LAUNCH = {1: 0.5, 2: 1, 3: 2, 4: 2}   # leapfrog steps per launch of each kernel kind (SIMPLE: H and E launches)
+DOMINANT_KERNEL = {1: "simple_h_kernel/simple_e_kernel", 2: "fused_step_kernel", 3: "fused2_step_kernel",
+                   4: "fused2r_step_kernel"}
 ID_BYTES = 1  # material id per cell
 NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e nominal bandwidth (context beside the measured copy peak)
 
@@ -79,7 +84,12 @@ MEASURED_TRAFFIC = {
 }
 
 
+TUNING_OVERRIDE: dict | None = None   # --tuning: the single-cavity launch configuration to time instead
+
+
 def tuning_of(w) -> dict:
+    if TUNING_OVERRIDE is not None:
+        return dict(BENCH_TUNING, **TUNING_OVERRIDE)
     return w.get("tuning", BENCH_TUNING)
 
 
@@ -95,7 +105,7 @@ def kernel_source_hash(w=None) -> str:
     if (w or {}).get("order", 2) == 4:
         src = "k_order4.cu" if k == 1 else "k_fused4.cu"
     else:
-        src = {2: "k_fused.cu", 3: "k_fused2.cu"}.get(k, "k_simple.cu")
+        src = {2: "k_fused.cu", 3: "k_fused2.cu", 4: "k_fused2r.cu"}.get(k, "k_simple.cu")
     headers = ["fdtd_internal.cuh", "fused_common.cuh"] + (["order4.cuh"] if (w or {}).get("order", 2) == 4 else [])
     h = hashlib.sha256()
     for name in [src] + headers:
@@ -338,7 +348,7 @@ def run_batch(args, w):
             "batched_vs_plain": round(value / plain, 3),
             "clocks": clk.summary(),
             # each launch (one step, or two with the two-step kernel) is followed by the clock kernel
-            "gpu_launches": 2 * args.steps * per // (2 if tuning["kernel"] == 3 else 1)}
+            "gpu_launches": 2 * args.steps * per // (2 if tuning["kernel"] in (3, 4) else 1)}
 
 
 def run_serve(args, w):
@@ -485,7 +495,13 @@ def main():
     ap.add_argument("--legs", default="batched,served,precision",
                     help="comma-separated legs nested in the single-cavity line at N = 1 (batched: 256 uneven "
                          "cavities; served: the 10k-request Poisson stream; precision: 384^3 FP16/BF16); '' for none")
+    ap.add_argument("--tuning", default=None,
+                    help="JSON launch configuration of the single-cavity workloads (default: BENCH_TUNING or "
+                         "the workload's own)")
     args = ap.parse_args()
+    global TUNING_OVERRIDE
+    if args.tuning:
+        TUNING_OVERRIDE = json.loads(args.tuning)
     w = WORKLOADS[args.workload]
     standalone = {"batch": ("batched", run_batch), "serve": ("served", run_serve),
                   "precision": ("precision", run_precision)}

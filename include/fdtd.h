@@ -76,7 +76,9 @@ enum fdtd_kernel {
                                 per-position coefficient arrays); fdtd_autotune picks by timing */
     FDTD_KERNEL_SIMPLE = 1,  /* two launches per step (H, then E), one thread per cell; unfused baseline */
     FDTD_KERNEL_FUSED = 2,   /* one TMA-pipelined launch per step: H then E fused in a z-march */
-    FDTD_KERNEL_TEMPORAL = 3 /* two steps per launch (temporal blocking); an odd count ends with one FUSED step */
+    FDTD_KERNEL_TEMPORAL = 3, /* two steps per launch (temporal blocking); an odd count ends with one FUSED step */
+    FDTD_KERNEL_TEMPORAL2 = 4 /* TEMPORAL with two tile rows per consumer warp (tile_y 12 or 16): same tiles and
+                                 results (FP32: bit for bit), fewer instructions per cell-step */
 };
 
 /* Launch configuration of the step kernel; zero fields take the default. */
@@ -84,7 +86,7 @@ typedef struct fdtd_tuning {
     int kernel;       /* enum fdtd_kernel */
     int tile_y;       /* fused: cells per tile along y (FUSED: 4, 8 or 16; TEMPORAL: 8, 12 or 16; AUTO: any
                          of these, each kernel taking its default when the value is not one of its
-                         own); x tile is 64 cells (TEMPORAL: 60 for FP32, 56 for 16-bit storage) */
+                         own); x tile is 64 cells (TEMPORAL, TEMPORAL2: 60) */
     int zchunk;       /* fused: planes per tile along z (>= 1); 0 = choose for load balance */
     int ctas_per_sm;  /* fused: persistent CTAs per SM (1 or 2); 0 = as many as fit */
     int stages;       /* fused: TMA pipeline depth in planes (3..8, lowered to fit shared memory); 0 = default */
@@ -215,8 +217,9 @@ FDTD_API int fdtd_set_order(fdtd_ctx *ctx, int order);
 FDTD_API int fdtd_get_order(const fdtd_ctx *ctx);
 
 /* fdtd_autotune - choose the step kernel and launch shape by timing candidates on this
- * context's own state: the one-step kernel with 4, 8, 16-row tiles and the two-step kernel with
- * 8, 12, 16-row tiles and 4 or 6 ring slots (graphs on).  Each candidate runs trial_steps steps
+ * context's own state: the one-step kernel with 4, 8, 16-row tiles, the two-step kernel with
+ * 8, 12, 16-row tiles and 4 or 6 ring slots, and the two-step kernel with two rows per warp with
+ * 12 and 16-row tiles (graphs on).  Each candidate runs trial_steps steps
  * (rounded up to a multiple of 16; <= 0: 16) after one untimed run of the same length, timed
  * with CUDA events on the context's stream.  The fields are copied aside first (one extra copy
  * of the active arrays, freed before return) and restored afterwards, so the state and
@@ -304,7 +307,8 @@ FDTD_API int fdtd_batch_step(fdtd_batch *b, int nsteps);
 FDTD_API int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t);
 
 /* fdtd_batch_autotune - fdtd_autotune for a batch over its current members: the one-step kernel
- * with 4, 8, 16-row tiles and the two-step kernel with 8, 12, 16-row tiles, each timed over
+ * with 4, 8, 16-row tiles and the two-step kernels with 8, 12, 16-row tiles (two rows per warp:
+ * 12, 16), each timed over
  * trial_steps batch steps (rounded up to a multiple of 16; <= 0: 16) after an untimed run.
  * Members' fields, step counts and the batch clock are restored afterwards.  Not cached (the
  * members change).  out / ms_per_step may be NULL.  Synchronises the batch stream. */
@@ -332,6 +336,80 @@ FDTD_API void fdtd_batch_destroy(fdtd_batch *b);
 
 /* fdtd_batch_last_error - message of the last failed batch call. */
 FDTD_API const char *fdtd_batch_last_error(const fdtd_batch *b);
+
+/* ------------------------------------------------------------------------
+ * z-slab decomposition of one cavity (domain decomposition; Sec. 6 names it among the ways FDTD is
+ * spread over many processors).  A slab context owns the cells of global planes [k0, k1) of an
+ * nx*ny*nz_global cavity and keeps `ghost` copies of its neighbours' cells on each side that has a
+ * neighbour.  Steps run the ordinary kernels on the slab alone: on a ghost side the slab's local
+ * boundary acts as a PEC wall, which is wrong there, and the error moves inwards by the reach of
+ * the differences per step (1 plane for Eq. 2, 3 for order 4).  So after the ghost cells are
+ * refreshed from the neighbours' owned cells, the owned cells stay exact for floor(ghost / reach)
+ * steps; fdtd_step returns FDTD_ERR_STATE for more.  The owned values are then bit-identical to
+ * the same cells of the undivided cavity (FP32 storage; 16-bit storage as well when every slab
+ * stores with the same scales, see fdtd_set_storage_scales).
+ * ------------------------------------------------------------------------ */
+
+/* fdtd_create_slab - the slab [k0, k1) of an nx*ny*nz_global cavity, with g_lo = (k0 > 0 ? ghost : 0)
+ * ghost cells below and g_hi = (k1 < nz_global ? ghost : 0) above.  It is a context of
+ * nz_local = k1 - k0 + g_lo + g_hi cells along z whose local plane p is global plane k0 - g_lo + p;
+ * ce / ch are host canonical arrays of those local planes (as for fdtd_create with nz = nz_local; NULL
+ * for vacuum), storage and stream as for fdtd_create.  Every other call (set/get fields, step, order,
+ * tuning) applies to the slab as to a cavity of nz_local cells.  A load leaves the ghost cells
+ * untrusted: import (or exchange) both ghost sides before the first step.  FDTD_ERR_ARG when
+ * [k0, k1) is empty or outside [0, nz_global), ghost is not in [1, 64], the ghosts would reach outside
+ * the cavity, or a slab with a neighbour owns fewer than `ghost` planes. */
+FDTD_API int fdtd_create_slab(fdtd_ctx **out, int nx, int ny, int nz_global, int k0, int k1, int ghost, double dt,
+                              double dx, const float *const ce[3], const float *const ch[3], int storage,
+                              void *cuda_stream);
+
+/* fdtd_slab_info - info[7] = {nz_global, k0, k1, g_lo, g_hi, ghost, steps the owned cells stay exact
+ * before the next exchange (INT_MAX for a slab without neighbours)}.  FDTD_ERR_STATE for a context not
+ * made by fdtd_create_slab. */
+FDTD_API int fdtd_slab_info(const fdtd_ctx *ctx, int info[7]);
+
+/* fdtd_slab_halo_bytes - bytes that fdtd_slab_export writes and fdtd_slab_import reads for one side:
+ * 6 fields x ghost planes x ny x pitch storage elements (pitch = nx rounded up to 32; 4 or 2 bytes per
+ * element).  -1 for NULL or a context that is not a slab. */
+FDTD_API long long fdtd_slab_halo_bytes(const fdtd_ctx *ctx);
+
+/* fdtd_slab_export - copy the owned boundary cells of one side (side 0: the `ghost` lowest owned planes,
+ * 1: the highest) into buf, laid out as [field Ex..Hz][plane][y][x with the padded pitch] in the storage
+ * type and scaling of the slab (fdtd_slab_halo_bytes bytes).  on_device = 1: buf is device memory and
+ * the copy is ordered on the slab's stream (asynchronous); 0: host memory, the call waits for it.  The
+ * neighbour on that side imports the buffer.  FDTD_ERR_ARG for a side that is a wall of the cavity. */
+FDTD_API int fdtd_slab_export(fdtd_ctx *ctx, int side, void *buf, int on_device);
+
+/* fdtd_slab_import - write a neighbour's export into the ghost cells of one side (0 below, 1 above) and
+ * restore that side's step allowance.  The exporting slab must have the same nx, ny, storage, ghost
+ * depth and storage scales, and its state must be at the same step.  Stream ordering as export. */
+FDTD_API int fdtd_slab_import(fdtd_ctx *ctx, int side, const void *buf, int on_device);
+
+/* fdtd_slab_exchange - both directions between two neighbouring slabs (lo's k1 == hi's k0), device to
+ * device (the same GPU, or two GPUs through unified addressing): lo's highest owned cells into hi's
+ * lower ghosts and hi's lowest owned cells into lo's upper ghosts.  The copies run on lo's stream after
+ * the work already enqueued on hi's stream, and hi's stream waits for them; no host synchronisation.
+ * FDTD_ERR_ARG for slabs that are not neighbours or differ in size, storage, ghost depth or scales. */
+FDTD_API int fdtd_slab_exchange(fdtd_ctx *lo, fdtd_ctx *hi);
+
+/* fdtd_slab_energy - the part of the energy W (as fdtd_energy, FP64) that lies in the owned cells (the far
+ * z face with the slab that has it); the energies of all slabs add up to the cavity's.  The ghost cells
+ * must be current (no step since the last exchange on both sides), else FDTD_ERR_STATE.  Synchronises. */
+FDTD_API int fdtd_slab_energy(fdtd_ctx *ctx, double *W);
+
+/* fdtd_slab_divergence_sq - the owned parts of the squared divergence norms of fdtd_divergence (sums of
+ * squares: add them over slabs, then take the square roots).  Conditions as fdtd_slab_energy. */
+FDTD_API int fdtd_slab_divergence_sq(fdtd_ctx *ctx, double *divE2, double *divH2);
+
+/* fdtd_set_storage_scales - fix the power-of-two scales s_E, s_H with which later loads store 16-bit fields
+ * (0: chosen from the loaded data, the default).  Slabs of one cavity must share them: take
+ * fdtd_storage_scale_of of the largest |E| and |H| of the whole cavity.  FDTD_ERR_ARG for a value that is
+ * neither 0 nor a power of two.  Applies from the next fdtd_set_fields; no effect with FP32 storage. */
+FDTD_API int fdtd_set_storage_scales(fdtd_ctx *ctx, double s_e, double s_h);
+
+/* fdtd_storage_scale_of - the scale a load chooses for a field whose largest magnitude is maxabs:
+ * 2^(8 - ceil(log2 maxabs)), 1 for maxabs <= 0 or not finite. */
+FDTD_API double fdtd_storage_scale_of(double maxabs);
 
 /* ------------------------------------------------------------------------
  * Diagnostics

@@ -19,7 +19,7 @@ from . import build as _build
 FDTD_F32, FDTD_F16, FDTD_BF16 = 0, 1, 2
 FDTD_OK, FDTD_ERR_ARG, FDTD_ERR_OOM, FDTD_ERR_CUDA, FDTD_ERR_TIMEOUT, FDTD_ERR_STATE, FDTD_ERR_UNSTABLE = (
     0, -1, -2, -3, -4, -5, -6)
-FDTD_KERNEL_AUTO, FDTD_KERNEL_SIMPLE, FDTD_KERNEL_FUSED, FDTD_KERNEL_TEMPORAL = 0, 1, 2, 3
+FDTD_KERNEL_AUTO, FDTD_KERNEL_SIMPLE, FDTD_KERNEL_FUSED, FDTD_KERNEL_TEMPORAL, FDTD_KERNEL_TEMPORAL2 = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT", -5: "ERR_STATE",
                 -6: "ERR_UNSTABLE"}
 
@@ -33,6 +33,9 @@ EXPORTS = (
     "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune", "fdtd_set_sources", "fdtd_set_probes",
     "fdtd_get_probes", "fdtd_set_order", "fdtd_get_order", "fdtd_batch_retune", "fdtd_prefetch_fields",
     "fdtd_set_fields_prefetched", "fdtd_debug_fail_alloc", "fdtd_debug_tile_plan",
+    "fdtd_create_slab", "fdtd_slab_info", "fdtd_slab_halo_bytes", "fdtd_slab_export", "fdtd_slab_import",
+    "fdtd_slab_exchange", "fdtd_slab_energy", "fdtd_slab_divergence_sq", "fdtd_set_storage_scales",
+    "fdtd_storage_scale_of",
 )
 
 
@@ -114,6 +117,18 @@ def lib() -> ctypes.CDLL:
             L.fdtd_batch_retune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d),
                                             ctypes.POINTER(i)]
             L.fdtd_get_order.argtypes = [vp]
+            L.fdtd_create_slab.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i, d, d, vp, vp, i, vp]
+            L.fdtd_slab_info.argtypes = [vp, vp]
+            L.fdtd_slab_halo_bytes.argtypes = [vp]
+            L.fdtd_slab_halo_bytes.restype = ll
+            L.fdtd_slab_export.argtypes = [vp, i, vp, i]
+            L.fdtd_slab_import.argtypes = [vp, i, vp, i]
+            L.fdtd_slab_exchange.argtypes = [vp, vp]
+            L.fdtd_slab_energy.argtypes = [vp, ctypes.POINTER(d)]
+            L.fdtd_slab_divergence_sq.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
+            L.fdtd_set_storage_scales.argtypes = [vp, d, d]
+            L.fdtd_storage_scale_of.argtypes = [d]
+            L.fdtd_storage_scale_of.restype = d
             _LIB = L
         return _LIB
 
@@ -170,6 +185,83 @@ def fdtd_create(nx: int, ny: int, nz: int, dt: float, dx: float = 1.0, ce=None, 
                        int(storage), _stream_handle(stream))
     _check(None, rc)
     return out.value
+
+
+def fdtd_create_slab(nx: int, ny: int, nz_global: int, k0: int, k1: int, ghost: int, dt: float, dx: float = 1.0,
+                     ce=None, ch=None, storage: int = FDTD_F32, stream=None):
+    """A z-slab [k0, k1) of an nx*ny*nz_global cavity with `ghost` cells on each side that has a neighbour;
+    ce/ch are None or canonical host arrays of the slab's local planes (k0 - g_lo .. k1 + g_hi)."""
+    L = lib()
+    g_lo = ghost if k0 > 0 else 0
+    g_hi = ghost if k1 < nz_global else 0
+    shape = (k1 - k0 + g_lo + g_hi + 1, ny + 1, nx + 1)
+    keep = []
+
+    def arr3(c):
+        if c is None:
+            return None
+        if np.isscalar(c):
+            c = [c, c, c]
+        vs = [np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float32), shape)) for v in c]
+        keep.extend(vs)
+        return _ptr_array([v.ctypes.data for v in vs])
+
+    ce_p, ch_p = arr3(ce), arr3(ch)
+    out = ctypes.c_void_p()
+    rc = L.fdtd_create_slab(ctypes.byref(out), int(nx), int(ny), int(nz_global), int(k0), int(k1), int(ghost),
+                            float(dt), float(dx),
+                            ctypes.cast(ce_p, ctypes.c_void_p) if ce_p is not None else None,
+                            ctypes.cast(ch_p, ctypes.c_void_p) if ch_p is not None else None,
+                            int(storage), _stream_handle(stream))
+    _check(None, rc)
+    return out.value
+
+
+def fdtd_slab_info(ctx) -> dict:
+    info = (ctypes.c_int * 7)()
+    _check(ctx, lib().fdtd_slab_info(ctx, info))
+    return dict(zip(("nz_global", "k0", "k1", "g_lo", "g_hi", "ghost", "steps_left"), list(info)))
+
+
+def fdtd_slab_halo_bytes(ctx) -> int:
+    return int(lib().fdtd_slab_halo_bytes(ctx))
+
+
+def fdtd_slab_export(ctx, side: int, buf) -> None:
+    """Owned boundary cells of one side into buf: a device tensor (stream-ordered) or a host numpy array."""
+    on_device = hasattr(buf, "data_ptr")
+    ptr = buf.data_ptr() if on_device else buf.ctypes.data
+    _check(ctx, lib().fdtd_slab_export(ctx, int(side), ptr, int(on_device)))
+
+
+def fdtd_slab_import(ctx, side: int, buf) -> None:
+    on_device = hasattr(buf, "data_ptr")
+    ptr = buf.data_ptr() if on_device else np.ascontiguousarray(buf).ctypes.data
+    _check(ctx, lib().fdtd_slab_import(ctx, int(side), ptr, int(on_device)))
+
+
+def fdtd_slab_exchange(lo, hi) -> None:
+    _check(lo, lib().fdtd_slab_exchange(lo, hi))
+
+
+def fdtd_slab_energy(ctx) -> float:
+    w = ctypes.c_double()
+    _check(ctx, lib().fdtd_slab_energy(ctx, ctypes.byref(w)))
+    return w.value
+
+
+def fdtd_slab_divergence_sq(ctx) -> tuple[float, float]:
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().fdtd_slab_divergence_sq(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def fdtd_set_storage_scales(ctx, s_e: float, s_h: float) -> None:
+    _check(ctx, lib().fdtd_set_storage_scales(ctx, float(s_e), float(s_h)))
+
+
+def fdtd_storage_scale_of(maxabs: float) -> float:
+    return float(lib().fdtd_storage_scale_of(float(maxabs)))
 
 
 def _field_ptrs(fields, shape, on_device: bool, writable: bool):

@@ -110,6 +110,15 @@ struct fdtd_ctx {
     long long *d_xclock = nullptr;     // device: steps taken since fdtd_set_fields (advanced by the extras launch)
     long long bytes = 0;
     fdtd_batch *batch = nullptr;
+    float fixed_scale[2] = {0.f, 0.f};      // fdtd_set_storage_scales: s_E, s_H of later loads (0: from the data)
+    // z-slab of a larger cavity (fdtd_create_slab): local planes 0..nz are global planes z_off..z_off + nz;
+    // g_lo / g_hi ghost cells lie below / above the owned cells (0 on a side that is a real PEC wall);
+    // left[side] is how many more steps the owned cells stay exact before that side needs an import
+    struct SlabInfo {
+        int on = 0, nz_global = 0, z_off = 0, g_lo = 0, g_hi = 0, ghost = 0;
+        int left[2] = {0, 0};
+        cudaEvent_t ev = nullptr;
+    } slab;
     std::string err;
 };
 
@@ -124,6 +133,7 @@ struct fdtd_batch {
         long long nlaunch;      // launches it took part in since joining (each flips its copy)
     };
     int storage = 0;
+    int order = 2;                   // spatial order of every member (set by the first member joining)
     cudaStream_t stream = nullptr;
     std::vector<Member> members;
     long long step = 0;              // step clock: steps enqueued so far (a two-step launch advances it by 2)
@@ -191,7 +201,10 @@ int ensure_stage2(fdtd_ctx *c);
 struct Shape {
     int kind;   // 0: one step per launch, 1: two steps per launch, 2: one fourth-order step
     int tile_y, stages, ctas_per_sm;
+    int rows_per_warp;   // kind 1: rows per consumer warp (1, or 2 for FDTD_KERNEL_TEMPORAL2)
 };
+// Rows per consumer warp of the two-step kernel a tuning selects.
+inline int two_step_rows(const fdtd_tuning &t) { return t.kernel == FDTD_KERNEL_TEMPORAL2 ? 2 : 1; }
 Shape resolve_shape(int storage, const fdtd_tuning &t, int kind = 0);
 int choose_zlen(long long cols, int nz, int grid, int zchunk, int prologue_planes);
 long long simulate_plan(const std::vector<int> &plan, long long cols, int G, int prologue);
@@ -202,6 +215,12 @@ void append_tiles_plan(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_of
 void append_tiles(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y, int zlen, int kind = 0);
 std::vector<TileRec> assign_tiles(const std::vector<TileRec> &v, int G, int prologue, std::vector<int> &first);
 int build_tiles(fdtd_ctx *c, int kind);
+
+// ---- z-slabs (slab.cu)
+int slab_reach(const fdtd_ctx *c);                 // planes a step's dependence reaches (order 2: 1, order 4: 3)
+void slab_after_load(fdtd_ctx *c);                 // a load leaves the ghost cells untrusted
+int slab_check_steps(fdtd_ctx *c, int nsteps);     // FDTD_ERR_STATE when the ghosts do not cover nsteps
+void slab_took_steps(fdtd_ctx *c, int nsteps);
 
 // ---- point currents and probes (extras_api.cu)
 bool extras_on(const fdtd_ctx *c);

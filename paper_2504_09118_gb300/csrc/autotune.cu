@@ -18,6 +18,8 @@ std::vector<fdtd_tuning> tune_candidates(bool batch, int order) {
             if (batch && st != 4) continue;
             v.push_back(fdtd_tuning{FDTD_KERNEL_TEMPORAL, ty, 0, 0, st, 1});
         }
+    // two rows per consumer warp, with the deepest ring that fits beside its smaller exchange planes
+    for (int ty : {12, 16}) v.push_back(fdtd_tuning{FDTD_KERNEL_TEMPORAL2, ty, 0, 0, 0, 1});
     return v;
 }
 
@@ -148,7 +150,7 @@ int fdtd_batch_autotune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double
     if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         rc = bfail(b, FDTD_ERR_CUDA, "event create");
     if (!rc)
-        for (const fdtd_tuning &t : tune_candidates(true)) {
+        for (const fdtd_tuning &t : tune_candidates(true, b->order)) {
             if ((rc = fdtd_batch_set_tuning(b, &t)) != FDTD_OK) break;
             if ((rc = fdtd_batch_step(b, n)) != FDTD_OK) break;
             cudaEventRecord(e0, b->stream);
@@ -229,7 +231,7 @@ int fdtd_batch_retune(fdtd_batch *b, int trial_steps, fdtd_tuning *out, double *
             cells += (long long)mb.c->nx * mb.c->ny * mb.c->nz;
             ++running;
         }
-    const auto key = std::make_pair(b->storage, floor_log2(cells));
+    const auto key = std::make_pair(b->storage * 8 + b->order, floor_log2(cells));
     fdtd_tuning t{};
     double ms = -1.0;
     bool hit = false;

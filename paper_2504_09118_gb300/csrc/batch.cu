@@ -53,7 +53,12 @@ int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *c) {
     if (c->storage != b->storage) return bfail(b, FDTD_ERR_ARG, "storage mismatch");
     if (c->coef_mode == COEF_FULL) return bfail(b, FDTD_ERR_ARG, "per-position coefficient arrays are not batched");
     if (extras_on(c)) return bfail(b, FDTD_ERR_ARG, "contexts with currents or probes are not batched");
-    if (c->order != 2) return bfail(b, FDTD_ERR_ARG, "fourth-order contexts are not batched");
+    if (c->slab.on) return bfail(b, FDTD_ERR_ARG, "slab contexts are not batched");
+    // one spatial order per batch (the first member's; the kernel differs): second and fourth-order
+    // members go to batches of their own
+    if (!b->members.empty() && c->order != b->order)
+        return bfail(b, FDTD_ERR_ARG, "the batch runs order %d; this context has order %d", b->order, c->order);
+    if (b->members.empty()) b->order = c->order;
     // the member's pending work (set_fields) happened-before: its stream was synchronised by that call
     b->members.push_back({c, c->cur, b->step, b->launches, LLONG_MAX, c->steps, 0});
     c->batch = b;
@@ -106,13 +111,16 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t) {
     if (!b) return FDTD_ERR_ARG;
     fdtd_tuning n{};
     if (t) n = *t;
-    if (n.kernel == FDTD_KERNEL_SIMPLE || n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL)
-        return bfail(b, FDTD_ERR_ARG, "batches use the fused kernels (FUSED or TEMPORAL)");
-    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16,
-               ty_two = n.tile_y == 8 || n.tile_y == 12 || n.tile_y == 16;
-    if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL ? ty_two
-                      : n.kernel == FDTD_KERNEL_AUTO   ? (ty_one || ty_two)
-                                                       : ty_one))
+    if (n.kernel == FDTD_KERNEL_SIMPLE || n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL2)
+        return bfail(b, FDTD_ERR_ARG, "batches use the fused kernels (FUSED, TEMPORAL or TEMPORAL2)");
+    // FUSED: 4, 8 or 16 rows (12 too for fourth-order batches; a one-step second-order batch takes its
+    // default for it)
+    const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 12 || n.tile_y == 16,
+               ty_two = n.tile_y == 8 || n.tile_y == 12 || n.tile_y == 16, ty_two2 = n.tile_y == 12 || n.tile_y == 16;
+    if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL    ? ty_two
+                      : n.kernel == FDTD_KERNEL_TEMPORAL2 ? ty_two2
+                      : n.kernel == FDTD_KERNEL_AUTO      ? (ty_one || ty_two)
+                                                          : ty_one))
         return bfail(b, FDTD_ERR_ARG, "bad tile_y");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return bfail(b, FDTD_ERR_ARG, "bad stages");
     b->tuning = n;
@@ -130,8 +138,14 @@ static void batch_free_retired_graphs(fdtd_batch *b) {   // call only when the b
     b->retired_graphs.clear();
 }
 
+// Tile kind of the batch's launches: 2 (the fused fourth-order kernel) for a fourth-order batch whatever the
+// tuning's kernel, else 1 (two steps per launch) or 0 (one step).
 static int batch_kind(const fdtd_batch *b) {
-    return b->tuning.kernel == FDTD_KERNEL_TEMPORAL || b->tuning.kernel == FDTD_KERNEL_AUTO ? 1 : 0;
+    if (b->order == 4) return 2;
+    return b->tuning.kernel == FDTD_KERNEL_TEMPORAL || b->tuning.kernel == FDTD_KERNEL_TEMPORAL2 ||
+                   b->tuning.kernel == FDTD_KERNEL_AUTO
+               ? 1
+               : 0;
 }
 
 // Rebuild the packed tile list (asynchronously on the batch stream: the upload runs after the
@@ -141,7 +155,7 @@ static int batch_rebuild(fdtd_batch *b) {
     batch_retire_graphs(b);
     const int kind = batch_kind(b);
     Shape s = resolve_shape(b->storage, b->tuning, kind);
-    const int box_y = s.tile_y + (kind == 0 ? 2 : 4);
+    const int box_y = s.tile_y + (kind == 0 ? 2 : kind == 1 ? 4 : 6);
     const int G = num_sms() * s.ctas_per_sm;
     std::vector<TileRec> tiles;
     long long total_cols_planes = 0;
@@ -150,7 +164,7 @@ static int batch_rebuild(fdtd_batch *b) {
             cudaStreamSynchronize(b->stream);   // launches in flight may still read the old maps
             break;
         }
-    const int tw = kind == 0 ? kTileX : fused2_tile_w(b->storage);
+    const int tw = kind == 1 ? fused2_tile_w(b->storage) : kTileX;
     for (auto &mb : b->members) {
         if (mb.stop <= b->step) continue;   // finished members carry no tiles
         fdtd_ctx *c = mb.c;
@@ -199,7 +213,10 @@ static int batch_launch(fdtd_batch *b, int parity, int nsteps) {
     L.stages = s.stages;
     L.grid = b->grid;
     L.launch_steps = nsteps;
-    cudaError_t e = kind == 0 ? launch_fused_step(b->storage, L, b->stream) : launch_fused2_step(b->storage, L, b->stream);
+    L.rows_per_warp = s.rows_per_warp;
+    cudaError_t e = kind == 0   ? launch_fused_step(b->storage, L, b->stream)
+                    : kind == 1 ? launch_fused2_step(b->storage, L, b->stream)
+                                : launch_fused4_step(b->storage, L, b->stream);
     if (e == cudaSuccess) e = launch_step_counter(b->d_step, nsteps, b->stream);
     if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
     return FDTD_OK;
@@ -219,7 +236,7 @@ int fdtd_batch_step(fdtd_batch *b, int nsteps) {
     if (b->members.empty() || nsteps == 0) return FDTD_OK;
     if (int rc = batch_rebuild(b)) return rc;
     const int kind = batch_kind(b);
-    const int per = kind == 0 ? 1 : 2;   // steps per launch
+    const int per = kind == 1 ? 2 : 1;   // steps per launch
     int left = nsteps;
     const int K = 16;                    // steps per graph (an even number of launches: parity unchanged)
     if (b->tuning.use_graph && b->stream != nullptr && left >= K) {

@@ -79,6 +79,9 @@ CavityDesc make_desc(const fdtd_ctx *c, int parity_off) {
         d.inv_ch[q] = 1.0f / c->ch_s[q];
     }
     d.maps = c->d_maps;
+    d.kr_lo = 0;
+    d.kr_hi = c->nz;
+    d.face_top = 1;
     return d;
 }
 
@@ -154,7 +157,8 @@ bool use_fused(const fdtd_ctx *c) {
 // order only: the fourth-order scheme has a one-step kernel)
 bool use_temporal(const fdtd_ctx *c) {
     return use_fused(c) && c->order == 2 &&
-           (c->tuning.kernel == FDTD_KERNEL_TEMPORAL || c->tuning.kernel == FDTD_KERNEL_AUTO);
+           (c->tuning.kernel == FDTD_KERNEL_TEMPORAL || c->tuning.kernel == FDTD_KERNEL_TEMPORAL2 ||
+            c->tuning.kernel == FDTD_KERNEL_AUTO);
 }
 
 // Tile kind of a context's one-step launches: 0 (Eq. 2) or 2 (fourth order).
@@ -181,6 +185,7 @@ int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind) {
     L.grid = tl.grid;
     L.inject_timeout_us = inject_us;
     L.first = tl.first;
+    L.rows_per_warp = s.rows_per_warp;
     if (kind == 0)
         CK(c, launch_fused_step(c->storage, L, c->stream));
     else if (kind == 1)
@@ -528,6 +533,7 @@ void fdtd_destroy(fdtd_ctx *c) {
         if (c->packed[b]) cudaEventDestroy(c->packed[b]);
     }
     if (c->prefetched) cudaEventDestroy(c->prefetched);
+    if (c->slab.ev) cudaEventDestroy(c->slab.ev);
     if (c->prefetch_free) cudaEventDestroy(c->prefetch_free);
     delete c;
 }
@@ -539,16 +545,20 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
     if (!c) return FDTD_ERR_ARG;
     fdtd_tuning n{};
     if (t) n = *t;
-    if (n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
-    if (n.kernel == FDTD_KERNEL_TEMPORAL && c->order != 2)
-        return fail(c, FDTD_ERR_ARG, "the two-step kernel runs the second-order scheme only");
-    // one-step kernels: 4, 8 or 16 rows (the fourth-order kernel also 12); two-step kernel: 8, 12 or 16
+    if (n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL2) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
+    const bool two_step = n.kernel == FDTD_KERNEL_TEMPORAL || n.kernel == FDTD_KERNEL_TEMPORAL2;
+    if (two_step && c->order != 2)
+        return fail(c, FDTD_ERR_ARG, "the two-step kernels run the second-order scheme only");
+    // one-step kernels: 4, 8 or 16 rows (the fourth-order kernel also 12); two-step kernel: 8, 12 or 16;
+    // two-step kernel with two rows per warp: 12 or 16
     const bool ty_one = n.tile_y == 4 || n.tile_y == 8 || n.tile_y == 16 || (c->order == 4 && n.tile_y == 12),
-               ty_two = n.tile_y == 8 || n.tile_y == 12 || n.tile_y == 16;
-    if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL ? ty_two
-                      : n.kernel == FDTD_KERNEL_AUTO   ? (ty_one || ty_two)
-                                                       : ty_one))
-        return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (fourth order: also 12; two-step kernel: 8, 12 or 16)");
+               ty_two = n.tile_y == 8 || n.tile_y == 12 || n.tile_y == 16, ty_two2 = n.tile_y == 12 || n.tile_y == 16;
+    if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL    ? ty_two
+                      : n.kernel == FDTD_KERNEL_TEMPORAL2 ? ty_two2
+                      : n.kernel == FDTD_KERNEL_AUTO      ? (ty_one || ty_two)
+                                                          : ty_one))
+        return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (fourth order: also 12; two-step kernel: 8, 12 or 16; "
+                                     "two-step kernel with two rows per warp: 12 or 16)");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return fail(c, FDTD_ERR_ARG, "stages must be in [3, 8]");
     if (n.stages == 3 && c->order == 4) return fail(c, FDTD_ERR_ARG, "the fourth-order kernel needs stages >= 4");
     if (n.zchunk < 0 || n.ctas_per_sm < 0) return fail(c, FDTD_ERR_ARG, "negative tuning value");
@@ -568,13 +578,14 @@ int fdtd_set_order(fdtd_ctx *c, int order) {
     if (c->courant * gain * gain > 1.0 + 1e-6)
         return fail(c, FDTD_ERR_UNSTABLE, "Courant bound of order %d violated: max sqrt(3 ce ch) * %.4f = %.6f > 1",
                     order, gain, std::sqrt(c->courant) * gain);
-    if (order == 4 && c->tuning.kernel == FDTD_KERNEL_TEMPORAL)
-        return fail(c, FDTD_ERR_ARG, "the two-step kernel runs the second-order scheme only; retune first");
+    if (order == 4 && (c->tuning.kernel == FDTD_KERNEL_TEMPORAL || c->tuning.kernel == FDTD_KERNEL_TEMPORAL2))
+        return fail(c, FDTD_ERR_ARG, "the two-step kernels run the second-order scheme only; retune first");
     if (order == 4 && c->tuning.stages == 3)
         return fail(c, FDTD_ERR_ARG, "the fourth-order kernel needs stages >= 4; retune first");
     cudaStreamSynchronize(c->stream);   // no graph of this context may still be running
     drop_graphs(c->graphs);
     c->order = order;
+    slab_after_load(c);   // the ghost depth a step needs changed with the reach of the differences
     return FDTD_OK;
 }
 
@@ -612,7 +623,8 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
                 if (!std::isfinite(m)) return fail(c, FDTD_ERR_ARG, "field %d holds a non-finite value", q);
                 mx = std::max(mx, m);
             }
-            const float sc = mx > 0.f ? std::ldexp(1.0f, 8 - (int)std::ceil(std::log2((double)mx))) : 1.0f;
+            float sc = mx > 0.f ? std::ldexp(1.0f, 8 - (int)std::ceil(std::log2((double)mx))) : 1.0f;
+            if (c->fixed_scale[g] > 0.f) sc = c->fixed_scale[g];   // fdtd_set_storage_scales
             for (int q = 3 * g; q < 3 * g + 3; ++q) c->scale[q] = sc;
         }
         if (c->table_fused) {
@@ -660,6 +672,7 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
     c->cur = 0;
     c->steps = 0;
     c->has_fields = true;
+    slab_after_load(c);
     return check_status(c, c->d_status, c->stream);
 }
 
@@ -728,6 +741,7 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
     if (!c->has_fields) return fail(c, FDTD_ERR_STATE, "fdtd_set_fields has not been called");
     if (c->batch) return fail(c, FDTD_ERR_STATE, "context is a batch member; step the batch");
     if (nsteps == 0) return FDTD_OK;
+    if (int rc = slab_check_steps(c, nsteps)) return rc;
     const bool fused = use_fused(c);
     const bool extras = extras_on(c);
     // currents enter between the E update of one step and the H update of the next: one step per launch
@@ -790,6 +804,7 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
         if (fused) c->cur ^= 1;
         ++c->steps;
     }
+    slab_took_steps(c, nsteps);
     return FDTD_OK;
 }
 

@@ -6,8 +6,8 @@
 // is written to HBM (copy 1-s), so a step costs half the DRAM bytes of the one-step
 // kernel at the price of recomputing a wider halo.
 //
-// Tile: W = 64 - HX output columns (60 FP32, 56 16-bit: keeps the TMA x origin x0 - HX
-// on a 16-byte boundary) x TY output rows, over planes [kz0, kz1).  Consumer warps
+// Tile: W = 60 output columns x TY output rows, over planes [kz0, kz1); the TMA box starts at
+// x0 - 2 rounded down to the 16-byte granule (Geom2::box_x).  Consumer warps
 // r = 0..TY+2 own rows y = y0 - 2 + r; each lane owns the two cells x0 - 2 + 2 lane,
 // +1, so the lanes cover [x0 - 2, x0 + 62) at both levels:
 //   level 1  H1 rows y0-2 .. y0+TY,   E1 rows y0-1 .. y0+TY    (from units k, k+1)
@@ -36,9 +36,13 @@ constexpr int NTR2 = 8;
 constexpr uint64_t kWaitLimitNs2 = 2000000000ull;
 
 template <typename T> struct Geom2 {
-    static constexpr int HX = 16 / (int)sizeof(T);   // 4 (FP32) or 8 (16-bit)
-    static constexpr int W = 64 - HX;                 // output columns per tile
-    static constexpr int BX = 64 + 2 * HX;            // field box width
+    static constexpr int HX = 16 / (int)sizeof(T);   // 4 (FP32) or 8 (16-bit): elements per 16-byte TMA granule
+    static constexpr int W = 60;                      // output columns per tile
+    static constexpr int BX = 64 + 2 * HX;            // field box width (covers the lanes' cells from any origin shift)
+    // The box starts at the lane cells' first column x0 - 2 rounded down to the 16-byte granule, so that every
+    // tile origin (a multiple of 60) gives a legal TMA x coordinate; a lane's box column is shifted by the
+    // remainder (2 for FP32, 0..6 for 16-bit storage).
+    __host__ __device__ static constexpr int box_x(int x0) { return (x0 - 2) & ~(HX - 1); }
     static constexpr int IBX = 80;                    // id box width (bytes)
 };
 
@@ -80,7 +84,7 @@ template <int TY> __host__ __device__ constexpr int threads2() { return (TY + 4)
 template <typename T, int TY, bool BATCH>
 __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fused2Params P) {
     using G = Geom2<T>;
-    constexpr int HX = G::HX, BX = G::BX, W = G::W;
+    constexpr int BX = G::BX, W = G::W;
     constexpr int FB = box_bytes<T, TY>(), FS = box_stride<T, TY>(), FE = FS / (int)sizeof(T);
     static_assert(FS == FB, "field boxes must be whole 128-byte blocks: one 4-D load writes them back to back");
     constexpr int NCW = TY + 3, NCT = NCW * 32;
@@ -124,6 +128,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
 
     // =========================================================== producer warp
     if (warp == NCW) {
+#if FDTD_TMA_EVICT_LAST
+        const uint64_t l2_keep = l2_policy_evict_last();   // unit loads stay in L2 for the neighbouring tiles
+#endif
         int issued = 0, m = 0, s = 0;
         uint32_t rnd = 0;
         bool ok = true;
@@ -157,12 +164,17 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                     const bool has_id = rec->mode == COEF_ID8;
                     unsigned char *dst = slots + s * SB;
                     fence_proxy_async_smem();
-                    if (tma_x_ok(P.status, rec->x0 - HX, (int)sizeof(T)) &&
+                    if (tma_x_ok(P.status, G::box_x(rec->x0), (int)sizeof(T)) &&
                         (!has_id || tma_x_ok(P.status, rec->id_x0, 1))) {
                         mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? idbox_bytes<TY>() : 0));
                         // the six field boxes in one load: a 4-D box (x, y, plane, field) lands as six
                         // consecutive FB-byte boxes (FS == FB)
-                        tma_load_4d(dst, rec->maps + src_copy * 6, rec->x0 - HX, rec->y0 - 2, kk, 0, &full[s]);
+#if FDTD_TMA_EVICT_LAST
+                        tma_load_4d_hint(dst, rec->maps + src_copy * 6, G::box_x(rec->x0), rec->y0 - 2, kk, 0, &full[s],
+                                         l2_keep);
+#else
+                        tma_load_4d(dst, rec->maps + src_copy * 6, G::box_x(rec->x0), rec->y0 - 2, kk, 0, &full[s]);
+#endif
                         if (has_id)
                             tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
                     } else {
@@ -188,7 +200,6 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
 
     // =========================================================== consumer warps
     const int r = warp;                      // row warp: y = y0 - 2 + r
-    const int bx = HX - 2 + 2 * lane;        // box column of the lane's first cell
     const int by = r;                        // box row
     const int pc = 2 * lane + 2;             // shared plane column of the first cell
     const int pr = r + 1;                    // shared plane row
@@ -209,6 +220,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         }
         const TileRec *rec = &recs[m++ % NTR2];
         const int x0 = rec->x0, y0 = rec->y0, kz0 = rec->kz0, kz1 = rec->kz1;
+        const int bx = (x0 - 2) - G::box_x(x0) + 2 * lane;   // box column of the lane's first cell
         const int nx = rec->nx, ny = rec->ny, nz = rec->nz;
         const long long pitch = rec->pitch, plane = rec->plane;
         const bool id_mode = rec->mode == COEF_ID8;
@@ -473,6 +485,7 @@ cudaError_t fused2_occupancy(int storage, int tile_y, int stages, int *ctas_per_
 }
 
 cudaError_t launch_fused2_step(int storage, const FusedLaunch &L, cudaStream_t s) {
+    if (L.rows_per_warp == 2) return launch_fused2r_step(storage, L, s);
     if (L.ntiles <= 0) return cudaSuccess;
     if (L.stages < 3 || L.stages > 8) return cudaErrorInvalidValue;
     cudaError_t e = cudaErrorInvalidValue;

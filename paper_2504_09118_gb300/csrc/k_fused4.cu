@@ -54,6 +54,7 @@ template <typename T> struct Geom4 {
 
 struct Fused4Params {
     const TileRec *recs;
+    const long long *step;   // batch step clock compared with TileRec::stop (NULL: a single cavity)
     int ntiles;
     int parity;
     int *status;
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = P.stages, SB = P.slot_bytes;
+    const long long clock = P.step ? *P.step : 0;   // batch step clock: finished members' tiles are skipped
     const int t_begin = P.first ? __ldg(P.first + blockIdx.x) : (int)blockIdx.x;
     const int t_end = P.first ? __ldg(P.first + blockIdx.x + 1) : P.ntiles;
     const int t_step = P.first ? 1 : (int)gridDim.x;
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
         uint32_t rnd = 0;
         bool ok = true;
         for (int t = t_begin; t < t_end && ok; t += t_step) {
+            if (__ldg(&P.recs[t].stop) <= clock) continue;   // member already took its last step
             TileRec *rec = &recs[m++ % NTR4];
             int u0 = 0, u1 = 0;   // planes of the tile's first and last unit
             for (int u = 0;; ++u) {
@@ -222,6 +225,7 @@ __global__ void __launch_bounds__(block_threads4<TY>(), (TY <= 4 ? 2 : 1)) fused
     };
 
     for (int t = t_begin; t < t_end; t += t_step) {
+        if (__ldg(&P.recs[t].stop) <= clock) continue;   // same skip rule as the producer
         // ---------------- tile start: record, table, prologue units P0-1 .. P0+1 (E z-taps)
         const T *u_a = wait_next();
         if (bar_sync_or(2, NCT, u_a == nullptr || *abort_flag != 0)) {
@@ -489,6 +493,7 @@ cudaError_t launch4_typed(const FusedLaunch &L, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     Fused4Params P;
     P.recs = L.recs;
+    P.step = L.step;
     P.ntiles = L.ntiles;
     P.parity = L.parity;
     P.status = L.status;

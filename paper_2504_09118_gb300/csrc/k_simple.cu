@@ -5,6 +5,7 @@
 // then curl E components), each updating one copy of the fields in place; it
 // is the debugging baseline of the fused kernel and the path for coefficient
 // sets too varied for a one-byte material id (COEF_FULL).
+#include "df.cuh"
 #include "launch.h"
 
 namespace fdtd {
@@ -136,38 +137,41 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
-// Reciprocal coefficients in FP64 for the reductions: 1/ce (c = 0..2) and 1/ch (c = 3..5).
-// Material-id mode keeps a table of them in shared memory (filled by the block before use), scalar
-// mode six registers; per-position arrays divide per cell (that mode is rare and slow anyway).
-struct InvCoef64 {
+// Reciprocal coefficients of the reductions as pairs (df.cuh): 1/ce (c = 0..2) and 1/ch (c = 3..5).
+// Material-id mode keeps them in a shared table (filled by the block before use), scalar mode in six
+// registers; per-position arrays take the reciprocal per cell (that mode is rare and slow anyway).
+struct InvCoefDF {
     const CavityDesc *d;
-    const double *tab;   // shared, 6 per id (COEF_ID8)
-    double sc[6];        // COEF_SCALAR
-    __device__ __forceinline__ double operator()(int c, long long o, int m) const {
+    const df::F2 *tab;   // shared, 6 per id (COEF_ID8)
+    df::F2 sc[6];        // COEF_SCALAR
+    __device__ __forceinline__ df::F2 operator()(int c, long long o, int m) const {
         if (d->coef_mode == COEF_ID8) return tab[6 * m + c];
         if (d->coef_mode == COEF_SCALAR) return sc[c];
-        return 1.0 / (double)d->coef[c][o];
+        return df::recip(d->coef[c][o]);
     }
 };
 
-// Fills tab (6 * ntab doubles, shared) and the scalar reciprocals; call with the whole block, then sync.
-__device__ __forceinline__ InvCoef64 make_inv_coef64(const CavityDesc &d, double *tab) {
-    InvCoef64 r;
+// Fills tab (6 * ntab pairs, shared) and the scalar reciprocals; call with the whole block, then sync.
+__device__ __forceinline__ InvCoefDF make_inv_coef_df(const CavityDesc &d, df::F2 *tab) {
+    InvCoefDF r;
     r.d = &d;
     r.tab = tab;
     for (int c = 0; c < 3; ++c) {
-        r.sc[c] = 1.0 / (double)d.ce[c];
-        r.sc[3 + c] = 1.0 / (double)d.ch[c];
+        r.sc[c] = df::recip(d.ce[c]);
+        r.sc[3 + c] = df::recip(d.ch[c]);
     }
     if (d.coef_mode == COEF_ID8)
         for (int e = threadIdx.x; e < 6 * d.ntab; e += blockDim.x) {
             const int m = e / 6, c = e % 6;
-            tab[e] = 1.0 / (double)d.table[8 * m + (c < 3 ? c : c + 1)];
+            tab[e] = df::recip(d.table[8 * m + (c < 3 ? c : c + 1)]);
         }
     return r;
 }
 
-// 1/ch in FP64 at far-face entry fi of face array c.
+// 1/ch at far-face entry fi of face array c, as a pair and in FP64.
+__device__ __forceinline__ df::F2 face_inv_ch_df(const CavityDesc &d, int c, long long fi) {
+    return df::recip(d.coef_mode == COEF_SCALAR ? d.ch[c] : d.face_ch[c][fi]);
+}
 __device__ __forceinline__ double face_inv_ch64(const CavityDesc &d, int c, long long fi) {
     return d.coef_mode == COEF_SCALAR ? 1.0 / (double)d.ch[c] : 1.0 / (double)d.face_ch[c][fi];
 }
@@ -175,67 +179,88 @@ __device__ __forceinline__ double face_inv_ch64(const CavityDesc &d, int c, long
 // Per block, in a fixed order (warps over rows, lanes along x; far-face H appended):
 //   WHAT == 0: energy sum  E^2/ce + H^2/ch - H curl E   (W without the 1/2 dt/dx factor)
 //   WHAT == 1: sum of divE^2 over interior nodes and of divH^2 over cells.
-// Every term is formed in FP64 from the stored values (converted exactly to double: the curl
-// differences of two stored values are then exact, the reciprocal coefficients are FP64) and summed
-// in FP64, per lane and then per block in a fixed order, so the result is deterministic.
+// Every term is formed from the stored values with error-free FP32 transformations (the curl
+// differences as exact pairs, the reciprocal coefficients as pairs; df.cuh) and a lane accumulates
+// its cells of a row with Dot2, about 2^-48 relative; the row sums are added in FP64, then per block
+// and over blocks in a fixed order, so the result is deterministic.  (GB300's FP64 rate made the same
+// sums in FP64 eight times slower at 512^3.)
 template <typename T, int WHAT>
 __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const CavityDesc d, int copy, double *partial) {
     __shared__ double sh[kRedThreads / 32];
-    __shared__ double itab[6 * kMaxTable];
-    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    __shared__ df::F2 itab[6 * kMaxTable];
+    const int nx = d.nx, ny = d.ny;
     const long long P = d.pitch, Z = d.plane;
     double s0 = 0.0, s1 = 0.0;
     const bool ids = d.coef_mode == COEF_ID8;
-    const InvCoef64 IC = make_inv_coef64(d, itab);
+    const InvCoefDF IC = make_inv_coef_df(d, itab);
     __syncthreads();
-    auto F = [&](int f, long long o) -> double { return (double)ld_field<T>(d, copy, f, o); };
-    auto ICo = [&](int c, long long o) -> double { return IC(c, o, ids ? d.id[o] : 0); };
+    const int nz = d.nz;
+    auto F = [&](int f, long long o) -> float { return ld_field<T>(d, copy, f, o); };
+    auto ICo = [&](int c, long long o) -> df::F2 { return IC(c, o, ids ? d.id[o] : 0); };
     // one warp per (j, k) row, lanes along x: coalesced loads
     const int lane = threadIdx.x & 31;
-    const long long nrows = (long long)ny * nz;
+    // rows of the planes [kr_lo, kr_hi) (the owned cells of a z-slab; every plane otherwise)
+    const long long nrows = (long long)ny * (d.kr_hi - d.kr_lo);
     const long long nwarps = ((long long)gridDim.x * kRedThreads) >> 5;
     for (long long r = ((long long)blockIdx.x * kRedThreads + threadIdx.x) >> 5; r < nrows; r += nwarps) {
-        const int j = (int)(r % ny), k = (int)(r / ny);
+        const int j = (int)(r % ny), k = d.kr_lo + (int)(r / ny);
+        df::Acc a0, a1;
         for (int i = lane; i < nx; i += 32) {
             const long long o = (long long)k * Z + (long long)j * P + i;
-            const double ex = F(0, o), ey = F(1, o), ez = F(2, o), hx = F(3, o), hy = F(4, o), hz = F(5, o);
+            const float ex = F(0, o), ey = F(1, o), ez = F(2, o), hx = F(3, o), hy = F(4, o), hz = F(5, o);
             const int m = ids ? d.id[o] : 0;
             if (WHAT == 0) {
-                const double ex_j1 = j + 1 < ny ? F(0, o + P) : 0.0, ex_k1 = k + 1 < nz ? F(0, o + Z) : 0.0;
-                const double ey_i1 = i + 1 < nx ? F(1, o + 1) : 0.0, ey_k1 = k + 1 < nz ? F(1, o + Z) : 0.0;
-                const double ez_i1 = i + 1 < nx ? F(2, o + 1) : 0.0, ez_j1 = j + 1 < ny ? F(2, o + P) : 0.0;
-                const double cx = (ez_j1 - ez) - (ey_k1 - ey);
-                const double cy = (ex_k1 - ex) - (ez_i1 - ez);
-                const double cz = (ey_i1 - ey) - (ex_j1 - ex);
-                const double e = ex * ex * IC(0, o, m) + ey * ey * IC(1, o, m) + ez * ez * IC(2, o, m);
-                const double h = hx * (hx * IC(3, o, m) - cx) + hy * (hy * IC(4, o, m) - cy) +
-                                 hz * (hz * IC(5, o, m) - cz);
-                s0 += e + h;
+                const float ex_j1 = j + 1 < ny ? F(0, o + P) : 0.f, ex_k1 = k + 1 < nz ? F(0, o + Z) : 0.f;
+                const float ey_i1 = i + 1 < nx ? F(1, o + 1) : 0.f, ey_k1 = k + 1 < nz ? F(1, o + Z) : 0.f;
+                const float ez_i1 = i + 1 < nx ? F(2, o + 1) : 0.f, ez_j1 = j + 1 < ny ? F(2, o + P) : 0.f;
+                a0.sq_times(ex, IC(0, o, m));
+                a0.sq_times(ey, IC(1, o, m));
+                a0.sq_times(ez, IC(2, o, m));
+                a0.sq_times(hx, IC(3, o, m));
+                a0.prod(-hx, df::diff2(ez_j1, ez, ey_k1, ey));
+                a0.sq_times(hy, IC(4, o, m));
+                a0.prod(-hy, df::diff2(ex_k1, ex, ez_i1, ez));
+                a0.sq_times(hz, IC(5, o, m));
+                a0.prod(-hz, df::diff2(ey_i1, ey, ex_j1, ex));
             } else {
                 if (i >= 1 && j >= 1 && k >= 1) {
-                    const double de = (ex * IC(0, o, m) - F(0, o - 1) * ICo(0, o - 1)) +
-                                      (ey * IC(1, o, m) - F(1, o - P) * ICo(1, o - P)) +
-                                      (ez * IC(2, o, m) - F(2, o - Z) * ICo(2, o - Z));
-                    s0 += de * de;
+                    df::Acc de;   // sum over c of D_c(node) - D_c(node - e_c), D = E / ce
+                    de.prod(ex, IC(0, o, m));
+                    de.prod(-F(0, o - 1), ICo(0, o - 1));
+                    de.prod(ey, IC(1, o, m));
+                    de.prod(-F(1, o - P), ICo(1, o - P));
+                    de.prod(ez, IC(2, o, m));
+                    de.prod(-F(2, o - Z), ICo(2, o - Z));
+                    a0.square(de.pair());
                 }
+                df::Acc dh;   // sum over c of B_c(cell + e_c) - B_c(cell), B = H / ch
                 const long long fx = (long long)k * ny + j, fy = (long long)k * nx + i, fz = (long long)j * nx + i;
-                const double bx1 = i + 1 < nx ? F(3, o + 1) * ICo(3, o + 1) : d.face[0][fx] * face_inv_ch64(d, 0, fx);
-                const double by1 = j + 1 < ny ? F(4, o + P) * ICo(4, o + P) : d.face[1][fy] * face_inv_ch64(d, 1, fy);
-                const double bz1 = k + 1 < nz ? F(5, o + Z) * ICo(5, o + Z) : d.face[2][fz] * face_inv_ch64(d, 2, fz);
-                const double dh = (bx1 - hx * IC(3, o, m)) + (by1 - hy * IC(4, o, m)) + (bz1 - hz * IC(5, o, m));
-                s1 += dh * dh;
+                if (i + 1 < nx) dh.prod(F(3, o + 1), ICo(3, o + 1));
+                else dh.prod(d.face[0][fx], face_inv_ch_df(d, 0, fx));
+                if (j + 1 < ny) dh.prod(F(4, o + P), ICo(4, o + P));
+                else dh.prod(d.face[1][fy], face_inv_ch_df(d, 1, fy));
+                if (k + 1 < nz) dh.prod(F(5, o + Z), ICo(5, o + Z));
+                else dh.prod(d.face[2][fz], face_inv_ch_df(d, 2, fz));
+                dh.prod(-hx, IC(3, o, m));
+                dh.prod(-hy, IC(4, o, m));
+                dh.prod(-hz, IC(5, o, m));
+                a1.square(dh.pair());
             }
         }
+        s0 += a0.take();
+        s1 += a1.take();
     }
     if (WHAT == 0) {
-        // constant far-face normal H: curl E vanishes there, so its energy term is H^2/ch
-        const long long nfx = (long long)ny * nz, nfy = (long long)nx * nz, nfz = (long long)nx * ny;
+        // constant far-face normal H: curl E vanishes there, so its energy term is H^2/ch (the x and y
+        // faces over the summed planes, the z face when the range reaches it); few terms: FP64
+        const int nk = d.kr_hi - d.kr_lo;
+        const long long nfx = (long long)ny * nk, nfy = (long long)nx * nk, nfz = d.face_top ? (long long)nx * ny : 0;
         for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < nfx + nfy + nfz;
              n += (long long)gridDim.x * kRedThreads) {
             int c;
             long long fi;
-            if (n < nfx) { c = 0; fi = n; }
-            else if (n < nfx + nfy) { c = 1; fi = n - nfx; }
+            if (n < nfx) { c = 0; fi = n + (long long)d.kr_lo * ny; }
+            else if (n < nfx + nfy) { c = 1; fi = n - nfx + (long long)d.kr_lo * nx; }
             else { c = 2; fi = n - nfx - nfy; }
             const double h = d.face[c][fi];
             s0 += h * h * face_inv_ch64(d, c, fi);

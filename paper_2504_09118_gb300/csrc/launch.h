@@ -40,6 +40,7 @@ struct FusedLaunch {
     const int *first;          // device, grid + 1 entries: CTA b takes tiles [first[b], first[b+1]) in order
                                // (NULL: CTA b takes tiles b, b + grid, b + 2 grid, ...)
     int launch_steps;          // two-step kernel: 2, or 1 (every tile stores its level-1 result only)
+    int rows_per_warp;         // two-step kernel: 1 (k_fused2.cu) or 2 (k_fused2r.cu); 0 means 1
 };
 // Shared memory bytes and max co-resident CTAs per SM for a fused configuration.
 int fused_smem_bytes(int storage, int tile_y, int stages);
@@ -69,6 +70,11 @@ int fused2_tile_w(int storage);
 int fused2_smem_bytes(int storage, int tile_y, int stages);
 cudaError_t fused2_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
 cudaError_t launch_fused2_step(int storage, const FusedLaunch &L, cudaStream_t s);
+// The two-step kernel with two rows per consumer warp (k_fused2r.cu; tile heights 12 and 16): the same
+// tiles, boxes and results, a different split of the rows over the warps.
+int fused2r_smem_bytes(int storage, int tile_y, int stages);
+cudaError_t fused2r_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
+cudaError_t launch_fused2r_step(int storage, const FusedLaunch &L, cudaStream_t s);
 // Fused fourth-order kernel (k_fused4.cu): shared memory, occupancy, launch (stages 4..8).
 int fused4_smem_bytes(int storage, int tile_y, int stages);
 cudaError_t fused4_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);

@@ -11,10 +11,14 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind) {
     static std::map<int, int> occ_cache;   // (kind, storage, tile_y, stages) -> max CTAs per SM
     Shape s;
     s.kind = kind;
+    s.rows_per_warp = kind == 1 ? two_step_rows(t) : 1;
+    const bool rows2 = s.rows_per_warp == 2;
     if (kind == 2)
         s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 12 || t.tile_y == 16) ? t.tile_y : 12;
     else if (kind == 0)
         s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 16) ? t.tile_y : 8;
+    else if (rows2)
+        s.tile_y = (t.tile_y == 12 || t.tile_y == 16) ? t.tile_y : 16;
     else
         s.tile_y = (t.tile_y == 8 || t.tile_y == 12 || t.tile_y == 16) ? t.tile_y : 16;
     const int min_st = kind == 2 ? 4 : 3;
@@ -22,12 +26,12 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind) {
     // the deepest ring that fits, which measured best for each of its tile heights
     s.stages = (t.stages >= min_st && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : kind == 1 ? 6 : 8);
     auto smem = [&](int st) {
-        return kind == 0 ? fused_smem_bytes(storage, s.tile_y, st)
-               : kind == 1 ? fused2_smem_bytes(storage, s.tile_y, st)
+        return kind == 0   ? fused_smem_bytes(storage, s.tile_y, st)
+               : kind == 1 ? (rows2 ? fused2r_smem_bytes(storage, s.tile_y, st) : fused2_smem_bytes(storage, s.tile_y, st))
                            : fused4_smem_bytes(storage, s.tile_y, st);
     };
     while (s.stages > min_st && smem(s.stages) > 227 * 1024) --s.stages;
-    const int key = ((kind * 4 + storage) * 64 + s.tile_y) * 16 + s.stages;
+    const int key = (((kind * 4 + storage) * 64 + s.tile_y) * 16 + s.stages) * 4 + s.rows_per_warp;
     int occ = 0;
     {
         std::lock_guard<std::mutex> g(mu);
@@ -36,7 +40,8 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind) {
             occ = it->second;
         } else {
             cudaError_t e = kind == 0   ? fused_occupancy(storage, s.tile_y, s.stages, &occ)
-                            : kind == 1 ? fused2_occupancy(storage, s.tile_y, s.stages, &occ)
+                            : kind == 1 ? (rows2 ? fused2r_occupancy(storage, s.tile_y, s.stages, &occ)
+                                                 : fused2_occupancy(storage, s.tile_y, s.stages, &occ))
                                         : fused4_occupancy(storage, s.tile_y, s.stages, &occ);
             if (e != cudaSuccess || occ < 1) occ = 1;
             occ_cache[key] = occ;

@@ -20,8 +20,8 @@ def _case(seed):
     steps = int(rng.integers(1, 14))
     coef = str(rng.choice(["vacuum", "spheres", "table"]))
     if order == 2:
-        kernel = int(rng.choice([2, 3]))
-        tile_y = int(rng.choice([4, 8, 16] if kernel == 2 else [8, 12, 16]))
+        kernel = int(rng.choice([2, 3, 4]))
+        tile_y = int(rng.choice({2: [4, 8, 16], 3: [8, 12, 16], 4: [12, 16]}[kernel]))
         stages = int(rng.integers(3, 9))
     else:
         kernel = 2
@@ -76,7 +76,7 @@ def test_16bit_fused_tilings_agree(seed):
     storage = 1 + seed % 2
     ce, ch = _coefs(coef, dims, 5000 + seed)
     f = ci.random_fields(6000 + seed, *dims)
-    base = dict(kernel=tuning["kernel"], tile_y=8, use_graph=tuning["use_graph"])
+    base = dict(kernel=tuning["kernel"], tile_y=12 if tuning["kernel"] == 4 else 8, use_graph=tuning["use_graph"])
     out = []
     for t in (base, tuning):
         with Cavity(*dims, DT, 1.0, ce, ch, storage, order=order) as cav:

@@ -212,12 +212,19 @@ def test_api_rules():
         with pytest.raises(FdtdError):
             cav.tune(kernel=2, stages=3)
         cav.set_fields(f)
+        other = Cavity(*dims, DT, 1.0)
+        other.set_fields(f)
         b = binding.fdtd_batch_create(0)
         try:
-            with pytest.raises(FdtdError):
+            binding.fdtd_batch_add(b, other.handle)     # a second-order batch
+            with pytest.raises(FdtdError):               # takes no fourth-order member
                 binding.fdtd_batch_add(b, cav.handle)
+            with pytest.raises(FdtdError):               # and its members keep their order
+                binding.fdtd_set_order(other.handle, 4)
+            binding.fdtd_batch_remove(b, other.handle)
         finally:
             binding.fdtd_batch_destroy(b)
+            other.close()
         # back to Eq. 2: the step is the second-order oracle's again
         binding.fdtd_set_order(cav.handle, 2)
         cav.step(5)

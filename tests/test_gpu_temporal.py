@@ -52,7 +52,7 @@ def assert_bitwise(a, b):
         assert bad.size == 0, (ci.COMPONENTS[n], len(bad), bad[:6].tolist(), float(np.max(np.abs(x - y))))
 
 
-# x extents around the two-step kernel's tile edges (60 cells per tile in FP32)
+# x extents around the two-step kernel's tile edges (60 cells per tile)
 @pytest.mark.parametrize("dims", [(4, 4, 4), (7, 9, 11), (130, 67, 45), (1, 3, 2), (64, 8, 3), (61, 13, 1),
                                   (121, 40, 33), (60, 12, 2), (120, 10, 6), (181, 17, 9), (2, 70, 5)])
 @pytest.mark.parametrize("mat", ["vacuum", "spheres", "few"])
@@ -132,7 +132,7 @@ def test_two_step_16bit_vs_oracle(storage):
 
 
 @pytest.mark.parametrize("storage", [1, 2])
-@pytest.mark.parametrize("dims", [(67, 29, 18), (113, 21, 9), (168, 11, 7)])   # 16-bit x tiles: 56 cells
+@pytest.mark.parametrize("dims", [(67, 29, 18), (113, 21, 9), (168, 11, 7)])   # around the 60-cell x tiles
 def test_two_step_16bit_independent_of_tiling(storage, dims):
     f = ci.random_fields(6, *dims)
     a, *_ = run_gpu(f, dims, steps=12, storage=storage, tuning={"kernel": 3, "tile_y": 8})
