@@ -54,6 +54,9 @@ WORKLOADS = {
     "serve": dict(kind="serve", rate=200.0, seed=6, budget_gb=120),
     # error study: 384^3 spheres, 1000 steps, FP32 / FP16 / BF16 storage against the FP64 oracle
     "precision": dict(kind="precision", n=(384, 384, 384), steps=1000, sphere_seed=3, field_seed=4, spheres=32),
+    # the single512 cavity as 4 z-slabs on this GPU: two ghost planes per side, one two-step launch per exchange
+    "slab512": dict(kind="slab", n=(512, 512, 512), steps=200, storage=0, sphere_seed=1, field_seed=2, spheres=32,
+                    nslabs=4, ghost=2),
     # the fourth-order (2,4) scheme on the single512 cavity (fused fourth-order kernel, one step per launch)
     "order4_512": dict(n=(512, 512, 512), steps=200, storage=0, sphere_seed=1, field_seed=2, spheres=32, order=4,
                        tuning=dict(kernel=2, tile_y=12, stages=5, zchunk=0, ctas_per_sm=0, use_graph=1)),
@@ -79,8 +82,8 @@ NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e nominal bandwidth (context beside the m
 # SHA-256 of the kernel source and the device headers it includes, as measured; ignored (reported null)
 # once any of them changes.
 MEASURED_TRAFFIC = {
-    # ncu, 512^3 bench configuration, mean of three launches of the two-step kernel
-    ("single512", "fa00a1b7df30a467"): 7.10e9,
+    # ncu, 512^3 bench configuration, mean of three launches of the two-step kernel (6.83 / 7.01 / 6.98 GB)
+    ("single512", "da8f9336c28260b3"): 6.94e9,
 }
 
 
@@ -474,6 +477,58 @@ def run_precision(args, w):
                              "per field)"}
 
 
+def run_slab(args, w):
+    """The single-cavity workload split into z-slabs on this GPU (slab contexts on their own streams,
+    device-to-device ghost exchanges between neighbours): Gcell-updates/s of the whole cavity, against the
+    same cavity undivided in the same run.  Returns the leg's results."""
+    import torch
+    from paper_2504_09118_gb300 import Cavity
+    from paper_2504_09118_gb300.slab import SlabDomain
+    torch.cuda.set_device(0)
+    nx, ny, nz = w["n"]
+    cells, per = nx * ny * nz, w["steps"]
+    ce, ch = sphere_coefs(w)
+    f = ci.random_fields(w["field_seed"], nx, ny, nz)
+    tuning = tuning_of(w)
+    streams = [torch.cuda.Stream() for _ in range(w["nslabs"])]
+    out = {}
+    with SlabDomain(nx, ny, nz, ci.COURANT_HALF_DT, 1.0, ce, ch, w["storage"], w["nslabs"], w["ghost"], 2,
+                    tuning, streams) as dom:
+        dom.set_fields(f)
+        for _ in range(args.warmup):
+            dom.step(per)
+        torch.cuda.synchronize()
+        with ClockSampler(0, None) as clk:
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                dom.step(per)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        w_slab = dom.energy()
+        out["slabs"] = {"value": round(cells * per * args.steps / dt / 1e9, 3), "clocks": clk.summary(),
+                        "ms_per_step": round(1e3 * dt / args.steps, 3), "energy": w_slab}
+    with Cavity(nx, ny, nz, ci.COURANT_HALF_DT, 1.0, ce, ch, w["storage"]) as cav:
+        cav.tune(**tuning)
+        cav.set_fields(f)
+        for _ in range(args.warmup):
+            cav.step(per)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            cav.step(per)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out["one_cavity"] = {"value": round(cells * per * args.steps / dt / 1e9, 3),
+                             "ms_per_step": round(1e3 * dt / args.steps, 3)}
+    return {"metric": "Gcell-updates/s", "value": out["slabs"]["value"], "unit": "Gcell-updates/s",
+            "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "slab512", "cells": [nx, ny, nz], "nslabs": w["nslabs"], "ghost": w["ghost"],
+                       "leapfrog_steps_per_bench_step": per, "tuning": tuning,
+                       "exchange": "device to device between neighbouring slab contexts, every 2 steps"},
+            "slabs": out["slabs"], "one_cavity": out["one_cavity"],
+            "slabs_vs_one_cavity": round(out["slabs"]["value"] / out["one_cavity"]["value"], 3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -504,7 +559,7 @@ def main():
         TUNING_OVERRIDE = json.loads(args.tuning)
     w = WORKLOADS[args.workload]
     standalone = {"batch": ("batched", run_batch), "serve": ("served", run_serve),
-                  "precision": ("precision", run_precision)}
+                  "precision": ("precision", run_precision), "slab": ("slab", run_slab)}
     if args.impl == "ours" and w.get("kind") in standalone:
         name, fn = standalone[w["kind"]]
         leg = fn(args, w)

@@ -32,10 +32,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-#ifndef FDTD_TMA_EVICT_LAST
-#define FDTD_TMA_EVICT_LAST 0   // 1: the two-step kernel's unit loads carry an L2 evict-last policy
-#endif
-
 #ifndef FDTD_CHECK
 #define FDTD_CHECK 0   // 1: every global store and TMA x origin of the fused kernels is checked first
 #endif

@@ -128,9 +128,6 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
 
     // =========================================================== producer warp
     if (warp == NCW) {
-#if FDTD_TMA_EVICT_LAST
-        const uint64_t l2_keep = l2_policy_evict_last();   // unit loads stay in L2 for the neighbouring tiles
-#endif
         int issued = 0, m = 0, s = 0;
         uint32_t rnd = 0;
         bool ok = true;
@@ -169,12 +166,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                         mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? idbox_bytes<TY>() : 0));
                         // the six field boxes in one load: a 4-D box (x, y, plane, field) lands as six
                         // consecutive FB-byte boxes (FS == FB)
-#if FDTD_TMA_EVICT_LAST
-                        tma_load_4d_hint(dst, rec->maps + src_copy * 6, G::box_x(rec->x0), rec->y0 - 2, kk, 0, &full[s],
-                                         l2_keep);
-#else
                         tma_load_4d(dst, rec->maps + src_copy * 6, G::box_x(rec->x0), rec->y0 - 2, kk, 0, &full[s]);
-#endif
                         if (has_id)
                             tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
                     } else {

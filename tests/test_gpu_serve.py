@@ -103,6 +103,38 @@ def test_served_results_match_oracle(kernel, K):
                 assert all(np.array_equal(a, b) for a, b in zip(r.result, solo(r, kernel))), r.id
 
 
+def test_mixed_order_stream_matches_oracle():
+    """Second and fourth-order requests in one stream: each order runs in batches of its own (FP32 and
+    BF16), and every result matches the FP64 oracle of its own scheme."""
+    import oracle
+    from paper_2504_09118_gb300 import Cavity
+    from paper_2504_09118_gb300.serve import Server
+    reqs = stream_requests(15, 9, max_side=32, max_steps=90)
+    for r in reqs[::3]:
+        r.order = 4
+    srv = Server(DT, result="fields", K=16, tuning={"kernel": 3, "tile_y": 16})
+    try:
+        st = srv.run(reqs)
+        keys = set(srv.batches)
+    finally:
+        srv.close()
+    assert st.n == len(reqs) and st.failed == 0
+    assert {(0, 4), (2, 4)} & keys and (0, 2) in keys
+    for r in reqs:
+        ref = oracle.as_f64(r.fields)
+        (oracle.step4 if r.order == 4 else oracle.step)(ref, DT, DT, r.steps, omp=True)
+        dims = (r.nx, r.ny, r.nz)
+        if r.storage == 0:
+            compare_fields(r.result, ref, dims, REL_L2_F32)
+            if r.order == 4:   # equal to the fourth-order kernel stepping the request alone
+                with Cavity(*dims, DT, 1.0, None, None, 0, order=4) as c:
+                    c.set_fields(r.fields)
+                    c.step(r.steps)
+                    assert all(np.array_equal(a, b) for a, b in zip(r.result, c.get_fields())), r.id
+        else:
+            compare_fields(r.result, ref, dims, _random_walk_bound(r.steps))
+
+
 def test_budget_limits_concurrency():
     from paper_2504_09118_gb300.serve import Server, device_bytes_estimate
     reqs = stream_requests(10, 2, max_side=24, max_steps=20)

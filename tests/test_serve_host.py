@@ -80,7 +80,7 @@ class FakeCavity:
     fail_create = set()     # (nx, ny, nz) whose creation fails as if out of memory
     fail_load = set()       # ... whose set_fields fails
 
-    def __init__(self, nx, ny, nz, dt, dx, ce, ch, storage, stream):
+    def __init__(self, nx, ny, nz, dt, dx, ce, ch, storage, stream, order=2):
         if (nx, ny, nz) in FakeCavity.fail_create:
             raise B.FdtdError(B.FDTD_ERR_OOM, "out of device memory")
         self.handle = self
@@ -164,8 +164,8 @@ def test_admission_budget_slots_and_exact_steps(fake_server, monkeypatch):
     reqs[30].nx, reqs[30].ny, reqs[30].nz = 400, 400, 400
     orig_init = FakeCavity.__init__
 
-    def tagged_init(self, nx, ny, nz, *a):   # the request a context belongs to: the first unadmitted one
-        orig_init(self, nx, ny, nz, *a)       # of its size (admission is in arrival order)
+    def tagged_init(self, nx, ny, nz, *a, **kw):   # the request a context belongs to: the first unadmitted
+        orig_init(self, nx, ny, nz, *a, **kw)       # one of its size (admission is in arrival order)
         self.rid = next(r.id for r in reqs if (r.nx, r.ny, r.nz) == (nx, ny, nz) and np.isnan(r.t_admit))
     monkeypatch.setattr(FakeCavity, "__init__", tagged_init)
     stats = srv.run(reqs, clock=clock)
