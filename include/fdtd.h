@@ -404,7 +404,8 @@ FDTD_API int fdtd_slab_divergence_sq(fdtd_ctx *ctx, double *divE2, double *divH2
 /* fdtd_set_storage_scales - fix the power-of-two scales s_E, s_H with which later loads store 16-bit fields
  * (0: chosen from the loaded data, the default).  Slabs of one cavity must share them: take
  * fdtd_storage_scale_of of the largest |E| and |H| of the whole cavity.  FDTD_ERR_ARG for a value that is
- * neither 0 nor a power of two.  Applies from the next fdtd_set_fields; no effect with FP32 storage. */
+ * neither 0 nor a power of two, and from the next fdtd_set_fields when a loaded field times its fixed
+ * scale exceeds the FP16 range.  Applies from the next fdtd_set_fields; no effect with FP32 storage. */
 FDTD_API int fdtd_set_storage_scales(fdtd_ctx *ctx, double s_e, double s_h);
 
 /* fdtd_storage_scale_of - the scale a load chooses for a field whose largest magnitude is maxabs:

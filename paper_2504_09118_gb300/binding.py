@@ -227,16 +227,30 @@ def fdtd_slab_halo_bytes(ctx) -> int:
     return int(lib().fdtd_slab_halo_bytes(ctx))
 
 
+def _buffer(buf, writable: bool):
+    """(pointer, on_device) of a halo buffer: a CUDA tensor, a CPU tensor or a numpy array (contiguous)."""
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("halo buffers must be contiguous")
+        return buf.data_ptr(), bool(getattr(buf, "is_cuda", False))
+    if not (isinstance(buf, np.ndarray) and buf.flags.c_contiguous and (buf.flags.writeable or not writable)):
+        raise ValueError("halo buffers must be contiguous (and writable for an export)")
+    return buf.ctypes.data, False
+
+
 def fdtd_slab_export(ctx, side: int, buf) -> None:
-    """Owned boundary cells of one side into buf: a device tensor (stream-ordered) or a host numpy array."""
-    on_device = hasattr(buf, "data_ptr")
-    ptr = buf.data_ptr() if on_device else buf.ctypes.data
+    """Owned boundary cells of one side into buf: a device tensor (stream-ordered) or host memory (a CPU
+    tensor or numpy array; the call waits for the copy)."""
+    ptr, on_device = _buffer(buf, True)
+    if buf.nbytes < fdtd_slab_halo_bytes(ctx):
+        raise ValueError("halo buffer smaller than fdtd_slab_halo_bytes")
     _check(ctx, lib().fdtd_slab_export(ctx, int(side), ptr, int(on_device)))
 
 
 def fdtd_slab_import(ctx, side: int, buf) -> None:
-    on_device = hasattr(buf, "data_ptr")
-    ptr = buf.data_ptr() if on_device else np.ascontiguousarray(buf).ctypes.data
+    ptr, on_device = _buffer(buf, False)
+    if buf.nbytes < fdtd_slab_halo_bytes(ctx):
+        raise ValueError("halo buffer smaller than fdtd_slab_halo_bytes")
     _check(ctx, lib().fdtd_slab_import(ctx, int(side), ptr, int(on_device)))
 
 

@@ -624,7 +624,12 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
                 mx = std::max(mx, m);
             }
             float sc = mx > 0.f ? std::ldexp(1.0f, 8 - (int)std::ceil(std::log2((double)mx))) : 1.0f;
-            if (c->fixed_scale[g] > 0.f) sc = c->fixed_scale[g];   // fdtd_set_storage_scales
+            if (c->fixed_scale[g] > 0.f) {   // fdtd_set_storage_scales
+                sc = c->fixed_scale[g];
+                if (c->storage == FDTD_F16 && (double)mx * sc > 60000.0)
+                    return fail(c, FDTD_ERR_ARG, "fixed storage scale %g overflows FP16 for |%s| up to %g", sc,
+                                g ? "H" : "E", (double)mx);
+            }
             for (int q = 3 * g; q < 3 * g + 3; ++q) c->scale[q] = sc;
         }
         if (c->table_fused) {

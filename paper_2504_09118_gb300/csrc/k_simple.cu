@@ -19,12 +19,14 @@ __device__ __forceinline__ bool tangential(int comp, int i, int j, int k) {
            (comp == 2 && (i == 0 || j == 0));
 }
 
+// Planes per thread of the layout kernels: their loads are issued together before the stores, so that a
+// thread keeps several DRAM reads in flight (one element per thread left these kernels latency-bound).
+constexpr int KZs = 4;
+
 template <typename T>
-__global__ void pack_kernel(const CavityDesc d, int copy, int comp, const float *__restrict__ canon, float *face) {
-    const int i = blockIdx.x * BXs + threadIdx.x, j = blockIdx.y * BYs + threadIdx.y, k = blockIdx.z;
+__device__ __forceinline__ void pack_one(const CavityDesc &d, int copy, int comp, float v, int i, int j, int k,
+                                         float *face) {
     const int nx = d.nx, ny = d.ny, nz = d.nz;
-    if (i > nx || j > ny) return;
-    float v = canon[((long long)k * (ny + 1) + j) * (nx + 1) + i];
     if (i < nx && j < ny && k < nz) {
         if (comp < 3 && tangential(comp, i, j, k)) v = 0.f;
         st_field<T>(d, copy, comp, (long long)k * d.plane + (long long)j * d.pitch + i, v);
@@ -38,22 +40,44 @@ __global__ void pack_kernel(const CavityDesc d, int copy, int comp, const float 
     if (comp == 5 && k == nz && i < nx && j < ny) face[(long long)j * nx + i] = q;
 }
 
+// Canonical component -> active layout (and far faces); each thread takes KZs planes of one (i, j).
 template <typename T>
-__global__ void unpack_kernel(const CavityDesc d, int copy, int comp, float *__restrict__ canon) {
-    const int i = blockIdx.x * BXs + threadIdx.x, j = blockIdx.y * BYs + threadIdx.y, k = blockIdx.z;
+__global__ void pack_kernel(const CavityDesc d, int copy, int comp, const float *__restrict__ canon, float *face) {
+    const int i = blockIdx.x * BXs + threadIdx.x, j = blockIdx.y * BYs + threadIdx.y, k0 = blockIdx.z * KZs;
     const int nx = d.nx, ny = d.ny, nz = d.nz;
     if (i > nx || j > ny) return;
-    float v = 0.f;
-    if (i < nx && j < ny && k < nz) {
-        v = ld_field<T>(d, copy, comp, (long long)k * d.plane + (long long)j * d.pitch + i);
-    } else if (comp == 3 && i == nx && j < ny && k < nz) {
-        v = d.face[0][(long long)k * ny + j];
-    } else if (comp == 4 && j == ny && i < nx && k < nz) {
-        v = d.face[1][(long long)k * nx + i];
-    } else if (comp == 5 && k == nz && i < nx && j < ny) {
-        v = d.face[2][(long long)j * nx + i];
-    }
-    canon[((long long)k * (ny + 1) + j) * (nx + 1) + i] = v;
+    const long long zs = (long long)(ny + 1) * (nx + 1), base = (long long)j * (nx + 1) + i;
+    float v[KZs];
+#pragma unroll
+    for (int q = 0; q < KZs; ++q) v[q] = k0 + q <= nz ? canon[(k0 + q) * zs + base] : 0.f;
+#pragma unroll
+    for (int q = 0; q < KZs; ++q)
+        if (k0 + q <= nz) pack_one<T>(d, copy, comp, v[q], i, j, k0 + q, face);
+}
+
+template <typename T>
+__device__ __forceinline__ float unpack_one(const CavityDesc &d, int copy, int comp, int i, int j, int k) {
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    if (i < nx && j < ny && k < nz) return ld_field<T>(d, copy, comp, (long long)k * d.plane + (long long)j * d.pitch + i);
+    if (comp == 3 && i == nx && j < ny && k < nz) return d.face[0][(long long)k * ny + j];
+    if (comp == 4 && j == ny && i < nx && k < nz) return d.face[1][(long long)k * nx + i];
+    if (comp == 5 && k == nz && i < nx && j < ny) return d.face[2][(long long)j * nx + i];
+    return 0.f;
+}
+
+// Active layout (and far faces) -> canonical component, zero outside the extent; KZs planes per thread.
+template <typename T>
+__global__ void unpack_kernel(const CavityDesc d, int copy, int comp, float *__restrict__ canon) {
+    const int i = blockIdx.x * BXs + threadIdx.x, j = blockIdx.y * BYs + threadIdx.y, k0 = blockIdx.z * KZs;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    if (i > nx || j > ny) return;
+    const long long zs = (long long)(ny + 1) * (nx + 1), base = (long long)j * (nx + 1) + i;
+    float v[KZs];
+#pragma unroll
+    for (int q = 0; q < KZs; ++q) v[q] = k0 + q <= nz ? unpack_one<T>(d, copy, comp, i, j, k0 + q) : 0.f;
+#pragma unroll
+    for (int q = 0; q < KZs; ++q)
+        if (k0 + q <= nz) canon[(k0 + q) * zs + base] = v[q];
 }
 
 __device__ __forceinline__ bool in_extent(int comp, int i, int j, int k, int nx, int ny, int nz) {
@@ -304,13 +328,13 @@ cudaError_t simple_step_typed(const CavityDesc &d, int copy, cudaStream_t s) {
 
 cudaError_t launch_pack(int storage, const CavityDesc &d, int copy, int comp, const float *canon, float *face,
                         cudaStream_t s) {
-    dim3 blk(BXs, BYs), grd((d.nx + 1 + BXs - 1) / BXs, (d.ny + 1 + BYs - 1) / BYs, d.nz + 1);
+    dim3 blk(BXs, BYs), grd((d.nx + 1 + BXs - 1) / BXs, (d.ny + 1 + BYs - 1) / BYs, (d.nz + 1 + KZs - 1) / KZs);
     FDTD_STORAGE_DISPATCH(storage, pack_kernel<T><<<grd, blk, 0, s>>>(d, copy, comp, canon, face));
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(int storage, const CavityDesc &d, int copy, int comp, float *canon, cudaStream_t s) {
-    dim3 blk(BXs, BYs), grd((d.nx + 1 + BXs - 1) / BXs, (d.ny + 1 + BYs - 1) / BYs, d.nz + 1);
+    dim3 blk(BXs, BYs), grd((d.nx + 1 + BXs - 1) / BXs, (d.ny + 1 + BYs - 1) / BYs, (d.nz + 1 + KZs - 1) / KZs);
     FDTD_STORAGE_DISPATCH(storage, unpack_kernel<T><<<grd, blk, 0, s>>>(d, copy, comp, canon));
     return cudaGetLastError();
 }

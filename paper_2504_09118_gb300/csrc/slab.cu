@@ -100,6 +100,11 @@ int fdtd_create_slab(fdtd_ctx **out, int nx, int ny, int nz_global, int k0, int 
     c->slab.g_lo = g_lo;
     c->slab.g_hi = g_hi;
     c->slab.ghost = ghost;
+    // the exchange's ordering event belongs to the slab's device, which is current here
+    if (cudaEventCreateWithFlags(&c->slab.ev, cudaEventDisableTiming) != cudaSuccess) {
+        fdtd_destroy(c);
+        return fail(nullptr, FDTD_ERR_CUDA, "slab event create failed");
+    }
     slab_after_load(c);
     *out = c;
     return FDTD_OK;
@@ -160,8 +165,6 @@ int fdtd_slab_exchange(fdtd_ctx *lo, fdtd_ctx *hi) {
         return fail(lo, FDTD_ERR_ARG, "the slabs are not neighbours (k1 of the lower one != k0 of the upper one)");
     if (lo->scale[0] != hi->scale[0] || lo->scale[3] != hi->scale[3])
         return fail(lo, FDTD_ERR_ARG, "16-bit slabs need equal storage scales (fdtd_set_storage_scales)");
-    for (fdtd_ctx *c : {lo, hi})
-        if (!c->slab.ev) CK(c, cudaEventCreateWithFlags(&c->slab.ev, cudaEventDisableTiming));
     // both copies run on lo's stream after hi's earlier work; hi's later work waits for them
     CK(lo, cudaEventRecord(hi->slab.ev, hi->stream));
     CK(lo, cudaStreamWaitEvent(lo->stream, hi->slab.ev, 0));

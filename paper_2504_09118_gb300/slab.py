@@ -160,9 +160,10 @@ class SlabDomain:
 
 
 class CtxSlab:
-    """A slab context on this process's GPU in the shape DistributedSlab drives (device halo buffers)."""
+    """A slab context on this process's GPU in the shape DistributedSlab drives.  Halo buffers live in device
+    memory (for NCCL) or, with host=True, in pinned host memory (for a CPU transport such as gloo)."""
 
-    def __init__(self, handle, order: int, device=None):
+    def __init__(self, handle, order: int, device=None, host: bool = False):
         import torch
         self.h = handle
         info = B.fdtd_slab_info(handle)
@@ -171,15 +172,19 @@ class CtxSlab:
         n = B.fdtd_slab_halo_bytes(handle)
         self.nbytes = n
         self.device = device
+        self.host = host
 
         def buf():
+            if host:
+                return torch.empty(n, dtype=torch.uint8, pin_memory=True)
             return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
         self.send = [buf(), buf()]
         self.recv = [buf(), buf()]
 
     def export(self, side: int):
-        B.fdtd_slab_export(self.h, side, self.send[side])
-        B.fdtd_sync(self.h)   # the send below reads the buffer on another stream
+        B.fdtd_slab_export(self.h, side, self.send[side])   # a host export waits for its copy
+        if not self.host:
+            B.fdtd_sync(self.h)   # the send below reads the device buffer on another stream
         return self.send[side]
 
     def recv_buffer(self, side: int):
@@ -212,6 +217,11 @@ class DistributedSlab:
             recvs.append((side, r))
         for q in reqs:
             q.wait()
+        # a wait orders only torch's current stream after a device receive; the import runs on the slab's
+        # own stream, so the received bytes must be complete on the device first
+        if any(getattr(r, "is_cuda", False) for _, r in recvs):
+            import torch
+            torch.cuda.current_stream(recvs[0][1].device).synchronize()
         for side, r in recvs:
             self.slab.import_(side, r)
         self.fresh = True

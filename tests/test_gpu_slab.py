@@ -159,6 +159,17 @@ def test_slab_rules():
         with pytest.raises(FdtdError):
             B.fdtd_set_storage_scales(lo, 3.0, 1.0)
         assert B.fdtd_storage_scale_of(1.0) == 256.0 and B.fdtd_storage_scale_of(0.3) == 512.0
+        # a fixed FP16 scale that the loaded values would overflow is refused at the load
+        h16 = B.fdtd_create(nx, ny, 12, DT, 1.0, None, None, B.FDTD_F16)
+        try:
+            B.fdtd_set_storage_scales(h16, 2.0 ** 20, 256.0)
+            with pytest.raises(FdtdError) as e:
+                B.fdtd_set_fields(h16, f)
+            assert e.value.code == B.FDTD_ERR_ARG
+            B.fdtd_set_storage_scales(h16, 256.0, 256.0)
+            B.fdtd_set_fields(h16, f)
+        finally:
+            B.fdtd_destroy(h16)
     finally:
         B.fdtd_destroy(lo)
         B.fdtd_destroy(hi)
