@@ -46,6 +46,9 @@ WORKLOADS = {
     # small case for ncu captures (fields 0.8 GB > L2, a few launches)
     "single256": dict(n=(256, 256, 256), steps=20, storage=0, sphere_seed=1, field_seed=2, spheres=8),
     "single256_f16": dict(n=(256, 256, 256), steps=20, storage=1, sphere_seed=1, field_seed=2, spheres=8),
+    # DRAM-counter case of single512: the same 512 x 512 tiles over 64 planes (0.8 GB of fields > L2), whose
+    # traffic per plane is that of the full cavity (scaled by 512 / 64 for its launches)
+    "single512_z64": dict(n=(512, 512, 64), steps=20, storage=0, sphere_seed=1, field_seed=2, spheres=32),
     "precision384_f16": dict(n=(384, 384, 384), steps=1000, storage=1, sphere_seed=3, field_seed=4, spheres=32),
     "precision384_bf16": dict(n=(384, 384, 384), steps=1000, storage=2, sphere_seed=3, field_seed=4, spheres=32),
     # 256 independent cavities, sides iid U{16..96}, vacuum or spheres (p = 1/2), 500 steps per bench step

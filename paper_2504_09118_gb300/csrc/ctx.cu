@@ -98,7 +98,9 @@ int encode_maps(fdtd_ctx *c, int set, int box_y) {
     auto enc = get_encode();
     if (!enc) return fail(c, FDTD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const int hx = 16 / (int)esize(c->storage);
-    const int bx = kTileX + 2 * hx;
+    // field box width: one granule of halo on each side of the 64 lane cells, except for the two-step
+    // kernels, whose lane cells start 2 left of the tile and whose box origin is rounded down: 64 + one granule
+    const int bx = set == 1 ? kTileX + hx : kTileX + 2 * hx;
     std::vector<CUtensorMap> &maps = c->host_maps[set];
     maps.assign(kMapsPerCavity, CUtensorMap{});
     const size_t es = esize(c->storage);

@@ -38,7 +38,9 @@ constexpr uint64_t kWaitLimitNs2 = 2000000000ull;
 template <typename T> struct Geom2 {
     static constexpr int HX = 16 / (int)sizeof(T);   // 4 (FP32) or 8 (16-bit): elements per 16-byte TMA granule
     static constexpr int W = 60;                      // output columns per tile
-    static constexpr int BX = 64 + 2 * HX;            // field box width (covers the lanes' cells from any origin shift)
+    // field box width: the lanes read box columns shift .. shift + 64 (the last one for the x + 1 neighbour),
+    // and the origin shift is at most HX - 1, so 64 + HX columns cover every origin
+    static constexpr int BX = 64 + HX;
     // The box starts at the lane cells' first column x0 - 2 rounded down to the 16-byte granule, so that every
     // tile origin (a multiple of 60) gives a legal TMA x coordinate; a lane's box column is shifted by the
     // remainder (2 for FP32, 0..6 for 16-bit storage).
@@ -63,10 +65,12 @@ __host__ __device__ constexpr int al(int v, int a) { return (v + a - 1) / a * a;
 template <typename T, int TY> __host__ __device__ constexpr int box_bytes() {
     return Geom2<T>::BX * (TY + 4) * (int)sizeof(T);
 }
-template <typename T, int TY> __host__ __device__ constexpr int box_stride() { return al(box_bytes<T, TY>(), 128); }
+// The 4-D load lands the six field boxes back to back (field stride = box bytes, a multiple of 16); the id
+// box, a load of its own, starts at the next 128-byte boundary.
+template <typename T, int TY> __host__ __device__ constexpr int idbox_off() { return al(6 * box_bytes<T, TY>(), 128); }
 template <int TY> __host__ __device__ constexpr int idbox_bytes() { return Geom2<float>::IBX * (TY + 4); }
 template <typename T, int TY> __host__ __device__ constexpr int slot2_bytes() {
-    return al(6 * box_stride<T, TY>() + idbox_bytes<TY>(), 128);
+    return al(idbox_off<T, TY>() + idbox_bytes<TY>(), 128);
 }
 constexpr int PW = 68;   // shared plane row pitch: column x - x0 + 4 (lane cells at 2 lane + 2, + 3)
 template <int TY> __host__ __device__ constexpr int PR() { return TY + 5; }   // rows: r + 1 for r in -1 .. TY+3
@@ -85,8 +89,8 @@ template <typename T, int TY, bool BATCH>
 __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fused2Params P) {
     using G = Geom2<T>;
     constexpr int BX = G::BX, W = G::W;
-    constexpr int FB = box_bytes<T, TY>(), FS = box_stride<T, TY>(), FE = FS / (int)sizeof(T);
-    static_assert(FS == FB, "field boxes must be whole 128-byte blocks: one 4-D load writes them back to back");
+    constexpr int FB = box_bytes<T, TY>(), FE = FB / (int)sizeof(T), IDO = idbox_off<T, TY>();
+    static_assert(FB % 16 == 0 && FE % 2 == 0, "field boxes keep 16-byte rows and even-aligned pairs");
     constexpr int NCW = TY + 3, NCT = NCW * 32;
     constexpr int PF = plane_floats<TY>();
 
@@ -165,10 +169,10 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                         (!has_id || tma_x_ok(P.status, rec->id_x0, 1))) {
                         mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? idbox_bytes<TY>() : 0));
                         // the six field boxes in one load: a 4-D box (x, y, plane, field) lands as six
-                        // consecutive FB-byte boxes (FS == FB)
+                        // consecutive FB-byte boxes
                         tma_load_4d(dst, rec->maps + src_copy * 6, G::box_x(rec->x0), rec->y0 - 2, kk, 0, &full[s]);
                         if (has_id)
-                            tma_load_3d(dst + 6 * FS, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
+                            tma_load_3d(dst + IDO, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
                     } else {
                         mbar_arrive(&full[s]);   // checked build: the unit is skipped, the slot still completes
                     }
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
             ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the phases below shuffle across lanes
             const T *A = reinterpret_cast<const T *>(slots + sa * SB);
             const T *B = reinterpret_cast<const T *>(slots + sb * SB);
-            const uint8_t *ida = slots + sa * SB + 6 * FS;
+            const uint8_t *ida = slots + sa * SB + IDO;
             // H2(k-1) needs plane k-1 >= 0 (its inputs at plane -1 were never written)
             const bool do_e1 = k >= kz0 - 1;
             const bool do_h2 = !level1_only && k >= kz0 && k >= 1, do_e2 = !level1_only && k >= kz0 + 1;

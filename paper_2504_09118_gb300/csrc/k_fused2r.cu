@@ -34,7 +34,9 @@ constexpr uint64_t kWaitLimitNsR = 2000000000ull;
 template <typename T> struct GeomR {
     static constexpr int HX = 16 / (int)sizeof(T);   // 4 (FP32) or 8 (16-bit): elements per 16-byte TMA granule
     static constexpr int W = 60;                      // output columns per tile
-    static constexpr int BX = 64 + 2 * HX;            // field box width (covers the lanes' cells from any origin shift)
+    // field box width: the lanes read box columns shift .. shift + 64 (the last one for the x + 1 neighbour),
+    // and the origin shift is at most HX - 1, so 64 + HX columns cover every origin
+    static constexpr int BX = 64 + HX;
     // The box starts at the lane cells' first column x0 - 2 rounded down to the 16-byte granule, so that every
     // tile origin (a multiple of 60) gives a legal TMA x coordinate; a lane's box column is shifted by the
     // remainder (2 for FP32, 0..6 for 16-bit storage).
@@ -60,8 +62,10 @@ template <typename T, int TY> __host__ __device__ constexpr int boxr_bytes() {
     return GeomR<T>::BX * (TY + 4) * (int)sizeof(T);
 }
 template <int TY> __host__ __device__ constexpr int idboxr_bytes() { return GeomR<float>::IBX * (TY + 4); }
+// six field boxes back to back (one 4-D load), then the id box at the next 128-byte boundary
+template <typename T, int TY> __host__ __device__ constexpr int idboxr_off() { return alr(6 * boxr_bytes<T, TY>(), 128); }
 template <typename T, int TY> __host__ __device__ constexpr int slotr_bytes() {
-    return alr(6 * alr(boxr_bytes<T, TY>(), 128) + idboxr_bytes<TY>(), 128);
+    return alr(idboxr_off<T, TY>() + idboxr_bytes<TY>(), 128);
 }
 template <int TY> __host__ __device__ constexpr int nwarps_r() { return (TY + 4) / 2; }   // consumer warps
 constexpr int PWR = 68;   // shared plane row pitch: column x - x0 + 4 (lane cells at 2 lane + 2, + 3)
@@ -88,8 +92,8 @@ template <typename T, int TY, bool BATCH>
 __global__ void __launch_bounds__(threadsr<TY>(), 1) fused2r_step_kernel(const FusedRParams P) {
     using G = GeomR<T>;
     constexpr int BX = G::BX, W = G::W;
-    constexpr int FB = boxr_bytes<T, TY>(), FE = FB / (int)sizeof(T);
-    static_assert(FB % 128 == 0, "field boxes must be whole 128-byte blocks: one 4-D load writes them back to back");
+    constexpr int FB = boxr_bytes<T, TY>(), FE = FB / (int)sizeof(T), IDO = idboxr_off<T, TY>();
+    static_assert(FB % 16 == 0 && FE % 2 == 0, "field boxes keep 16-byte rows and even-aligned pairs");
     constexpr int NW = nwarps_r<TY>(), NCT = NW * 32;
     constexpr int PF = planer_floats<TY>();
     static_assert(2 * NW == TY + 4, "rows 0 .. TY + 3 in pairs");
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(threadsr<TY>(), 1) fused2r_step_kernel(const F
                         mbar_arrive_expect_tx(&full[s], 6 * FB + (has_id ? idboxr_bytes<TY>() : 0));
                         tma_load_4d(dst, rec->maps + src_copy * 6, G::box_x(rec->x0), rec->y0 - 2, kk, 0, &full[s]);
                         if (has_id)
-                            tma_load_3d(dst + 6 * FB, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
+                            tma_load_3d(dst + IDO, rec->maps + 12, rec->id_x0, rec->y0 - 2, kk, &full[s]);
                     } else {
                         mbar_arrive(&full[s]);
                     }
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(threadsr<TY>(), 1) fused2r_step_kernel(const F
             ok = __all_sync(0xffffffffu, ok);
             const T *Au = reinterpret_cast<const T *>(slots + sa * SB);
             const T *Bu = reinterpret_cast<const T *>(slots + sb * SB);
-            const uint8_t *ida = slots + sa * SB + 6 * FB;
+            const uint8_t *ida = slots + sa * SB + IDO;
             const bool do_e1 = k >= kz0 - 1;
             const bool do_h2 = !level1_only && k >= kz0 && k >= 1, do_e2 = !level1_only && k >= kz0 + 1;
             float *e1cur = e1b + (k & 1) * 2 * PF, *e1prv = e1b + ((k + 1) & 1) * 2 * PF;
