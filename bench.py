@@ -75,9 +75,9 @@ BENCH_TUNING = dict(kernel=3, tile_y=16, stages=4, zchunk=0, ctas_per_sm=0, use_
 # batch workload, and measured best on the serving stream; the mix changes every chunk, so it is fixed
 # rather than re-tuned).
 SERVE_TUNING = dict(kernel=3, tile_y=16, stages=4)
-STEPS_PER_LAUNCH = {1: 0.5, 2: 1, 3: 2, 4: 2}   # leapfrog steps per launch of each kernel kind (SIMPLE: H and E launches)
+STEPS_PER_LAUNCH = {1: 0.5, 2: 1, 3: 2, 4: 2, 5: 3}   # leapfrog steps per launch of each kernel kind (SIMPLE: H and E launches)
 DOMINANT_KERNEL = {1: "simple_h_kernel/simple_e_kernel", 2: "fused_step_kernel", 3: "fused2_step_kernel",
-                   4: "fused2r_step_kernel"}
+                   4: "fused2r_step_kernel", 5: "fused3_step_kernel"}
 ID_BYTES = 1  # material id per cell
 NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e nominal bandwidth (context beside the measured copy peak)
 

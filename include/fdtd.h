@@ -77,8 +77,11 @@ enum fdtd_kernel {
     FDTD_KERNEL_SIMPLE = 1,  /* two launches per step (H, then E), one thread per cell; unfused baseline */
     FDTD_KERNEL_FUSED = 2,   /* one TMA-pipelined launch per step: H then E fused in a z-march */
     FDTD_KERNEL_TEMPORAL = 3, /* two steps per launch (temporal blocking); an odd count ends with one FUSED step */
-    FDTD_KERNEL_TEMPORAL2 = 4 /* TEMPORAL with two tile rows per consumer warp (tile_y 12 or 16): same tiles and
+    FDTD_KERNEL_TEMPORAL2 = 4, /* TEMPORAL with two tile rows per consumer warp (tile_y 12 or 16): same tiles and
                                  results (FP32: bit for bit), fewer instructions per cell-step */
+    FDTD_KERNEL_TEMPORAL3 = 5 /* three steps per launch (single cavities, second order; tile_y 8, 10 or 12; 58-column
+                                 tiles); a remainder ends with FUSED steps; FP32 results bit for bit those of
+                                 TEMPORAL */
 };
 
 /* Launch configuration of the step kernel; zero fields take the default. */

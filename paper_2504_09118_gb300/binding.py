@@ -19,7 +19,8 @@ from . import build as _build
 FDTD_F32, FDTD_F16, FDTD_BF16 = 0, 1, 2
 FDTD_OK, FDTD_ERR_ARG, FDTD_ERR_OOM, FDTD_ERR_CUDA, FDTD_ERR_TIMEOUT, FDTD_ERR_STATE, FDTD_ERR_UNSTABLE = (
     0, -1, -2, -3, -4, -5, -6)
-FDTD_KERNEL_AUTO, FDTD_KERNEL_SIMPLE, FDTD_KERNEL_FUSED, FDTD_KERNEL_TEMPORAL, FDTD_KERNEL_TEMPORAL2 = 0, 1, 2, 3, 4
+(FDTD_KERNEL_AUTO, FDTD_KERNEL_SIMPLE, FDTD_KERNEL_FUSED, FDTD_KERNEL_TEMPORAL, FDTD_KERNEL_TEMPORAL2,
+ FDTD_KERNEL_TEMPORAL3) = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT", -5: "ERR_STATE",
                 -6: "ERR_UNSTABLE"}
 

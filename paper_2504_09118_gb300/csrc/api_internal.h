@@ -88,13 +88,13 @@ struct fdtd_ctx {
     unsigned *d_max = nullptr;
     CUtensorMap *d_maps = nullptr;          // kMapSets x kMapsPerCavity
     std::vector<CUtensorMap> host_maps[kMapSets];
-    int maps_by[kMapSets] = {0, 0, 0};      // box height each map set was encoded for (0: not yet)
+    int maps_by[kMapSets] = {0, 0, 0, 0};   // box height each map set was encoded for (0: not yet)
     CavityDesc *d_desc = nullptr;
     struct TileList {
         TileRec *d = nullptr;   // records, followed by the per-CTA range offsets
         int *first = nullptr;   // inside the same allocation as d
         int n = 0, grid = 0, key = 0;
-    } tl[3];                                // [0] one-step, [1] two-step, [2] fourth-order kernel
+    } tl[4];                                // [0] one-step, [1] two-step, [2] fourth-order, [3] three-step kernel
     int order = 2;                          // spatial order of the differences (2: Eq. 2, 4: the (2,4) scheme)
     double courant = 0.0;                   // max over cells of 3 ce ch (stable for order 2 when <= 1)
     int ch_uniform = 1;
@@ -199,7 +199,7 @@ int ensure_stage2(fdtd_ctx *c);
 
 // ---- launch planning (plan.cu)
 struct Shape {
-    int kind;   // 0: one step per launch, 1: two steps per launch, 2: one fourth-order step
+    int kind;   // 0: one step per launch, 1: two steps per launch, 2: one fourth-order step, 3: three steps
     int tile_y, stages, ctas_per_sm;
     int rows_per_warp;   // kind 1: rows per consumer warp (1, or 2 for FDTD_KERNEL_TEMPORAL2)
 };

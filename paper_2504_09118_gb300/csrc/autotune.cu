@@ -18,6 +18,9 @@ std::vector<fdtd_tuning> tune_candidates(bool batch, int order) {
             if (batch && st != 4) continue;
             v.push_back(fdtd_tuning{FDTD_KERNEL_TEMPORAL, ty, 0, 0, st, 1});
         }
+    // single cavities: three steps per launch, deepest ring that fits
+    if (!batch)
+        for (int ty : {8, 10, 12}) v.push_back(fdtd_tuning{FDTD_KERNEL_TEMPORAL3, ty, 0, 0, 0, 1});
     // two rows per consumer warp, with the deepest ring that fits beside its smaller exchange planes
     for (int ty : {12, 16}) v.push_back(fdtd_tuning{FDTD_KERNEL_TEMPORAL2, ty, 0, 0, 0, 1});
     return v;

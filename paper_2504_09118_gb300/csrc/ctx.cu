@@ -98,9 +98,10 @@ int encode_maps(fdtd_ctx *c, int set, int box_y) {
     auto enc = get_encode();
     if (!enc) return fail(c, FDTD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const int hx = 16 / (int)esize(c->storage);
-    // field box width: one granule of halo on each side of the 64 lane cells, except for the two-step
-    // kernels, whose lane cells start 2 left of the tile and whose box origin is rounded down: 64 + one granule
-    const int bx = set == 1 ? kTileX + hx : kTileX + 2 * hx;
+    // field box width: one granule of halo on each side of the 64 lane cells, except for the two- and
+    // three-step kernels, whose lane cells start left of the tile and whose box origin is rounded down to
+    // the granule: 64 + one granule
+    const int bx = (set == 1 || set == 3) ? kTileX + hx : kTileX + 2 * hx;
     std::vector<CUtensorMap> &maps = c->host_maps[set];
     maps.assign(kMapsPerCavity, CUtensorMap{});
     const size_t es = esize(c->storage);
@@ -160,8 +161,11 @@ bool use_fused(const fdtd_ctx *c) {
 bool use_temporal(const fdtd_ctx *c) {
     return use_fused(c) && c->order == 2 &&
            (c->tuning.kernel == FDTD_KERNEL_TEMPORAL || c->tuning.kernel == FDTD_KERNEL_TEMPORAL2 ||
-            c->tuning.kernel == FDTD_KERNEL_AUTO);
+            c->tuning.kernel == FDTD_KERNEL_TEMPORAL3 || c->tuning.kernel == FDTD_KERNEL_AUTO);
 }
+
+// Steps per launch of the context's multi-step kernel (use_temporal): 3 for TEMPORAL3, else 2.
+static int temporal_steps(const fdtd_ctx *c) { return c->tuning.kernel == FDTD_KERNEL_TEMPORAL3 ? 3 : 2; }
 
 // Tile kind of a context's one-step launches: 0 (Eq. 2) or 2 (fourth order).
 int one_step_kind(const fdtd_ctx *c) { return c->order == 4 ? 2 : 0; }
@@ -192,6 +196,8 @@ int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind) {
         CK(c, launch_fused_step(c->storage, L, c->stream));
     else if (kind == 1)
         CK(c, launch_fused2_step(c->storage, L, c->stream));
+    else if (kind == 3)
+        CK(c, launch_fused3_step(c->storage, L, c->stream));
     else
         CK(c, launch_fused4_step(c->storage, L, c->stream));
     return FDTD_OK;
@@ -520,7 +526,7 @@ void fdtd_destroy(fdtd_ctx *c) {
     for (void *p : {(void *)c->id, (void *)c->table, (void *)c->inv_table, (void *)c->table_fused,
                     (void *)c->d_status, (void *)c->d_partial, (void *)c->d_out, (void *)c->d_stage,
                     (void *)c->d_max, (void *)c->d_maps, (void *)c->d_desc, (void *)c->tl[0].d,
-                    (void *)c->tl[1].d, (void *)c->tl[2].d, (void *)c->d_src_comp, (void *)c->d_src_off, (void *)c->d_wave,
+                    (void *)c->tl[1].d, (void *)c->tl[2].d, (void *)c->tl[3].d, (void *)c->d_src_comp, (void *)c->d_src_off, (void *)c->d_wave,
                     (void *)c->d_probe_comp, (void *)c->d_probe_off, (void *)c->d_probe_buf, (void *)c->d_xclock})
         pool_free(p, st);
     pool_free(c->d_stage2, st);
@@ -547,8 +553,9 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
     if (!c) return FDTD_ERR_ARG;
     fdtd_tuning n{};
     if (t) n = *t;
-    if (n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL2) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
-    const bool two_step = n.kernel == FDTD_KERNEL_TEMPORAL || n.kernel == FDTD_KERNEL_TEMPORAL2;
+    if (n.kernel < 0 || n.kernel > FDTD_KERNEL_TEMPORAL3) return fail(c, FDTD_ERR_ARG, "bad kernel %d", n.kernel);
+    const bool two_step = n.kernel == FDTD_KERNEL_TEMPORAL || n.kernel == FDTD_KERNEL_TEMPORAL2 ||
+                          n.kernel == FDTD_KERNEL_TEMPORAL3;
     if (two_step && c->order != 2)
         return fail(c, FDTD_ERR_ARG, "the two-step kernels run the second-order scheme only");
     // one-step kernels: 4, 8 or 16 rows (the fourth-order kernel also 12); two-step kernel: 8, 12 or 16;
@@ -557,15 +564,16 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t) {
                ty_two = n.tile_y == 8 || n.tile_y == 12 || n.tile_y == 16, ty_two2 = n.tile_y == 12 || n.tile_y == 16;
     if (n.tile_y && !(n.kernel == FDTD_KERNEL_TEMPORAL    ? ty_two
                       : n.kernel == FDTD_KERNEL_TEMPORAL2 ? ty_two2
+                      : n.kernel == FDTD_KERNEL_TEMPORAL3 ? (n.tile_y == 8 || n.tile_y == 10 || n.tile_y == 12)
                       : n.kernel == FDTD_KERNEL_AUTO      ? (ty_one || ty_two)
                                                           : ty_one))
         return fail(c, FDTD_ERR_ARG, "tile_y must be 4, 8 or 16 (fourth order: also 12; two-step kernel: 8, 12 or 16; "
-                                     "two-step kernel with two rows per warp: 12 or 16)");
+                                     "two-step kernel with two rows per warp: 12 or 16; three-step kernel: 8, 10 or 12)");
     if (n.stages && (n.stages < 3 || n.stages > 8)) return fail(c, FDTD_ERR_ARG, "stages must be in [3, 8]");
     if (n.stages == 3 && c->order == 4) return fail(c, FDTD_ERR_ARG, "the fourth-order kernel needs stages >= 4");
     if (n.zchunk < 0 || n.ctas_per_sm < 0) return fail(c, FDTD_ERR_ARG, "negative tuning value");
     c->tuning = n;
-    c->tl[0].key = c->tl[1].key = c->tl[2].key = 0;   // force tile rebuilds
+    c->tl[0].key = c->tl[1].key = c->tl[2].key = c->tl[3].key = 0;   // force tile rebuilds
     cudaStreamSynchronize(c->stream);   // no graph of this context may still be running
     drop_graphs(c->graphs);
     return FDTD_OK;
@@ -580,8 +588,9 @@ int fdtd_set_order(fdtd_ctx *c, int order) {
     if (c->courant * gain * gain > 1.0 + 1e-6)
         return fail(c, FDTD_ERR_UNSTABLE, "Courant bound of order %d violated: max sqrt(3 ce ch) * %.4f = %.6f > 1",
                     order, gain, std::sqrt(c->courant) * gain);
-    if (order == 4 && (c->tuning.kernel == FDTD_KERNEL_TEMPORAL || c->tuning.kernel == FDTD_KERNEL_TEMPORAL2))
-        return fail(c, FDTD_ERR_ARG, "the two-step kernels run the second-order scheme only; retune first");
+    if (order == 4 && (c->tuning.kernel == FDTD_KERNEL_TEMPORAL || c->tuning.kernel == FDTD_KERNEL_TEMPORAL2 ||
+                       c->tuning.kernel == FDTD_KERNEL_TEMPORAL3))
+        return fail(c, FDTD_ERR_ARG, "the multi-step kernels run the second-order scheme only; retune first");
     if (order == 4 && c->tuning.stages == 3)
         return fail(c, FDTD_ERR_ARG, "the fourth-order kernel needs stages >= 4; retune first");
     cudaStreamSynchronize(c->stream);   // no graph of this context may still be running
@@ -645,7 +654,7 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
             CK(c, cudaMemcpyAsync(c->table_fused, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, c->stream));
             CK(c, cudaStreamSynchronize(c->stream));
         }
-        c->tl[0].key = c->tl[1].key = c->tl[2].key = 0;   // tile records embed the folded coefficients
+        c->tl[0].key = c->tl[1].key = c->tl[2].key = c->tl[3].key = 0;   // tile records embed the folded coefficients
         cudaStreamSynchronize(c->stream);
         drop_graphs(c->graphs);
     }
@@ -756,8 +765,10 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
     const int k1 = one_step_kind(c);
     if (fused)
         if (int rc = build_tiles(c, k1)) return rc;
+    // kind 1 (two steps per launch) or 3 (three steps per launch)
+    const int tkind = temporal_steps(c) == 3 ? 3 : 1, tper = temporal_steps(c);
     if (temporal)
-        if (int rc = build_tiles(c, 1)) return rc;
+        if (int rc = build_tiles(c, tkind)) return rc;
     // one launch from copy `parity` (fused kernels write copy parity ^ 1; the unfused one works in
     // place on copy cur), then the point currents and probes of that step
     auto step_launch = [&](int parity, int inj, int kind) -> int {
@@ -773,11 +784,11 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
         ++c->steps;
         --left;
     }
-    // kind 1 advances two steps per launch; either kind reads copy cur and writes copy 1 - cur.
-    // An odd remainder takes one launch of the one-step kernel at the end.
-    const int kind = temporal ? 1 : k1;
-    const int per = temporal ? 2 : 1;
-    const int K = 16;   // steps per graph
+    // kind 1 advances two steps per launch, kind 3 three; every fused kind reads copy cur and writes copy
+    // 1 - cur.  A remainder takes launches of the one-step kernel at the end.
+    const int kind = temporal ? tkind : k1;
+    const int per = temporal ? tper : 1;
+    const int K = per == 3 ? 18 : 16;   // steps per graph: an even number of launches
     if (c->tuning.use_graph && fused && c->stream != nullptr && left >= K) {
         GraphKey key{K, c->cur, kind + (extras ? 4 : 0)};
         auto it = c->graphs.find(key);
@@ -801,10 +812,10 @@ int fdtd_step(fdtd_ctx *c, int nsteps) {
         }
     }
     if (temporal)
-        for (; left >= 2; left -= 2) {
-            if (int rc = step_launch(c->cur, 0, 1)) return rc;
+        for (; left >= tper; left -= tper) {
+            if (int rc = step_launch(c->cur, 0, tkind)) return rc;
             c->cur ^= 1;
-            c->steps += 2;
+            c->steps += tper;
         }
     for (; left > 0; --left) {
         if (int rc = step_launch(c->cur, 0, k1)) return rc;

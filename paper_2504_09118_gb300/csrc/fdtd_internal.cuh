@@ -28,7 +28,7 @@ constexpr int kNumFields = 6;      // Ex, Ey, Ez, Hx, Hy, Hz
 constexpr int kMaxTable = 256;
 constexpr int kTileX = 64;         // fused kernel tile width along x (cells)
 constexpr int kMapsPerCavity = 13; // [parity 0: 6 fields][parity 1: 6 fields][id]
-constexpr int kMapSets = 3;        // box sets: one-step kernel, two-step kernel, fourth-order kernel
+constexpr int kMapSets = 4;        // box sets: one-step, two-step, fourth-order and three-step kernels
 
 template <typename T> struct Storage;
 template <> struct Storage<float> {

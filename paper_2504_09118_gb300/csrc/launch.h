@@ -75,6 +75,12 @@ cudaError_t launch_fused2_step(int storage, const FusedLaunch &L, cudaStream_t s
 int fused2r_smem_bytes(int storage, int tile_y, int stages);
 cudaError_t fused2r_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
 cudaError_t launch_fused2r_step(int storage, const FusedLaunch &L, cudaStream_t s);
+// Three-step (T = 3) kernel (k_fused3.cu; single cavities, tile heights 8, 10 and 12): output tile width along x,
+// shared memory, occupancy, launch.
+int fused3_tile_w();
+int fused3_smem_bytes(int storage, int tile_y, int stages);
+cudaError_t fused3_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
+cudaError_t launch_fused3_step(int storage, const FusedLaunch &L, cudaStream_t s);
 // Fused fourth-order kernel (k_fused4.cu): shared memory, occupancy, launch (stages 4..8).
 int fused4_smem_bytes(int storage, int tile_y, int stages);
 cudaError_t fused4_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);

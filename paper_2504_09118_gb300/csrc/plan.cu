@@ -15,6 +15,8 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind) {
     const bool rows2 = s.rows_per_warp == 2;
     if (kind == 2)
         s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 12 || t.tile_y == 16) ? t.tile_y : 12;
+    else if (kind == 3)
+        s.tile_y = (t.tile_y == 8 || t.tile_y == 10 || t.tile_y == 12) ? t.tile_y : 10;
     else if (kind == 0)
         s.tile_y = (t.tile_y == 4 || t.tile_y == 8 || t.tile_y == 16) ? t.tile_y : 8;
     else if (rows2)
@@ -24,10 +26,11 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind) {
     const int min_st = kind == 2 ? 4 : 3;
     // default ring depths: measured best at 512^3; the fourth-order kernel (three units resident) takes
     // the deepest ring that fits, which measured best for each of its tile heights
-    s.stages = (t.stages >= min_st && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : kind == 1 ? 6 : 8);
+    s.stages = (t.stages >= min_st && t.stages <= 8) ? t.stages : (kind == 0 ? 4 : kind == 1 ? 6 : 8);   // kind 3: deepest
     auto smem = [&](int st) {
         return kind == 0   ? fused_smem_bytes(storage, s.tile_y, st)
                : kind == 1 ? (rows2 ? fused2r_smem_bytes(storage, s.tile_y, st) : fused2_smem_bytes(storage, s.tile_y, st))
+               : kind == 3 ? fused3_smem_bytes(storage, s.tile_y, st)
                            : fused4_smem_bytes(storage, s.tile_y, st);
     };
     while (s.stages > min_st && smem(s.stages) > 227 * 1024) --s.stages;
@@ -42,6 +45,7 @@ Shape resolve_shape(int storage, const fdtd_tuning &t, int kind) {
             cudaError_t e = kind == 0   ? fused_occupancy(storage, s.tile_y, s.stages, &occ)
                             : kind == 1 ? (rows2 ? fused2r_occupancy(storage, s.tile_y, s.stages, &occ)
                                                  : fused2_occupancy(storage, s.tile_y, s.stages, &occ))
+                            : kind == 3 ? fused3_occupancy(storage, s.tile_y, s.stages, &occ)
                                         : fused4_occupancy(storage, s.tile_y, s.stages, &occ);
             if (e != cudaSuccess || occ < 1) occ = 1;
             occ_cache[key] = occ;
@@ -171,7 +175,7 @@ TileRec base_rec(const fdtd_ctx *c, int parity_off, int set) {
 void append_tiles_plan(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_off, int tile_y,
                        const std::vector<int> &plan, int kind) {
     const TileRec b = base_rec(c, parity_off, kind);
-    const int tw = kind == 1 ? fused2_tile_w(c->storage) : kTileX;
+    const int tw = kind == 1 ? fused2_tile_w(c->storage) : kind == 3 ? fused3_tile_w() : kTileX;
     int z0 = 0;
     for (int len : plan) {
         for (int y0 = 0; y0 < c->ny; y0 += tile_y)
@@ -181,7 +185,9 @@ void append_tiles_plan(std::vector<TileRec> &v, const fdtd_ctx *c, int parity_of
                 t.y0 = y0;
                 t.kz0 = z0;
                 t.kz1 = z0 + len;
-                t.id_x0 = (x0 - 2) & ~15;   // two-step kernel: 16-byte aligned origin of the id box
+                // two- and three-step kernels: 16-byte aligned origin of the id box (lane cells from x0 - 2,
+                // resp. x0 - 4)
+                t.id_x0 = (x0 - (kind == 3 ? 4 : 2)) & ~15;
                 v.push_back(t);
             }
         z0 += len;
@@ -224,9 +230,9 @@ int build_tiles(fdtd_ctx *c, int kind) {
     if (tl.key == s.tile_y && tl.d && tl.grid) return FDTD_OK;
     int rc = encode_maps(c, kind, s.tile_y + (kind == 0 ? 2 : kind == 1 ? 4 : 6));
     if (rc) return rc;
-    const int tw = kind == 1 ? fused2_tile_w(c->storage) : kTileX;
+    const int tw = kind == 1 ? fused2_tile_w(c->storage) : kind == 3 ? fused3_tile_w() : kTileX;
     const long long cols = (long long)((c->nx + tw - 1) / tw) * ((c->ny + s.tile_y - 1) / s.tile_y);
-    const int prologue = kind == 0 ? 1 : kind == 1 ? 3 : 4;
+    const int prologue = kind == 0 ? 1 : kind == 1 ? 3 : kind == 3 ? 5 : 4;
     const int G = (int)std::min<long long>((long long)num_sms() * s.ctas_per_sm, cols * c->nz);
     std::vector<TileRec> listed, v;
     std::vector<int> first;

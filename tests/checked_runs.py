@@ -10,11 +10,12 @@ import numpy as np
 import cavity_inputs as ci
 
 DT = ci.COURANT_HALF_DT
-# sizes around the tile edges of the fused kernels (64 and 60 cells in x, 4..16 rows in y)
+# sizes around the tile edges of the fused kernels (64, 60 and 58 cells in x, 4..16 rows in y)
 DIMS = [(1, 3, 2), (7, 9, 11), (61, 13, 5), (64, 8, 3), (65, 17, 9), (121, 40, 7), (130, 67, 12), (2, 70, 5)]
 TUNINGS = [dict(kernel=1), dict(kernel=2, tile_y=4), dict(kernel=2, tile_y=16, zchunk=3),
            dict(kernel=3, tile_y=8), dict(kernel=3, tile_y=12, zchunk=2, stages=3), dict(kernel=3, tile_y=16),
-           dict(kernel=4, tile_y=12, zchunk=2, stages=3), dict(kernel=4, tile_y=16)]
+           dict(kernel=4, tile_y=12, zchunk=2, stages=3), dict(kernel=4, tile_y=16),
+           dict(kernel=5, tile_y=8, zchunk=2, stages=3), dict(kernel=5, tile_y=12)]
 TUNINGS4 = [dict(kernel=1), dict(kernel=2, tile_y=4, stages=4), dict(kernel=2, tile_y=8, zchunk=3),
             dict(kernel=2, tile_y=12), dict(kernel=2, tile_y=16, stages=5)]
 

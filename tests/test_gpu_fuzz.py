@@ -20,8 +20,8 @@ def _case(seed):
     steps = int(rng.integers(1, 14))
     coef = str(rng.choice(["vacuum", "spheres", "table"]))
     if order == 2:
-        kernel = int(rng.choice([2, 3, 4]))
-        tile_y = int(rng.choice({2: [4, 8, 16], 3: [8, 12, 16], 4: [12, 16]}[kernel]))
+        kernel = int(rng.choice([2, 3, 4, 5]))
+        tile_y = int(rng.choice({2: [4, 8, 16], 3: [8, 12, 16], 4: [12, 16], 5: [8, 10, 12]}[kernel]))
         stages = int(rng.integers(3, 9))
     else:
         kernel = 2

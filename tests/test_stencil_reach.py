@@ -7,6 +7,7 @@ of s steps, so a stored value never needs an input outside its box:
   one-step kernel (Eq. 2)        s = 1, R = 1   box rows tile_y + 2
   two-step kernel (Eq. 2 twice)  s = 2, R = 2   box rows tile_y + 4
   fourth-order kernel            s = 1, R = 3   box rows tile_y + 6
+  three-step kernel              s = 3, R = 3   box rows tile_y + 6 (the same branch as the fourth order)
 
 The reach is also tight (some output does depend on a cell R away), so none of the boxes could be
 smaller.  The box heights are read from the host code that encodes the tensor maps."""
@@ -44,7 +45,7 @@ def reach(order, steps):
     return tuple(int(v) for v in out)
 
 
-@pytest.mark.parametrize("order,steps,expected", [(2, 1, 1), (2, 2, 2), (4, 1, 3), (4, 2, 6)])
+@pytest.mark.parametrize("order,steps,expected", [(2, 1, 1), (2, 2, 2), (2, 3, 3), (4, 1, 3), (4, 2, 6)])
 def test_reach_of_the_schemes(order, steps, expected):
     assert reach(order, steps) == (expected,) * 3
 
@@ -57,3 +58,5 @@ def test_box_heights_cover_the_reach_exactly():
     assert one_step == 2 * reach(2, 1)[1]
     assert two_step == 2 * reach(2, 2)[1]
     assert fourth == 2 * reach(4, 1)[1]
+    # kind 3 (three steps per launch) takes the last branch too
+    assert fourth == 2 * reach(2, 3)[1]
