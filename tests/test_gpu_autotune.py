@@ -24,8 +24,8 @@ def test_autotune_keeps_state_and_result():
         cav.step(3)
         before = cav.get_fields()
         tuning, ms = cav.autotune(16)
-        assert tuning["kernel"] in (2, 3) and ms > 0
-        assert tuning["tile_y"] in ((4, 8, 16) if tuning["kernel"] == 2 else (8, 12, 16))
+        assert tuning["kernel"] in (2, 3, 4, 5) and ms > 0
+        assert tuning["tile_y"] in {2: (4, 8, 16), 3: (8, 12, 16), 4: (12, 16), 5: (8, 10, 12)}[tuning["kernel"]]
         assert cav.steps_done == 3
         for x, y in zip(cav.get_fields(), before):
             assert np.array_equal(x, y)
@@ -69,7 +69,7 @@ def test_batch_autotune_keeps_members():
     binding.fdtd_batch_set_steps(b, mem[0][0].handle, 7)   # one member stops during the trials
     binding.fdtd_batch_step(b, 5)
     tuning, ms = binding.fdtd_batch_autotune(b, 16)
-    assert tuning["kernel"] in (2, 3) and ms > 0
+    assert tuning["kernel"] in (2, 3, 4) and ms > 0      # batches: no three-step kernel
     assert binding.fdtd_batch_steps_done(b) == 5
     binding.fdtd_batch_step(b, 19)
     binding.fdtd_batch_destroy(b)
@@ -105,7 +105,7 @@ def test_batch_retune_uses_the_size_bucket_model():
             binding.fdtd_batch_add(b, c.handle)
         binding.fdtd_batch_step(b, 3)
         t1, ms1, _ = binding.fdtd_batch_retune(b, 16)
-        assert t1["kernel"] in (2, 3) and ms1 > 0
+        assert t1["kernel"] in (2, 3, 4) and ms1 > 0
         t2, ms2, timed2 = binding.fdtd_batch_retune(b, 16)
         assert not timed2 and t2 == t1 and ms2 == ms1
         assert binding.fdtd_batch_steps_done(b) == 3
