@@ -16,8 +16,10 @@ pytestmark = pytest.mark.gpu
 
 CASES = [
     # (order, kernel tuning, ghost): two-step kernel with 2 ghost cells (one launch per exchange), the same
-    # with 4 (two launches), one-step kernel with 1, two rows per warp, fourth order with 3 and 6
+    # with 4 (two launches), one-step kernel with 1, two rows per warp, the three-step kernel with 3 (one
+    # launch per exchange), fourth order with 3 and 6
     (2, {"kernel": 3, "tile_y": 16}, 2),
+    (2, {"kernel": 5, "tile_y": 10}, 3),
     (2, {"kernel": 3, "tile_y": 8, "use_graph": 1}, 4),
     (2, {"kernel": 2, "tile_y": 8}, 1),
     (2, {"kernel": 4, "tile_y": 16}, 2),
