@@ -138,21 +138,25 @@ def test_fullsize_reductions_match_oracle_on_the_stored_state(workload):
 
 
 def test_512_two_step_equals_one_step_bitwise():
-    """The bench's launch configuration (two-step kernel) against the one-step kernel at full size."""
+    """The bench's launch configuration (two-step kernel) and the three-step kernel against the one-step
+    kernel at full size."""
     from paper_2504_09118_gb300 import Cavity
     w = bench.WORKLOADS["single512"]
     n = w["n"]
     ce, ch = bench.sphere_coefs(w)
     f = ci.random_fields(w["field_seed"], *n)
     out = []
-    for tuning in (dict(kernel=2, tile_y=8, stages=4, use_graph=1), bench.BENCH_TUNING):
+    # one-step kernel, the bench's two-step kernel, the three-step kernel (18 steps in a graph, 2 direct)
+    for tuning in (dict(kernel=2, tile_y=8, stages=4, use_graph=1), bench.BENCH_TUNING,
+                   dict(kernel=5, tile_y=12, use_graph=1)):
         with Cavity(*n, DT, 1.0, ce, ch) as cav:
             cav.tune(**tuning)
             cav.set_fields(f)
             cav.step(20)
             out.append(cav.get_fields())
-    for name, x, y in zip(ci.COMPONENTS, *out):
+    for name, x, y, z in zip(ci.COMPONENTS, *out):
         assert np.array_equal(x, y), name
+        assert np.array_equal(x, z), name
 
 
 @pytest.fixture(scope="module")
