@@ -140,7 +140,8 @@ struct fdtd_batch {
     long long launches = 0;          // launches enqueued so far; the next launch has parity launches & 1
     long long *d_step = nullptr;     // device copy of the step clock (advanced by a kernel after each launch)
     fdtd_tuning tuning{};
-    TileRec *d_tiles = nullptr;
+    TileRec *d_tiles = nullptr;      // tile records, then (at d_first) the per-CTA range offsets
+    int *d_first = nullptr;          // grid + 1 offsets when the tiles are assigned to CTAs on the host, else NULL
     int tiles_cap = 0, ntiles = 0, grid = 0;
     bool dirty = true;
     int *d_status = nullptr;

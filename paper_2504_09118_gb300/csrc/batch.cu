@@ -180,21 +180,34 @@ static int batch_rebuild(fdtd_batch *b) {
         append_tiles(tiles, mb.c, mb.cur0 ^ (int)(mb.join_launch & 1), s.tile_y, std::min(zlen, mb.c->nz), kind);
         for (size_t q = first; q < tiles.size(); ++q) tiles[q].stop = mb.stop;
     }
-    // longest tiles first, then round-robin over the persistent CTAs
+    // longest tiles first; with one CTA per SM each tile then goes to the CTA that frees first (host-balanced
+    // contiguous ranges, as for a single cavity), with co-resident CTAs round-robin
     std::stable_sort(tiles.begin(), tiles.end(),
                      [](const TileRec &a, const TileRec &c) { return (a.kz1 - a.kz0) > (c.kz1 - c.kz0); });
-    if ((int)tiles.size() > b->tiles_cap) {
+    const int grid = std::min((int)tiles.size(), G);
+    std::vector<int> first;
+    if (s.ctas_per_sm == 1 && !tiles.empty())
+        tiles = assign_tiles(tiles, grid, kind == 0 ? 1 : kind == 1 ? 3 : 4, first);
+    if ((int)tiles.size() > b->tiles_cap || !b->d_tiles) {
         pool_free(b->d_tiles, b->stream);
         b->d_tiles = nullptr;
         b->tiles_cap = std::max<int>((int)tiles.size(), 2 * b->tiles_cap);
-        if (pool_alloc((void **)&b->d_tiles, sizeof(TileRec) * b->tiles_cap, b->stream) != cudaSuccess)
-            return bfail(b, FDTD_ERR_OOM, "tile list alloc");
+        // room for the records and for the range offsets of up to two CTAs per SM
+        const size_t bytes = sizeof(TileRec) * b->tiles_cap + sizeof(int) * (2 * num_sms() + 1);
+        if (pool_alloc((void **)&b->d_tiles, bytes, b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_OOM, "tile list alloc");
     }
     if (!tiles.empty() && cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(TileRec) * tiles.size(),
                                           cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
         return bfail(b, FDTD_ERR_CUDA, "tile list upload");
+    b->d_first = nullptr;
+    if (!first.empty()) {
+        b->d_first = reinterpret_cast<int *>(b->d_tiles + b->tiles_cap);
+        if (cudaMemcpyAsync(b->d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice,
+                            b->stream) != cudaSuccess)
+            return bfail(b, FDTD_ERR_CUDA, "tile range upload");
+    }
     b->ntiles = (int)tiles.size();
-    b->grid = std::min(b->ntiles, G);
+    b->grid = grid;
     b->dirty = false;
     return FDTD_OK;
 }
@@ -205,6 +218,7 @@ static int batch_launch(fdtd_batch *b, int parity, int nsteps) {
     Shape s = resolve_shape(b->storage, b->tuning, kind);
     FusedLaunch L{};
     L.recs = b->d_tiles;
+    L.first = b->d_first;
     L.step = b->d_step;
     L.ntiles = b->ntiles;
     L.parity = parity;
