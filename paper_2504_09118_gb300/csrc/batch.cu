@@ -180,13 +180,23 @@ static int batch_rebuild(fdtd_batch *b) {
         append_tiles(tiles, mb.c, mb.cur0 ^ (int)(mb.join_launch & 1), s.tile_y, std::min(zlen, mb.c->nz), kind);
         for (size_t q = first; q < tiles.size(); ++q) tiles[q].stop = mb.stop;
     }
-    // longest tiles first; with one CTA per SM each tile then goes to the CTA that frees first (host-balanced
-    // contiguous ranges, as for a single cavity), with co-resident CTAs round-robin
+    // Longest tiles first.  When every running member stops at the same clock (or never), every tile takes
+    // part in every launch, and with one CTA per SM each tile goes to the CTA that frees first (host-balanced
+    // contiguous ranges, as for a single cavity).  Otherwise (members with their own step counts, as in
+    // serving) tiles drop out at different clocks and the round-robin deal spreads the holes over the CTAs;
+    // co-resident CTAs always take their tiles round-robin.
     std::stable_sort(tiles.begin(), tiles.end(),
                      [](const TileRec &a, const TileRec &c) { return (a.kz1 - a.kz0) > (c.kz1 - c.kz0); });
     const int grid = std::min((int)tiles.size(), G);
+    bool same_stop = true;
+    long long stop0 = -1;
+    for (auto &mb : b->members) {
+        if (mb.stop <= b->step) continue;
+        if (stop0 < 0) stop0 = mb.stop;
+        same_stop = same_stop && mb.stop == stop0;
+    }
     std::vector<int> first;
-    if (s.ctas_per_sm == 1 && !tiles.empty())
+    if (s.ctas_per_sm == 1 && same_stop && !tiles.empty())
         tiles = assign_tiles(tiles, grid, kind == 0 ? 1 : kind == 1 ? 3 : 4, first);
     if ((int)tiles.size() > b->tiles_cap || !b->d_tiles) {
         pool_free(b->d_tiles, b->stream);
