@@ -87,9 +87,10 @@ enum fdtd_kernel {
 /* Launch configuration of the step kernel; zero fields take the default. */
 typedef struct fdtd_tuning {
     int kernel;       /* enum fdtd_kernel */
-    int tile_y;       /* fused: cells per tile along y (FUSED: 4, 8 or 16; TEMPORAL: 8, 12 or 16; AUTO: any
-                         of these, each kernel taking its default when the value is not one of its
-                         own); x tile is 64 cells (TEMPORAL, TEMPORAL2: 60) */
+    int tile_y;       /* fused: cells per tile along y (FUSED: 4, 8 or 16, fourth order also 12; TEMPORAL:
+                         8, 12 or 16; TEMPORAL2: 12 or 16; TEMPORAL3: 8, 10 or 12; AUTO: any of these,
+                         each kernel taking its default when the value is not one of its own); x tile is
+                         64 cells (TEMPORAL, TEMPORAL2: 60; TEMPORAL3: 58) */
     int zchunk;       /* fused: planes per tile along z (>= 1); 0 = choose for load balance */
     int ctas_per_sm;  /* fused: persistent CTAs per SM (1 or 2); 0 = as many as fit */
     int stages;       /* fused: TMA pipeline depth in planes (3..8, lowered to fit shared memory); 0 = default */
@@ -191,7 +192,8 @@ FDTD_API int fdtd_divergence(fdtd_ctx *ctx, double *divE_l2, double *divH_l2);
 FDTD_API int fdtd_sync(fdtd_ctx *ctx);
 
 /* fdtd_set_tuning - choose the step kernel and its launch shape (NULL = defaults).  With spatial
- * order 4 (fdtd_set_order) kernel TEMPORAL and stages = 3 are FDTD_ERR_ARG. */
+ * order 4 (fdtd_set_order) the kernels TEMPORAL, TEMPORAL2 and TEMPORAL3 and stages = 3 are FDTD_ERR_ARG;
+ * so is a tile_y the chosen kernel does not take. */
 FDTD_API int fdtd_set_tuning(fdtd_ctx *ctx, const fdtd_tuning *t);
 
 /*
