@@ -223,8 +223,8 @@ FDTD_API int fdtd_get_order(const fdtd_ctx *ctx);
 
 /* fdtd_autotune - choose the step kernel and launch shape by timing candidates on this
  * context's own state: the one-step kernel with 4, 8, 16-row tiles, the two-step kernel with
- * 8, 12, 16-row tiles and 4 or 6 ring slots, and the two-step kernel with two rows per warp with
- * 12 and 16-row tiles (graphs on).  Each candidate runs trial_steps steps
+ * 8, 12, 16-row tiles and 4 or 6 ring slots, the three-step kernel with 8, 10, 12-row tiles, and the
+ * two-step kernel with two rows per warp with 12 and 16-row tiles (graphs on).  Each candidate runs trial_steps steps
  * (rounded up to a multiple of 16; <= 0: 16) after one untimed run of the same length, timed
  * with CUDA events on the context's stream.  The fields are copied aside first (one extra copy
  * of the active arrays, freed before return) and restored afterwards, so the state and
@@ -307,8 +307,10 @@ FDTD_API long long fdtd_batch_steps_done(const fdtd_batch *b);
  * result is bit-identical to stepping it alone with FP32 storage. */
 FDTD_API int fdtd_batch_step(fdtd_batch *b, int nsteps);
 
-/* fdtd_batch_set_tuning - launch shape for the batch kernel: FUSED (or AUTO: one step per launch)
- * or TEMPORAL (two steps per launch); may change between fdtd_batch_step calls. */
+/* fdtd_batch_set_tuning - launch shape for the batch kernel: FUSED (one step per launch) or TEMPORAL,
+ * TEMPORAL2 or AUTO (two steps per launch; TEMPORAL3 is for single cavities: FDTD_ERR_ARG); may change
+ * between fdtd_batch_step calls.  With one CTA per SM and every running member stopping at the same
+ * clock, tiles are assigned to the CTAs on the host for balance; otherwise they are dealt round-robin. */
 FDTD_API int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t);
 
 /* fdtd_batch_autotune - fdtd_autotune for a batch over its current members: the one-step kernel
