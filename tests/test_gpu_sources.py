@@ -39,7 +39,8 @@ def setup():
 
 
 @pytest.mark.parametrize("tuning", [dict(kernel=1), dict(kernel=2, use_graph=0), dict(kernel=2, use_graph=1),
-                                    dict(kernel=3, use_graph=1)])
+                                    dict(kernel=3, use_graph=1), dict(kernel=4, use_graph=1),
+                                    dict(kernel=5, use_graph=1)])
 def test_currents_and_probes_match_oracle(tuning):
     from paper_2504_09118_gb300 import Cavity
     ce, ch, f, waves = setup()
@@ -127,3 +128,24 @@ def test_recording_restarts_and_bad_arguments():
         cav.set_probes([], 1)
         cav.set_sources([], [])
         cav.autotune()                       # allowed again
+
+
+@pytest.mark.parametrize("kernel", [3, 5])
+def test_multi_step_kernels_resume_after_currents(kernel):
+    """While currents are set a multi-step tuning steps one step per launch; removing them resumes the two-
+    or three-step launches.  With FP32 storage both give the one-step kernel's values bit for bit."""
+    from paper_2504_09118_gb300 import Cavity
+    ce, ch, f, waves = setup()
+    runs = []
+    for k in (2, kernel):
+        with Cavity(*DIMS, DT, 1.0, ce, ch) as cav:
+            cav.tune(kernel=k, use_graph=1)
+            cav.set_fields(f)
+            cav.set_sources(SOURCES, waves)
+            cav.step(31)
+            cav.set_sources([], [])
+            cav.step(38)
+            assert cav.steps_done == 69
+            runs.append(cav.get_fields())
+    for name, a, b in zip(ci.COMPONENTS, *runs):
+        assert np.array_equal(a, b), name
