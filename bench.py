@@ -63,9 +63,13 @@ WORKLOADS = {
     # the fourth-order (2,4) scheme on the single512 cavity (fused fourth-order kernel, one step per launch)
     "order4_512": dict(n=(512, 512, 512), steps=200, storage=0, sphere_seed=1, field_seed=2, spheres=32, order=4,
                        tuning=dict(kernel=2, tile_y=12, stages=5, zchunk=0, ctas_per_sm=0, use_graph=1)),
-    # small case of the same for ncu captures
+    "order4_512_f16": dict(n=(512, 512, 512), steps=200, storage=1, sphere_seed=1, field_seed=2, spheres=32, order=4,
+                           tuning=dict(kernel=2, tile_y=12, stages=5, zchunk=0, ctas_per_sm=0, use_graph=1)),
+    # small case of the same for ncu captures (FP32 and FP16 storage)
     "order4_256": dict(n=(256, 256, 256), steps=20, storage=0, sphere_seed=1, field_seed=2, spheres=8, order=4,
                        tuning=dict(kernel=2, tile_y=12, stages=5, zchunk=0, ctas_per_sm=0, use_graph=1)),
+    "order4_256_f16": dict(n=(256, 256, 256), steps=20, storage=1, sphere_seed=1, field_seed=2, spheres=8, order=4,
+                           tuning=dict(kernel=2, tile_y=12, stages=5, zchunk=0, ctas_per_sm=0, use_graph=1)),
 }
 # Launch configuration the bench times (the full-size parity test uses the same): the two-step
 # temporal-blocking kernel, 60 x 16-cell tiles (FP32), 4-slot TMA ring (what fits beside 16-row
@@ -91,13 +95,14 @@ MEASURED_TRAFFIC = {
 }
 
 
-TUNING_OVERRIDE: dict | None = None   # --tuning: the single-cavity launch configuration to time instead
+TUNING_OVERRIDE: dict | None = None   # --tuning: fields of the single-cavity launch configuration to replace
 
 
 def tuning_of(w) -> dict:
+    base = w.get("tuning", BENCH_TUNING)
     if TUNING_OVERRIDE is not None:
-        return dict(BENCH_TUNING, **TUNING_OVERRIDE)
-    return w.get("tuning", BENCH_TUNING)
+        return dict(base, **TUNING_OVERRIDE)
+    return base
 
 
 def dominant_kernel(w) -> str:
@@ -555,8 +560,8 @@ def main():
                     help="comma-separated legs nested in the single-cavity line at N = 1 (batched: 256 uneven "
                          "cavities; served: the 10k-request Poisson stream; precision: 384^3 FP16/BF16); '' for none")
     ap.add_argument("--tuning", default=None,
-                    help="JSON launch configuration of the single-cavity workloads (default: BENCH_TUNING or "
-                         "the workload's own)")
+                    help="JSON fields replacing those of the single-cavity workload's launch configuration (its "
+                         "own, else BENCH_TUNING)")
     args = ap.parse_args()
     global TUNING_OVERRIDE
     if args.tuning:
