@@ -381,8 +381,8 @@ def run_serve(args, w):
     tuning = json.loads(args.serve_tuning) if args.serve_tuning else SERVE_TUNING
 
     def make_server(retune=False):
-        return Server(ci.COURANT_HALF_DT, hbm_budget_bytes=int(w["budget_gb"] * (1 << 30)), max_slots=1024, K=16,
-                      tuning=tuning, result="energy", fields_fn=fields_fn, retune=retune)
+        return Server(ci.COURANT_HALF_DT, hbm_budget_bytes=int(w["budget_gb"] * (1 << 30)), max_slots=1024,
+                      K=args.serve_chunk, tuning=tuning, result="energy", fields_fn=fields_fn, retune=retune)
 
     # untimed warm-up: a short stream of the same recipe (another seed) through a server of its own, so
     # that library load, pool growth, tensor maps and graph captures are not charged to the timed stream
@@ -422,7 +422,7 @@ def run_serve(args, w):
             "dtype": "f32 or bf16-storage per request", "data": "synthetic",
             "config": {"workload": "serve", "requests": len(stream), "rate_hz": w["rate"],
                        "sides": "log-uniform 16-256 per axis", "steps": "U{100..2000}", "bf16": "Bernoulli(1/2)",
-                       "budget_gb": w["budget_gb"], "graph_steps": 16, "tuning": tuning, "max_slots": 1024,
+                       "budget_gb": w["budget_gb"], "graph_steps": args.serve_chunk, "tuning": tuning, "max_slots": 1024,
                        "warmup_requests": len(warm), "seed": w["seed"]},
             "serving": {"p50_s": round(st.p50_s, 4), "p99_s": round(st.p99_s, 4), "mean_s": round(st.mean_s, 4),
                         "wall_s": round(st.wall_s, 3), "max_active": st.max_active,
@@ -549,6 +549,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clocks-csv", default=None)
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-chunk", type=int, default=32,
+                    help="serving: steps each batch advances per pass of the loop (one graph replay when a multiple of 16)")
     ap.add_argument("--serve-seq-requests", type=int, default=1000,
                     help="closed-loop prefix of the stream served by the sequential baseline")
     ap.add_argument("--serve-tuning", default=None,
