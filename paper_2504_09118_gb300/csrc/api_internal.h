@@ -143,6 +143,12 @@ struct fdtd_batch {
     TileRec *d_tiles = nullptr;      // tile records, then (at d_first) the per-CTA range offsets
     int *d_first = nullptr;          // grid + 1 offsets when the tiles are assigned to CTAs on the host, else NULL
     int tiles_cap = 0, ntiles = 0, grid = 0;
+    // pinned staging of the tile-list uploads, two buffers used in turn: a copy from pageable memory may
+    // wait for the stream, which would drain the queued launches at every change of membership
+    void *h_stage[2] = {nullptr, nullptr};
+    size_t h_stage_cap[2] = {0, 0};
+    cudaEvent_t h_stage_ev[2] = {nullptr, nullptr};   // recorded after each buffer's last upload
+    int h_stage_next = 0;
     bool dirty = true;
     int *d_status = nullptr;
     cudaEvent_t done_ev = nullptr;   // recorded at member removal; the member's stream waits on it
@@ -152,7 +158,9 @@ struct fdtd_batch {
     std::deque<std::pair<long long, cudaEvent_t>> marks;
     std::vector<cudaEvent_t> free_marks;
     std::map<fdtd::GraphKey, cudaGraphExec_t> graphs;
-    std::vector<cudaGraphExec_t> retired_graphs;   // destroyed at the next synchronisation point
+    // (batch clock when retired, graph): destroyed once a completion mark at or past that clock has passed,
+    // or at the next synchronisation point
+    std::vector<std::pair<long long, cudaGraphExec_t>> retired_graphs;
     std::string err;
 };
 

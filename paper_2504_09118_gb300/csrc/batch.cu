@@ -129,13 +129,26 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t) {
 }
 
 static void batch_retire_graphs(fdtd_batch *b) {
-    for (auto &kv : b->graphs) b->retired_graphs.push_back(kv.second);
+    for (auto &kv : b->graphs) b->retired_graphs.emplace_back(b->step, kv.second);
     b->graphs.clear();
 }
 
 static void batch_free_retired_graphs(fdtd_batch *b) {   // call only when the batch stream is idle
-    for (cudaGraphExec_t g : b->retired_graphs) cudaGraphExecDestroy(g);
+    for (auto &rg : b->retired_graphs) cudaGraphExecDestroy(rg.second);
     b->retired_graphs.clear();
+}
+
+// Destroys the retired graphs whose last launches are done: a graph retired at clock c was last launched
+// before the completion mark at clock c was recorded.
+static void batch_free_finished_graphs(fdtd_batch *b, long long done_clock) {
+    size_t keep = 0;
+    for (size_t q = 0; q < b->retired_graphs.size(); ++q) {
+        if (b->retired_graphs[q].first <= done_clock)
+            cudaGraphExecDestroy(b->retired_graphs[q].second);
+        else
+            b->retired_graphs[keep++] = b->retired_graphs[q];
+    }
+    b->retired_graphs.resize(keep);
 }
 
 // Tile kind of the batch's launches: 2 (the fused fourth-order kernel) for a fourth-order batch whatever the
@@ -206,16 +219,36 @@ static int batch_rebuild(fdtd_batch *b) {
         const size_t bytes = sizeof(TileRec) * b->tiles_cap + sizeof(int) * (2 * num_sms() + 1);
         if (pool_alloc((void **)&b->d_tiles, bytes, b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_OOM, "tile list alloc");
     }
-    if (!tiles.empty() && cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(TileRec) * tiles.size(),
-                                          cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    // upload through the pinned staging buffer whose previous upload (two rebuilds ago) has finished
+    const size_t rec_bytes = sizeof(TileRec) * tiles.size(), first_bytes = sizeof(int) * first.size();
+    const int si = b->h_stage_next;
+    b->h_stage_next ^= 1;
+    if (b->h_stage_ev[si]) {
+        if (cudaEventSynchronize(b->h_stage_ev[si]) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "staging wait");
+    } else if (cudaEventCreateWithFlags(&b->h_stage_ev[si], cudaEventDisableTiming) != cudaSuccess) {
+        return bfail(b, FDTD_ERR_CUDA, "event create");
+    }
+    if (b->h_stage_cap[si] < rec_bytes + first_bytes) {
+        cudaFreeHost(b->h_stage[si]);
+        b->h_stage[si] = nullptr;
+        b->h_stage_cap[si] = 0;
+        const size_t cap = std::max(rec_bytes + first_bytes, 2 * b->h_stage_cap[si ^ 1]);
+        if (cudaMallocHost(&b->h_stage[si], cap) != cudaSuccess) return bfail(b, FDTD_ERR_OOM, "pinned staging alloc");
+        b->h_stage_cap[si] = cap;
+    }
+    char *stage = static_cast<char *>(b->h_stage[si]);
+    if (rec_bytes) memcpy(stage, tiles.data(), rec_bytes);
+    if (first_bytes) memcpy(stage + rec_bytes, first.data(), first_bytes);
+    if (rec_bytes && cudaMemcpyAsync(b->d_tiles, stage, rec_bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
         return bfail(b, FDTD_ERR_CUDA, "tile list upload");
     b->d_first = nullptr;
-    if (!first.empty()) {
+    if (first_bytes) {
         b->d_first = reinterpret_cast<int *>(b->d_tiles + b->tiles_cap);
-        if (cudaMemcpyAsync(b->d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice,
-                            b->stream) != cudaSuccess)
+        if (cudaMemcpyAsync(b->d_first, stage + rec_bytes, first_bytes, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess)
             return bfail(b, FDTD_ERR_CUDA, "tile range upload");
     }
+    if (cudaEventRecord(b->h_stage_ev[si], b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "event record");
     b->ntiles = (int)tiles.size();
     b->grid = grid;
     b->dirty = false;
@@ -297,10 +330,13 @@ int fdtd_batch_step(fdtd_batch *b, int nsteps) {
         left -= n;
     }
     // completion mark at the new clock; marks whose work has finished are recycled (the newest stays)
+    long long done_clock = -1;
     while (b->marks.size() > 1 && cudaEventQuery(b->marks.front().second) == cudaSuccess) {
+        done_clock = b->marks.front().first;
         b->free_marks.push_back(b->marks.front().second);
         b->marks.pop_front();
     }
+    if (done_clock >= 0 && !b->retired_graphs.empty()) batch_free_finished_graphs(b, done_clock);
     cudaEvent_t ev = nullptr;
     if (!b->free_marks.empty()) {
         ev = b->free_marks.back();
@@ -338,6 +374,10 @@ void fdtd_batch_destroy(fdtd_batch *b) {
     pool_free(b->d_status, b->stream);
     pool_free(b->d_step, b->stream);
     cudaStreamSynchronize(b->stream);
+    for (int q = 0; q < 2; ++q) {
+        cudaFreeHost(b->h_stage[q]);
+        if (b->h_stage_ev[q]) cudaEventDestroy(b->h_stage_ev[q]);
+    }
     cudaEventDestroy(b->done_ev);
     for (auto &mk : b->marks) cudaEventDestroy(mk.second);
     for (cudaEvent_t e : b->free_marks) cudaEventDestroy(e);
