@@ -192,6 +192,7 @@ int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind) {
     L.inject_timeout_us = inject_us;
     L.first = tl.first;
     L.rows_per_warp = s.rows_per_warp;
+    L.coef_class = coef_class_of(c->coef_mode, c->ch_uniform);
     if (kind == 0)
         CK(c, launch_fused_step(c->storage, L, c->stream));
     else if (kind == 1)

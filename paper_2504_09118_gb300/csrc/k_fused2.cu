@@ -23,6 +23,8 @@
 // E1 and H2 need no barrier between them.  A producer warp streams plane units (six field boxes with a 2-cell halo in y, id box) through an
 // S-slot TMA ring exactly as the one-step kernel does; waits are bounded and a shared
 // abort flag ends the CTA together (see k_fused.cu).
+#include <type_traits>
+
 #include "fused_common.cuh"
 #include "launch.h"
 
@@ -84,8 +86,10 @@ template <typename T, int TY> __host__ __device__ constexpr int smem2_bytes(int 
 template <int TY> __host__ __device__ constexpr int threads2() { return (TY + 4) * 32; }
 
 // BATCH: tiles carry their member's stop clock (skip finished members, one-step stores for a member
-// with one step left); a single cavity's launch compiles without those checks.
-template <typename T, int TY, bool BATCH>
+// with one step left); a single cavity's launch compiles without those checks.  CM: the CoefClass of
+// every tile (COEF_CLASS_ANY reads each record's mode), so that a single cavity's kernel carries no
+// per-plane test of its coefficient layout.
+template <typename T, int TY, bool BATCH, int CM>
 __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fused2Params P) {
     using G = Geom2<T>;
     constexpr int BX = G::BX, W = G::W;
@@ -93,6 +97,10 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
     static_assert(FB % 16 == 0 && FE % 2 == 0, "field boxes keep 16-byte rows and even-aligned pairs");
     constexpr int NCW = TY + 3, NCT = NCW * 32;
     constexpr int PF = plane_floats<TY>();
+    // the steady-state plane body (below) for launches of one coefficient layout; a batch, whose
+    // instance also carries the stop-clock logic, runs every plane through the general body, which
+    // needs fewer registers (no spill at 16 rows)
+    constexpr bool SPLIT = !BATCH && CM != COEF_CLASS_ANY;
 
     extern __shared__ __align__(128) unsigned char smem[];
     if (smem_u32(smem) & 127u) {
@@ -162,7 +170,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 const int kk = kb + k;
                 if (lane == 0) {
                     const int src_copy = P.parity ^ rec->parity_off;
-                    const bool has_id = rec->mode == COEF_ID8;
+                    const bool has_id = CM == COEF_CLASS_ANY ? rec->mode == COEF_ID8 : CM >= COEF_CLASS_ID_UNIFORM_H;
                     unsigned char *dst = slots + s * SB;
                     fence_proxy_async_smem();
                     if (tma_x_ok(P.status, G::box_x(rec->x0), (int)sizeof(T)) &&
@@ -209,8 +217,8 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
 
     for (int t = t_begin; t < t_end; t += t_step) {
         if (BATCH && __ldg(&P.recs[t].stop) <= clock) continue;   // same skip rule as the producer
-        bool ok = wait_full(sa, pa);
-        if (bar_sync_or(2, NCT, !ok || *abort_flag != 0)) {
+        bool ok0 = wait_full(sa, pa);
+        if (bar_sync_or(2, NCT, !ok0 || *abort_flag != 0)) {
             if (threadIdx.x == 0) atomicOr(P.status, STATUS_TIMEOUT);
             return;
         }
@@ -219,8 +227,8 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         const int bx = (x0 - 2) - G::box_x(x0) + 2 * lane;   // box column of the lane's first cell
         const int nx = rec->nx, ny = rec->ny, nz = rec->nz;
         const long long pitch = rec->pitch, plane = rec->plane;
-        const bool id_mode = rec->mode == COEF_ID8;
-        const bool ch_uni = rec->ch_uniform != 0;
+        const bool id_mode = CM == COEF_CLASS_ANY ? rec->mode == COEF_ID8 : CM >= COEF_CLASS_ID_UNIFORM_H;
+        const bool ch_uni = CM == COEF_CLASS_ANY ? rec->ch_uniform != 0 : CM != COEF_CLASS_ID;
         const int idoff = x0 - 2 - rec->id_x0;   // lane cells start this many bytes into the id box
         if (id_mode && rec->table != tab_cached) {
             const float4 *src = rec->table;
@@ -243,6 +251,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         const bool out_row = r >= 2 && r < TY + 2 && gj < ny;      // level-2 outputs of this row are stored
         const bool out_a = lane >= 1 && 2 * lane - 2 < W && gi < nx; // both cells share the column window
         const int kb = kz0 > 2 ? kz0 - 2 : 0;
+        // planes [ks, kz1) run every phase with no plane-dependent mask (k >= 1 for E1 and k - 1 >= 1 for
+        // E2, k < nz, not the tile's last plane); the planes before ks and the last plane kz1 test them
+        const int ks = kz0 + 1 > 2 ? kz0 + 1 : 2;
         const bool level1_only = BATCH && (P.launch_steps == 1 || rec->stop - clock == 1);
 
         auto at = [&](const T *base, int f, int xx, int yy) { return base + f * FE + yy * BX + xx; };
@@ -259,8 +270,11 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         float2 h2px = zero2, h2py = zero2;                 // H2(j-2) (Hx, Hy)
         uint32_t idprev = 0;                               // material ids of plane j-1
 
-#pragma unroll 2   // consecutive planes renamed instead of copied (the carried z neighbours)
-        for (int k = kb; k <= kz1; ++k) {
+        // One z-plane iteration.  ST (steady): k in [ks, kz1), where every phase runs, no mask depends on
+        // k, and a failed ring wait only drops the stores: the phases then read a stale slot (in bounds)
+        // instead of being skipped, so nothing is zeroed or voted per plane.
+        auto plane_step = [&](const int k, auto steady) {
+            constexpr bool ST = decltype(steady)::value;
             int sb = sa + 1;
             uint32_t pb = pa;
             if (sb == S) {
@@ -268,20 +282,23 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 pb ^= 1u;
             }
             // unit k (slot sa) was waited for as the next unit of the previous plane, or at the tile start
-            ok = wait_full(sb, pb);
-            ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the phases below shuffle across lanes
+            bool ok = wait_full(sb, pb);
+            if (!ST) ok = __all_sync(0xffffffffu, ok);   // warp-uniform: the phases below shuffle across lanes
+            const bool run = ST || ok;
             const T *A = reinterpret_cast<const T *>(slots + sa * SB);
             const T *B = reinterpret_cast<const T *>(slots + sb * SB);
             const uint8_t *ida = slots + sa * SB + IDO;
             // H2(k-1) needs plane k-1 >= 0 (its inputs at plane -1 were never written)
-            const bool do_e1 = k >= kz0 - 1;
-            const bool do_h2 = !level1_only && k >= kz0 && k >= 1, do_e2 = !level1_only && k >= kz0 + 1;
+            const bool do_e1 = ST || k >= kz0 - 1;
+            const bool do_h2 = !level1_only && (ST || (k >= kz0 && k >= 1));
+            const bool do_e2 = !level1_only && (ST || k >= kz0 + 1);
             float *e1cur = e1b + (k & 1) * 2 * PF, *e1prv = e1b + ((k + 1) & 1) * 2 * PF;
 
             // ---------------- phase 1: H1(k) on the lane's two cells
-            float2 e0x = zero2, e0y = zero2, e0z = zero2, h1x_ = zero2, h1y_ = zero2, h1z_ = zero2;
+            float2 e0x, e0y, e0z, h1x_, h1y_, h1z_;
             uint32_t idpair = 0;
-            if (ok) {
+            if (!ST) e0x = e0y = e0z = h1x_ = h1y_ = h1z_ = zero2;
+            if (run) {
                 e0x = Pair<T>::ld(at(A, 0, bx, by));
                 e0y = Pair<T>::ld(at(A, 1, bx, by));
                 e0z = Pair<T>::ld(at(A, 2, bx, by));
@@ -308,15 +325,17 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
             asm volatile("bar.sync 1, %0;" ::"r"(NCT) : "memory");
 
             // ---------------- phase 2: E1(k) (zero outside the cavity: tangential at its far faces)
-            float2 e1x = zero2, e1y = zero2, e1z = zero2;
-            if (ok && do_e1 && r >= 1) {
+            // (in ST, a row that skips a phase leaves its pairs unset: no later phase of that row reads them)
+            float2 e1x, e1y, e1z;
+            if (!ST) e1x = e1y = e1z = zero2;
+            if (run && do_e1 && r >= 1) {
                 const float2 hx_ym = *reinterpret_cast<const float2 *>(sh1x + (pr - 1) * PW + pc);
                 const float2 hz_ym = *reinterpret_cast<const float2 *>(sh1z + (pr - 1) * PW + pc);
                 const float hz_xm = __shfl_up_sync(0xffffffffu, h1z_.y, 1);
                 const float hy_xm = __shfl_up_sync(0xffffffffu, h1y_.y, 1);
                 float4 ca, cb;
                 coef(idpair, 0, ca, cb);
-                const bool inz = k < nz, k1 = k >= 1, j1 = gj >= 1;
+                const bool inz = ST || k < nz, k1 = ST || k >= 1, j1 = gj >= 1;
                 const bool va = rowin && ina && inz, vb = rowin && inb && inz;
                 const bool i1a = gi >= 1;
                 const float2 cex = make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
@@ -329,7 +348,8 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 if (!vb) { e1x.y = 0.f; e1y.y = 0.f; e1z.y = 0.f; }
                 *reinterpret_cast<float2 *>(e1cur + pr * PW + pc) = e1x;
                 *reinterpret_cast<float2 *>(e1cur + PF + pr * PW + pc) = e1z;
-                if (level1_only && out_row && out_a && k >= kz0 && k < kz1) {   // one step: (H1, E1) is the result
+                // one step: (H1, E1) is the result
+                if (level1_only && ok && out_row && out_a && (ST || (k >= kz0 && k < kz1))) {
                     const long long g = (long long)k * plane + (long long)gj * pitch + gi;
                     if (store_ok(P.status, g, 2, plane * nz)) {
                         Pair<T>::st_cs(dst0 + g, e1x.x, e1x.y);
@@ -347,8 +367,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
             // buffer after the phase-3 -> 4 barrier of this iteration and the phase-1 -> 2 barrier of the next.
 
             // ---------------- phase 3: H2(k-1) = H1(k-1) - ch curl E1 (plane k-1, z+1 from plane k)
-            float2 h2x = zero2, h2y = zero2, h2z = zero2;
-            if (ok && do_h2 && r >= 1 && r <= TY + 1) {
+            float2 h2x, h2y, h2z;
+            if (!ST) h2x = h2y = h2z = zero2;
+            if (run && do_h2 && r >= 1 && r <= TY + 1) {
                 const float2 ex_y1 = *reinterpret_cast<const float2 *>(e1prv + (pr + 1) * PW + pc);
                 const float2 ez_y1 = *reinterpret_cast<const float2 *>(e1prv + PF + (pr + 1) * PW + pc);
                 const float ey_x2 = __shfl_down_sync(0xffffffffu, e1py.x, 1);
@@ -368,13 +389,13 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
             asm volatile("bar.sync 1, %0;" ::"r"(NCT) : "memory");
 
             // ---------------- phase 4: E2(k-1) = E1(k-1) + ce curl H2, and the level-2 stores
-            if (ok && do_e2 && out_row) {
+            if (run && do_e2 && out_row) {
                 const float2 hx_ym = *reinterpret_cast<const float2 *>(sh2x + (pr - 1) * PW + pc);
                 const float2 hz_ym = *reinterpret_cast<const float2 *>(sh2z + (pr - 1) * PW + pc);
                 float4 ca, cb;
                 coef(idprev, 0, ca, cb);
                 const int kk = k - 1;
-                const bool k1 = kk >= 1, j1 = gj >= 1, i1a = gi >= 1;
+                const bool k1 = ST || kk >= 1, j1 = gj >= 1, i1a = gi >= 1;
                 const float2 cex = make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
                 const float2 cey = make_float2((i1a && k1) ? ca.y : 0.f, k1 ? cb.y : 0.f);
                 const float2 cez = make_float2((i1a && j1) ? ca.z : 0.f, j1 ? cb.z : 0.f);
@@ -382,7 +403,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 const float2 e2y = fma2(cey, sub2(sub2(h2x, h2px), sub2(h2z, make_float2(h2z_xm, h2z.x))), e1py);
                 const float2 e2z = fma2(cez, sub2(sub2(h2y, make_float2(h2y_xm, h2y.x)), sub2(h2x, hx_ym)), e1pz);
                 const long long g = (long long)kk * plane + (long long)gj * pitch + gi;
-                if (out_a && store_ok(P.status, g, 2, plane * nz)) {
+                if (out_a && ok && store_ok(P.status, g, 2, plane * nz)) {
                     Pair<T>::st_cs(dst0 + g, e2x.x, e2x.y);
                     Pair<T>::st_cs(dst0 + g + 1 * fstride, e2y.x, e2y.y);
                     Pair<T>::st_cs(dst0 + g + 2 * fstride, e2z.x, e2z.y);
@@ -402,7 +423,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
             e1pz = e1z;
             idprev = idpair;
             // ---------------- release unit k (and k+1 after the last plane)
-            const bool last = k == kz1;
+            const bool last = !ST && k == kz1;
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&empty[sa]);
@@ -414,14 +435,24 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 sa = 0;
                 pa ^= 1u;
             }
+        };
+
+        for (int k = kb; k <= kz1;) {
+            if (SPLIT && k >= ks && k < kz1) {
+#pragma unroll 2   // consecutive planes renamed instead of copied (the carried z neighbours)
+                for (; k < kz1; ++k) plane_step(k, std::true_type{});
+            } else {
+                plane_step(k, std::false_type{});
+                ++k;
+            }
         }
     }
 }
 
-template <typename T, int TY, bool BATCH>
+template <typename T, int TY, bool BATCH, int CM>
 cudaError_t launch2_typed(const FusedLaunch &L, cudaStream_t s) {
     const int smem = smem2_bytes<T, TY>(L.stages);
-    auto kern = fused2_step_kernel<T, TY, BATCH>;
+    auto kern = fused2_step_kernel<T, TY, BATCH, CM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     Fused2Params P;
@@ -441,7 +472,7 @@ cudaError_t launch2_typed(const FusedLaunch &L, cudaStream_t s) {
 template <typename T, int TY>
 cudaError_t occupancy2_typed(int stages, int *n) {
     const int smem = smem2_bytes<T, TY>(stages);
-    auto kern = fused2_step_kernel<T, TY, false>;
+    auto kern = fused2_step_kernel<T, TY, false, COEF_CLASS_ID_UNIFORM_H>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, threads2<TY>(), smem);
@@ -486,9 +517,15 @@ cudaError_t launch_fused2_step(int storage, const FusedLaunch &L, cudaStream_t s
     if (L.stages < 3 || L.stages > 8) return cudaErrorInvalidValue;
     cudaError_t e = cudaErrorInvalidValue;
     if (L.step || L.launch_steps == 1)   // a batch launch (or a one-step store launch)
-        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, true>(L, s)));
+        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, true, COEF_CLASS_ANY>(L, s)));
+    else if (L.coef_class == COEF_CLASS_SCALAR)
+        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false, COEF_CLASS_SCALAR>(L, s)));
+    else if (L.coef_class == COEF_CLASS_ID_UNIFORM_H)
+        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false, COEF_CLASS_ID_UNIFORM_H>(L, s)));
+    else if (L.coef_class == COEF_CLASS_ID)
+        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false, COEF_CLASS_ID>(L, s)));
     else
-        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false>(L, s)));
+        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false, COEF_CLASS_ANY>(L, s)));
     return e;
 }
 

@@ -41,7 +41,20 @@ struct FusedLaunch {
                                // (NULL: CTA b takes tiles b, b + grid, b + 2 grid, ...)
     int launch_steps;          // two-step kernel: 2, or 1 (every tile stores its level-1 result only)
     int rows_per_warp;         // two-step kernel: 1 (k_fused2.cu) or 2 (k_fused2r.cu); 0 means 1
+    int coef_class;            // CoefClass shared by every tile (COEF_CLASS_ANY: read from each record)
 };
+// Coefficient layout shared by all tiles of a launch, so that a kernel can be compiled for it.
+enum CoefClass : int {
+    COEF_CLASS_ANY = 0,        // tiles may differ (batches of mixed members): the record's mode decides
+    COEF_CLASS_SCALAR = 1,     // COEF_SCALAR: three ce and three ch for the whole cavity
+    COEF_CLASS_ID_UNIFORM_H = 2,  // COEF_ID8 with the same ch in every cell
+    COEF_CLASS_ID = 3,         // COEF_ID8 with ce and ch per material id
+};
+inline int coef_class_of(int coef_mode, int ch_uniform) {
+    if (coef_mode == COEF_SCALAR) return COEF_CLASS_SCALAR;
+    if (coef_mode == COEF_ID8) return ch_uniform ? COEF_CLASS_ID_UNIFORM_H : COEF_CLASS_ID;
+    return COEF_CLASS_ANY;
+}
 // Shared memory bytes and max co-resident CTAs per SM for a fused configuration.
 int fused_smem_bytes(int storage, int tile_y, int stages);
 cudaError_t fused_occupancy(int storage, int tile_y, int stages, int *ctas_per_sm);
