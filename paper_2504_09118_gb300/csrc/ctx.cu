@@ -135,7 +135,10 @@ int encode_maps(fdtd_ctx *c, int set, int box_y) {
         cuuint64_t gstr[2] = {(cuuint64_t)c->pitch, (cuuint64_t)c->pitch * c->ny};
         // ids from 16 bytes left of the tile; the fourth-order kernel also needs its right halo
         cuuint32_t box[3] = {(cuuint32_t)(kTileX + (set == 2 ? 32 : 16)), (cuuint32_t)box_y, 1};
-        CUresult r = enc(&maps[12], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->id, gdim, gstr, box, estr,
+        // the two-step kernels read the PEC-coded ids when the context has them (their records then
+        // carry table_pec)
+        uint8_t *ids = set == 1 && c->id_pec ? c->id_pec : c->id;
+        CUresult r = enc(&maps[12], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, ids, gdim, gstr, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(c, FDTD_ERR_CUDA, "id tensor map encode failed (%d)", (int)r);
@@ -192,7 +195,7 @@ int launch_one(fdtd_ctx *c, int parity, int inject_us, int kind) {
     L.inject_timeout_us = inject_us;
     L.first = tl.first;
     L.rows_per_warp = s.rows_per_warp;
-    L.coef_class = coef_class_of(c->coef_mode, c->ch_uniform);
+    L.coef_class = coef_class_of(c->coef_mode, c->ch_uniform, kind == 1 && c->id_pec);
     if (kind == 0)
         CK(c, launch_fused_step(c->storage, L, c->stream));
     else if (kind == 1)
@@ -254,6 +257,27 @@ struct TupleHash {
         return (size_t)h;
     }
 };
+
+// PEC as materials.  tab: ntab entries of 8 floats (ce xyz, pad, ch xyz, pad), as folded for the fused
+// kernels.  Entry 1 + 8 m + f is material m on the faces f (bit 0: i = 0, bit 1: j = 0, bit 2: k = 0)
+// with the E coefficients of the components tangential to those faces set to zero (Ex lies in the
+// j = 0 and k = 0 faces, Ey in i = 0 and k = 0, Ez in i = 0 and j = 0), so that an update with that
+// entry keeps them at their initial zero.  Entry 0 is what a TMA box reads outside the cavity: ce = 0
+// (E there stays the 0 it was read as) and material 0's ch.
+std::vector<float> pec_table(const std::vector<float> &tab, int ntab) {
+    std::vector<float> t(8 * kMaxTable, 0.f);
+    for (int q = 0; q < 3; ++q) t[4 + q] = tab[4 + q];
+    for (int m = 0; m < ntab; ++m)
+        for (int f = 0; f < 8; ++f) {
+            float *e = &t[8 * (1 + 8 * m + f)];
+            const bool i0 = f & 1, j0 = f & 2, k0 = f & 4;
+            e[0] = (j0 || k0) ? 0.f : tab[8 * m + 0];
+            e[1] = (i0 || k0) ? 0.f : tab[8 * m + 1];
+            e[2] = (i0 || j0) ? 0.f : tab[8 * m + 2];
+            for (int q = 0; q < 3; ++q) e[4 + q] = tab[8 * m + 4 + q];
+        }
+    return t;
+}
 
 }  // namespace
 
@@ -472,6 +496,27 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
             if ((e = cudaMemcpy2D(c->id, c->pitch, ids.data(), nx, nx, (size_t)ny * nz, cudaMemcpyHostToDevice)) !=
                 cudaSuccess)
                 return cfail("id copy", e);
+            if (c->ntab <= kMaxPecMaterials) {
+                // PEC as materials for the two-step kernel: the face a cell lies on selects its table entry
+                std::vector<uint8_t> pec(ids.size());
+                for (int k = 0; k < nz; ++k)
+                    for (int j = 0; j < ny; ++j)
+                        for (int i = 0; i < nx; ++i) {
+                            const size_t q = ((size_t)k * ny + j) * nx + i;
+                            pec[q] = (uint8_t)(1 + 8 * ids[q] + (i == 0 ? 1 : 0) + (j == 0 ? 2 : 0) + (k == 0 ? 4 : 0));
+                        }
+                if ((e = dmalloc(c, (void **)&c->id_pec, c->arr_elems)) != cudaSuccess) return cfail("id alloc", e);
+                if ((e = cudaMemset(c->id_pec, 0, c->arr_elems)) != cudaSuccess) return cfail("memset", e);
+                if ((e = cudaMemcpy2D(c->id_pec, c->pitch, pec.data(), nx, nx, (size_t)ny * nz,
+                                      cudaMemcpyHostToDevice)) != cudaSuccess)
+                    return cfail("id copy", e);
+                const std::vector<float> tp = pec_table(tab, c->ntab);
+                if ((e = dmalloc(c, (void **)&c->table_pec, tp.size() * 4)) != cudaSuccess)
+                    return cfail("table alloc", e);
+                if ((e = cudaMemcpy(c->table_pec, tp.data(), tp.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+                    return cfail("table copy", e);
+                c->ntab_pec = 1 + 8 * c->ntab;
+            }
         } else {
             c->coef_mode = COEF_FULL;
             std::vector<float> row((size_t)c->pitch * ny * nz, 0.f);
@@ -524,7 +569,8 @@ void fdtd_destroy(fdtd_ctx *c) {
         pool_free(c->face_ch[q], st);
     }
     for (int a = 0; a < 6; ++a) pool_free(c->coef_full[a], st);
-    for (void *p : {(void *)c->id, (void *)c->table, (void *)c->inv_table, (void *)c->table_fused,
+    for (void *p : {(void *)c->id, (void *)c->id_pec, (void *)c->table_pec, (void *)c->table, (void *)c->inv_table,
+                    (void *)c->table_fused,
                     (void *)c->d_status, (void *)c->d_partial, (void *)c->d_out, (void *)c->d_stage,
                     (void *)c->d_max, (void *)c->d_maps, (void *)c->d_desc, (void *)c->tl[0].d,
                     (void *)c->tl[1].d, (void *)c->tl[2].d, (void *)c->tl[3].d, (void *)c->d_src_comp, (void *)c->d_src_off, (void *)c->d_wave,
@@ -654,6 +700,11 @@ int fdtd_set_fields(fdtd_ctx *c, const float *const f[6], int on_device) {
                 }
             CK(c, cudaMemcpyAsync(c->table_fused, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, c->stream));
             CK(c, cudaStreamSynchronize(c->stream));
+            if (c->table_pec) {
+                const std::vector<float> tp = pec_table(tf, c->ntab);
+                CK(c, cudaMemcpyAsync(c->table_pec, tp.data(), tp.size() * 4, cudaMemcpyHostToDevice, c->stream));
+                CK(c, cudaStreamSynchronize(c->stream));
+            }
         }
         c->tl[0].key = c->tl[1].key = c->tl[2].key = c->tl[3].key = 0;   // tile records embed the folded coefficients
         cudaStreamSynchronize(c->stream);

@@ -26,6 +26,7 @@ enum CoefMode : int { COEF_SCALAR = 0, COEF_ID8 = 1, COEF_FULL = 2 };
 
 constexpr int kNumFields = 6;      // Ex, Ey, Ez, Hx, Hy, Hz
 constexpr int kMaxTable = 256;
+constexpr int kMaxPecMaterials = (kMaxTable - 1) / 8;   // 31: 1 + 8 x materials table entries
 constexpr int kTileX = 64;         // fused kernel tile width along x (cells)
 constexpr int kMapsPerCavity = 13; // [parity 0: 6 fields][parity 1: 6 fields][id]
 constexpr int kMapSets = 4;        // box sets: one-step, two-step, fourth-order and three-step kernels

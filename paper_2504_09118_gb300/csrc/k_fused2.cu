@@ -101,6 +101,9 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
     // instance also carries the stop-clock logic, runs every plane through the general body, which
     // needs fewer registers (no spill at 16 rows)
     constexpr bool SPLIT = !BATCH && CM != COEF_CLASS_ANY;
+    // PEC-coded ids (COEF_CLASS_PEC_*): the table zeroes the E coefficients on the faces and outside the
+    // cavity (where the box read E = 0, so fma(0, curl, 0) = +0), so the steady planes need no masks
+    constexpr bool PEC_TABLE = CM == COEF_CLASS_PEC_ID_UNIFORM_H || CM == COEF_CLASS_PEC_ID;
 
     extern __shared__ __align__(128) unsigned char smem[];
     if (smem_u32(smem) & 127u) {
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
         const int nx = rec->nx, ny = rec->ny, nz = rec->nz;
         const long long pitch = rec->pitch, plane = rec->plane;
         const bool id_mode = CM == COEF_CLASS_ANY ? rec->mode == COEF_ID8 : CM >= COEF_CLASS_ID_UNIFORM_H;
-        const bool ch_uni = CM == COEF_CLASS_ANY ? rec->ch_uniform != 0 : CM != COEF_CLASS_ID;
+        const bool ch_uni = CM == COEF_CLASS_ANY ? rec->ch_uniform != 0 : CM != COEF_CLASS_ID && CM != COEF_CLASS_PEC_ID;
         const int idoff = x0 - 2 - rec->id_x0;   // lane cells start this many bytes into the id box
         if (id_mode && rec->table != tab_cached) {
             const float4 *src = rec->table;
@@ -338,14 +341,18 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 const bool inz = ST || k < nz, k1 = ST || k >= 1, j1 = gj >= 1;
                 const bool va = rowin && ina && inz, vb = rowin && inb && inz;
                 const bool i1a = gi >= 1;
-                const float2 cex = make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
-                const float2 cey = make_float2((i1a && k1) ? ca.y : 0.f, k1 ? cb.y : 0.f);
-                const float2 cez = make_float2((i1a && j1) ? ca.z : 0.f, j1 ? cb.z : 0.f);
+                constexpr bool NOMASK = ST && PEC_TABLE;
+                const float2 cex = NOMASK ? make_float2(ca.x, cb.x)
+                                          : make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
+                const float2 cey = NOMASK ? make_float2(ca.y, cb.y)
+                                          : make_float2((i1a && k1) ? ca.y : 0.f, k1 ? cb.y : 0.f);
+                const float2 cez = NOMASK ? make_float2(ca.z, cb.z)
+                                          : make_float2((i1a && j1) ? ca.z : 0.f, j1 ? cb.z : 0.f);
                 e1x = fma2(cex, sub2(sub2(h1z_, hz_ym), sub2(h1y_, h1py)), e0x);
                 e1y = fma2(cey, sub2(sub2(h1x_, h1px), sub2(h1z_, make_float2(hz_xm, h1z_.x))), e0y);
                 e1z = fma2(cez, sub2(sub2(h1y_, make_float2(hy_xm, h1y_.x)), sub2(h1x_, hx_ym)), e0z);
-                if (!va) { e1x.x = 0.f; e1y.x = 0.f; e1z.x = 0.f; }
-                if (!vb) { e1x.y = 0.f; e1y.y = 0.f; e1z.y = 0.f; }
+                if (!NOMASK && !va) { e1x.x = 0.f; e1y.x = 0.f; e1z.x = 0.f; }
+                if (!NOMASK && !vb) { e1x.y = 0.f; e1y.y = 0.f; e1z.y = 0.f; }
                 *reinterpret_cast<float2 *>(e1cur + pr * PW + pc) = e1x;
                 *reinterpret_cast<float2 *>(e1cur + PF + pr * PW + pc) = e1z;
                 // one step: (H1, E1) is the result
@@ -396,9 +403,13 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
                 coef(idprev, 0, ca, cb);
                 const int kk = k - 1;
                 const bool k1 = ST || kk >= 1, j1 = gj >= 1, i1a = gi >= 1;
-                const float2 cex = make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
-                const float2 cey = make_float2((i1a && k1) ? ca.y : 0.f, k1 ? cb.y : 0.f);
-                const float2 cez = make_float2((i1a && j1) ? ca.z : 0.f, j1 ? cb.z : 0.f);
+                constexpr bool NOMASK = ST && PEC_TABLE;
+                const float2 cex = NOMASK ? make_float2(ca.x, cb.x)
+                                          : make_float2((j1 && k1) ? ca.x : 0.f, (j1 && k1) ? cb.x : 0.f);
+                const float2 cey = NOMASK ? make_float2(ca.y, cb.y)
+                                          : make_float2((i1a && k1) ? ca.y : 0.f, k1 ? cb.y : 0.f);
+                const float2 cez = NOMASK ? make_float2(ca.z, cb.z)
+                                          : make_float2((i1a && j1) ? ca.z : 0.f, j1 ? cb.z : 0.f);
                 const float2 e2x = fma2(cex, sub2(sub2(h2z, hz_ym), sub2(h2y, h2py)), e1px);
                 const float2 e2y = fma2(cey, sub2(sub2(h2x, h2px), sub2(h2z, make_float2(h2z_xm, h2z.x))), e1py);
                 const float2 e2z = fma2(cez, sub2(sub2(h2y, make_float2(h2y_xm, h2y.x)), sub2(h2x, hx_ym)), e1pz);
@@ -524,6 +535,10 @@ cudaError_t launch_fused2_step(int storage, const FusedLaunch &L, cudaStream_t s
         FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false, COEF_CLASS_ID_UNIFORM_H>(L, s)));
     else if (L.coef_class == COEF_CLASS_ID)
         FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false, COEF_CLASS_ID>(L, s)));
+    else if (L.coef_class == COEF_CLASS_PEC_ID_UNIFORM_H)
+        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false, COEF_CLASS_PEC_ID_UNIFORM_H>(L, s)));
+    else if (L.coef_class == COEF_CLASS_PEC_ID)
+        FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false, COEF_CLASS_PEC_ID>(L, s)));
     else
         FDTD_DISPATCH2(storage, L.tile_y, e = (launch2_typed<T, TY, false, COEF_CLASS_ANY>(L, s)));
     return e;

@@ -49,10 +49,16 @@ enum CoefClass : int {
     COEF_CLASS_SCALAR = 1,     // COEF_SCALAR: three ce and three ch for the whole cavity
     COEF_CLASS_ID_UNIFORM_H = 2,  // COEF_ID8 with the same ch in every cell
     COEF_CLASS_ID = 3,         // COEF_ID8 with ce and ch per material id
+    // COEF_ID8 whose ids and table code the PEC faces (fdtd_ctx::id_pec): no per-cell masks in the kernel
+    COEF_CLASS_PEC_ID_UNIFORM_H = 4,
+    COEF_CLASS_PEC_ID = 5,
 };
-inline int coef_class_of(int coef_mode, int ch_uniform) {
+inline int coef_class_of(int coef_mode, int ch_uniform, bool pec_ids) {
     if (coef_mode == COEF_SCALAR) return COEF_CLASS_SCALAR;
-    if (coef_mode == COEF_ID8) return ch_uniform ? COEF_CLASS_ID_UNIFORM_H : COEF_CLASS_ID;
+    if (coef_mode == COEF_ID8) {
+        if (pec_ids) return ch_uniform ? COEF_CLASS_PEC_ID_UNIFORM_H : COEF_CLASS_PEC_ID;
+        return ch_uniform ? COEF_CLASS_ID_UNIFORM_H : COEF_CLASS_ID;
+    }
     return COEF_CLASS_ANY;
 }
 // Shared memory bytes and max co-resident CTAs per SM for a fused configuration.

@@ -159,8 +159,10 @@ TileRec base_rec(const fdtd_ctx *c, int parity_off, int set) {
         r.ce[q] = c->ce_s[q] * re;
         r.ch[q] = c->ch_s[q] / re;
     }
-    r.table = reinterpret_cast<const float4 *>(c->table_fused);
-    r.ntab = c->ntab;
+    // the two-step map set reads the PEC-coded ids (encode_maps) and takes their table
+    const bool pec = set == 1 && c->id_pec;
+    r.table = reinterpret_cast<const float4 *>(pec ? c->table_pec : c->table_fused);
+    r.ntab = pec ? c->ntab_pec : c->ntab;
     r.stop = LLONG_MAX;
     r.maps = c->d_maps + set * kMapsPerCavity;
     for (int f = 0; f < 6; ++f) {
