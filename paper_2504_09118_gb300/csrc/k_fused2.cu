@@ -448,13 +448,18 @@ __global__ void __launch_bounds__(threads2<TY>(), 1) fused2_step_kernel(const Fu
             }
         };
 
-        for (int k = kb; k <= kz1;) {
-            if (SPLIT && k >= ks && k < kz1) {
+        if (!SPLIT) {
 #pragma unroll 2   // consecutive planes renamed instead of copied (the carried z neighbours)
-                for (; k < kz1; ++k) plane_step(k, std::true_type{});
-            } else {
-                plane_step(k, std::false_type{});
-                ++k;
+            for (int k = kb; k <= kz1; ++k) plane_step(k, std::false_type{});
+        } else {
+            for (int k = kb; k <= kz1;) {
+                if (k >= ks && k < kz1) {
+#pragma unroll 2
+                    for (; k < kz1; ++k) plane_step(k, std::true_type{});
+                } else {
+                    plane_step(k, std::false_type{});
+                    ++k;
+                }
             }
         }
     }
