@@ -90,8 +90,8 @@ NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e nominal bandwidth (context beside the m
 # once any of them changes.
 MEASURED_TRAFFIC = {
     # ncu (one-pass metric set), 512^3 bench configuration, mean of three launches of the two-step kernel
-    # (6.77 / 6.84 / 6.85 GB; an earlier capture of the same kernel code gave a mean of 6.86 GB)
-    ("single512", "7f063af921d61b9c"): 6.821e9,
+    # (6.84 / 6.94 / 6.89 GB)
+    ("single512", "958f0b38f0fa4d27"): 6.889e9,
 }
 
 

@@ -69,7 +69,7 @@ struct fdtd_ctx {
     float *table_fused = nullptr;     // table with the storage-scale ratios folded in (fused kernel)
     std::vector<float> host_table;    // 8 floats per entry: ce xyz, pad, ch xyz, pad
     int ntab = 0;
-    // PEC as materials (two-step kernel, up to kMaxPecMaterials materials): per cell 1 + 8 id + faces
+    // PEC as materials (two-step kernel, up to kMaxPecMaterials materials): per cell 1 + id + ntab faces
     // (bit 0: i = 0, bit 1: j = 0, bit 2: k = 0), 0 outside the cavity; table_pec holds the folded
     // coefficients with the E components tangential to those faces set to zero (entry 0: ce = 0)
     uint8_t *id_pec = nullptr;

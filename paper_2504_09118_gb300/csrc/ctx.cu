@@ -259,17 +259,19 @@ struct TupleHash {
 };
 
 // PEC as materials.  tab: ntab entries of 8 floats (ce xyz, pad, ch xyz, pad), as folded for the fused
-// kernels.  Entry 1 + 8 m + f is material m on the faces f (bit 0: i = 0, bit 1: j = 0, bit 2: k = 0)
+// kernels.  Entry 1 + m + ntab f is material m on the faces f (bit 0: i = 0, bit 1: j = 0, bit 2: k = 0)
 // with the E coefficients of the components tangential to those faces set to zero (Ex lies in the
 // j = 0 and k = 0 faces, Ey in i = 0 and k = 0, Ez in i = 0 and j = 0), so that an update with that
 // entry keeps them at their initial zero.  Entry 0 is what a TMA box reads outside the cavity: ce = 0
-// (E there stays the 0 it was read as) and material 0's ch.
+// (E there stays the 0 it was read as) and material 0's ch.  Face-major order keeps the interior
+// entries (f = 0) of all materials adjacent, 32 bytes apart, as in the plain table: lanes of a warp
+// that read different materials then hit different shared-memory banks.
 std::vector<float> pec_table(const std::vector<float> &tab, int ntab) {
     std::vector<float> t(8 * kMaxTable, 0.f);
     for (int q = 0; q < 3; ++q) t[4 + q] = tab[4 + q];
     for (int m = 0; m < ntab; ++m)
         for (int f = 0; f < 8; ++f) {
-            float *e = &t[8 * (1 + 8 * m + f)];
+            float *e = &t[8 * (1 + m + ntab * f)];
             const bool i0 = f & 1, j0 = f & 2, k0 = f & 4;
             e[0] = (j0 || k0) ? 0.f : tab[8 * m + 0];
             e[1] = (i0 || k0) ? 0.f : tab[8 * m + 1];
@@ -503,7 +505,8 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
                     for (int j = 0; j < ny; ++j)
                         for (int i = 0; i < nx; ++i) {
                             const size_t q = ((size_t)k * ny + j) * nx + i;
-                            pec[q] = (uint8_t)(1 + 8 * ids[q] + (i == 0 ? 1 : 0) + (j == 0 ? 2 : 0) + (k == 0 ? 4 : 0));
+                            const int faces = (i == 0 ? 1 : 0) + (j == 0 ? 2 : 0) + (k == 0 ? 4 : 0);
+                            pec[q] = (uint8_t)(1 + ids[q] + c->ntab * faces);
                         }
                 if ((e = dmalloc(c, (void **)&c->id_pec, c->arr_elems)) != cudaSuccess) return cfail("id alloc", e);
                 if ((e = cudaMemset(c->id_pec, 0, c->arr_elems)) != cudaSuccess) return cfail("memset", e);

@@ -1,8 +1,8 @@
 """PEC as materials in the two-step kernel.
 
 A context whose coefficients compress to at most 31 material tuples also holds, for the two-step
-kernels, a second id array: 1 + 8 x id + one bit per low face the cell lies on (i = 0, j = 0, k = 0),
-and 0 outside the cavity.  Its table zeroes the E coefficients of the components tangential to those
+kernels, a second id array: 1 + id + ntab x (one bit per low face the cell lies on: i = 0, j = 0,
+k = 0), and 0 outside the cavity.  Its table zeroes the E coefficients of the components tangential to those
 faces, since tangential E vanishes on the PEC walls (Sec. 2).  Entry 0 zeroes ce, so E stays at the 0
 a box reads outside the cavity.  The kernel's steady planes then apply no per-cell masks.
 
