@@ -111,7 +111,10 @@ typedef struct fdtd_tuning {
  *   cuda_stream cudaStream_t to issue all work on (NULL = legacy default stream).
  * The library copies the coefficients (compressing them to a one-byte material
  * id per cell plus a table when at most 256 distinct per-cell tuples occur)
- * and owns all device memory until fdtd_destroy.  Fields start at zero.
+ * and owns all device memory until fdtd_destroy.  With at most 31 tuples it
+ * also keeps a second one-byte id per cell for the two-step kernels, which
+ * codes the PEC faces the cell lies on (Sec. 2: tangential E vanishes on the
+ * walls) into its table entry.  Fields start at zero.
  * Returns FDTD_ERR_UNSTABLE (and no context) when some cell has
  * sqrt(3 * ce * ch) > 1 for a co-located pair, FDTD_ERR_ARG for sizes < 1 or
  * > 32768 or non-positive coefficients.  On error *out is NULL.
@@ -263,7 +266,7 @@ FDTD_API int fdtd_get_probes(fdtd_ctx *ctx, float *out, int *nrecorded);
 /* fdtd_steps_done - steps taken since the last fdtd_set_fields (-1 for a NULL ctx). */
 FDTD_API long long fdtd_steps_done(const fdtd_ctx *ctx);
 
-/* fdtd_device_bytes - device memory the context holds (fields, ping-pong copy, coefficients). */
+/* fdtd_device_bytes - device memory the context holds (fields, ping-pong copy, coefficients, material ids). */
 FDTD_API long long fdtd_device_bytes(const fdtd_ctx *ctx);
 
 /* fdtd_destroy - free the context and its device memory (synchronises first). NULL is a no-op. */
