@@ -25,6 +25,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -91,7 +92,7 @@ NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e nominal bandwidth (context beside the m
 MEASURED_TRAFFIC = {
     # ncu (one-pass metric set), 512^3 bench configuration, mean of three launches of the two-step kernel
     # (6.84 / 6.94 / 6.89 GB)
-    ("single512", "958f0b38f0fa4d27"): 6.889e9,
+    ("single512", "810efbd94e2c72f5"): 6.889e9,
 }
 
 
@@ -121,8 +122,16 @@ def kernel_source_hash(w=None) -> str:
     headers = ["fdtd_internal.cuh", "fused_common.cuh"] + (["order4.cuh"] if (w or {}).get("order", 2) == 4 else [])
     h = hashlib.sha256()
     for name in [src] + headers:
-        h.update(open(os.path.join(ROOT, "paper_2504_09118_gb300", "csrc", name), "rb").read())
+        h.update(code_only(open(os.path.join(ROOT, "paper_2504_09118_gb300", "csrc", name)).read()).encode())
     return h.hexdigest()[:16]
+
+
+def code_only(text: str) -> str:
+    """CUDA source without comments and whitespace runs: what the compiler sees, so that a comment edit
+    keeps a measured traffic figure attached to the unchanged kernel."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
 
 
 def measured_peaks():

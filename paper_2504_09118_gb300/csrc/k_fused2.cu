@@ -20,9 +20,19 @@
 //
 // Per z-plane iteration j: [H1(j)] bar [E1(j)] [H2(j-1)] bar [E2(j-1) + stores], the last phase
 // running into the next plane's H1 (they share no data); H2(j-1) reads no E1(j) of another warp, so
-// E1 and H2 need no barrier between them.  A producer warp streams plane units (six field boxes with a 2-cell halo in y, id box) through an
-// S-slot TMA ring exactly as the one-step kernel does; waits are bounded and a shared
-// abort flag ends the CTA together (see k_fused.cu).
+// E1 and H2 need no barrier between them.  A producer warp streams plane units (six field boxes with
+// a 2-cell halo in y, id box) through an S-slot TMA ring exactly as the one-step kernel does; waits
+// are bounded and a shared abort flag ends the CTA together (see k_fused.cu).
+//
+// The plane iteration is one body compiled twice.  The general instance tests, per plane, which
+// phases run and which PEC masks apply (a tile's first planes and its last one); the steady instance
+// runs the planes in between, where neither depends on the plane.  With PEC-coded material ids (the
+// faces a cell lies on select a table entry whose tangential E coefficients are zero, and entry 0,
+// read outside the cavity, has ce = 0) the steady planes apply no masks at all.  Every value keeps
+// the operation sequence of the one-step kernel: a masked coefficient there is the same zero in the
+// same fused multiply-add.  The kernel is compiled per coefficient class (CoefClass), so a single
+// cavity's launch tests its coefficient layout nowhere; batches keep a runtime class and the general
+// body.
 #include <type_traits>
 
 #include "fused_common.cuh"

@@ -1,7 +1,7 @@
 """bench.py's contract on the CPU: the reference arm (the FP64 oracle timed on the host cores) prints one
 JSON line with the keys the contract names, other ranks print nothing, workloads it does not cover get an
-`unavailable` line; and the clock-sampler summary reads nvidia-smi's CSV (median SM clock, throttle
-reasons) correctly."""
+`unavailable` line; the clock-sampler summary reads nvidia-smi's CSV (median SM clock, throttle
+reasons) correctly; and the key of the measured-traffic table follows the kernel's code, not its comments."""
 import json
 import os
 import subprocess
@@ -66,3 +66,13 @@ def test_clock_summary(tmp_path):
     assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and s["sm_mhz"] == 1500.0
     p.write_text("")
     assert bench.ClockSampler(0, str(p)).summary()["reasons"] == ["no samples"]
+
+
+def test_traffic_key_ignores_comments():
+    """The measured DRAM traffic is keyed on the kernel's code, not its comments or layout."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f(int x) {  // add one\n    return x + 1; /* the\n result */ }\n"
+    b = "// header\nint f(int x) {\n  return x + 1;\n}\n"
+    assert bench.code_only(a) == bench.code_only(b) == "int f(int x) { return x + 1; }"
+    assert bench.code_only("return x + 2;") != bench.code_only("return x + 1;")
