@@ -456,6 +456,23 @@ FDTD_API int fdtd_debug_fail_alloc(int after);
 FDTD_API int fdtd_debug_tile_plan(long long cols, int nz, int ctas, int prologue, int zchunk, int *chunks,
                                   int max_chunks, int *nchunks, long long *makespan, int *cta_of_tile);
 
+/* fdtd_debug_pec_code, fdtd_debug_pec_table - host only (no GPU, no context): the PEC-coded material
+ * ids that the two-step kernels read for contexts with 1 <= ntab <= 31 material tuples.  Tangential E
+ * vanishes on the PEC walls (Sec. 2); these write that condition as materials, so that the kernels'
+ * inner loop applies no per-cell masks.
+ *   fdtd_debug_pec_code   *code = the coded id of a cell of material id (0 <= id < ntab) at cell
+ *                         (i, j, k), i, j, k >= 0: 1 + id + ntab x faces, where faces has bit 0 set
+ *                         for i = 0, bit 1 for j = 0 and bit 2 for k = 0.  Cells outside the cavity
+ *                         read code 0.
+ *   fdtd_debug_pec_table  tab: ntab entries of 8 floats (ce x, y, z, pad, ch x, y, z, pad), caller-owned.
+ *                         out: 8 (1 + 8 ntab) floats (caller-owned) receive the coded table.  Entry 0
+ *                         has ce = 0 and material 0's ch.  Entry 1 + m + ntab f has material m's
+ *                         coefficients, with ce set to 0 for each E component tangential to a face in f
+ *                         (x to the j = 0 and k = 0 faces, y to i = 0 and k = 0, z to i = 0 and j = 0).
+ * Both return FDTD_ERR_ARG for NULL pointers or arguments outside those ranges. */
+FDTD_API int fdtd_debug_pec_code(int ntab, int id, int i, int j, int k, int *code);
+FDTD_API int fdtd_debug_pec_table(const float *tab, int ntab, float *out);
+
 /*
  * fdtd_energy_static - the same energy W as fdtd_energy (second-order scheme), computed from
  * caller-owned device arrays by a path that allocates no device memory.  (The paper has no

@@ -33,7 +33,8 @@ EXPORTS = (
     "fdtd_debug_inject_timeout", "fdtd_version", "fdtd_energy_static", "fdtd_batch_set_steps",
     "fdtd_batch_steps_done", "fdtd_autotune", "fdtd_batch_autotune", "fdtd_set_sources", "fdtd_set_probes",
     "fdtd_get_probes", "fdtd_set_order", "fdtd_get_order", "fdtd_batch_retune", "fdtd_prefetch_fields",
-    "fdtd_set_fields_prefetched", "fdtd_debug_fail_alloc", "fdtd_debug_tile_plan",
+    "fdtd_set_fields_prefetched", "fdtd_debug_fail_alloc", "fdtd_debug_tile_plan", "fdtd_debug_pec_code",
+    "fdtd_debug_pec_table",
     "fdtd_create_slab", "fdtd_slab_info", "fdtd_slab_halo_bytes", "fdtd_slab_export", "fdtd_slab_import",
     "fdtd_slab_exchange", "fdtd_slab_energy", "fdtd_slab_divergence_sq", "fdtd_set_storage_scales",
     "fdtd_storage_scale_of",
@@ -114,6 +115,8 @@ def lib() -> ctypes.CDLL:
             L.fdtd_prefetch_fields.argtypes = [vp, vp]
             L.fdtd_debug_fail_alloc.argtypes = [i]
             L.fdtd_debug_tile_plan.argtypes = [ll, i, i, i, i, vp, i, ctypes.POINTER(i), ctypes.POINTER(ll), vp]
+            L.fdtd_debug_pec_code.argtypes = [i, i, i, i, i, ctypes.POINTER(i)]
+            L.fdtd_debug_pec_table.argtypes = [vp, i, vp]
             L.fdtd_set_fields_prefetched.argtypes = [vp]
             L.fdtd_batch_retune.argtypes = [vp, i, ctypes.POINTER(fdtd_tuning), ctypes.POINTER(d),
                                             ctypes.POINTER(i)]
@@ -343,6 +346,25 @@ def fdtd_debug_tile_plan(cols: int, nz: int, ctas: int, prologue: int, zchunk: i
         if rc != FDTD_OK:
             raise FdtdError(rc, "fdtd_debug_tile_plan: invalid arguments")
     return [int(x) for x in chunks[:n.value]], int(ms.value), cta
+
+
+def fdtd_debug_pec_code(ntab: int, mat: int, i: int, j: int, k: int) -> int:
+    """Host-only: the PEC-coded id the two-step kernels read for a cell of material `mat` at (i, j, k)."""
+    code = ctypes.c_int(0)
+    rc = lib().fdtd_debug_pec_code(int(ntab), int(mat), int(i), int(j), int(k), ctypes.byref(code))
+    if rc != FDTD_OK:
+        raise FdtdError(rc, "fdtd_debug_pec_code: invalid arguments")
+    return int(code.value)
+
+
+def fdtd_debug_pec_table(tab) -> np.ndarray:
+    """Host-only: the PEC-coded table built from tab (ntab x 8 floats), shape (1 + 8 ntab, 8)."""
+    t = np.ascontiguousarray(np.asarray(tab, np.float32).reshape(-1, 8))
+    out = np.zeros((1 + 8 * len(t), 8), np.float32)
+    rc = lib().fdtd_debug_pec_table(t.ctypes.data, len(t), out.ctypes.data)
+    if rc != FDTD_OK:
+        raise FdtdError(rc, "fdtd_debug_pec_table: invalid arguments")
+    return out
 
 
 def fdtd_set_fields_prefetched(ctx) -> None:

@@ -266,6 +266,12 @@ struct TupleHash {
 // (E there stays the 0 it was read as) and material 0's ch.  Face-major order keeps the interior
 // entries (f = 0) of all materials adjacent, 32 bytes apart, as in the plain table: lanes of a warp
 // that read different materials then hit different shared-memory banks.
+// PEC-coded id of a cell of material id on the faces it lies on (entry 1 + id + ntab f of pec_table).
+int pec_code(int id, int ntab, int i, int j, int k) {
+    const int faces = (i == 0 ? 1 : 0) + (j == 0 ? 2 : 0) + (k == 0 ? 4 : 0);
+    return 1 + id + ntab * faces;
+}
+
 std::vector<float> pec_table(const std::vector<float> &tab, int ntab) {
     std::vector<float> t(8 * kMaxTable, 0.f);
     for (int q = 0; q < 3; ++q) t[4 + q] = tab[4 + q];
@@ -293,6 +299,20 @@ using namespace fdtd;
 extern "C" {
 
 const char *fdtd_version(void) { return "fdtd-gb300 0.1 (sm_103a)"; }
+
+int fdtd_debug_pec_code(int ntab, int id, int i, int j, int k, int *code) {
+    if (!code || ntab < 1 || ntab > kMaxPecMaterials || id < 0 || id >= ntab || i < 0 || j < 0 || k < 0)
+        return FDTD_ERR_ARG;
+    *code = pec_code(id, ntab, i, j, k);
+    return FDTD_OK;
+}
+
+int fdtd_debug_pec_table(const float *tab, int ntab, float *out) {
+    if (!tab || !out || ntab < 1 || ntab > kMaxPecMaterials) return FDTD_ERR_ARG;
+    const std::vector<float> t = pec_table(std::vector<float>(tab, tab + 8 * ntab), ntab);
+    std::copy(t.begin(), t.begin() + 8 * (1 + 8 * ntab), out);
+    return FDTD_OK;
+}
 
 const char *fdtd_last_error(const fdtd_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
@@ -505,8 +525,7 @@ int fdtd_create(fdtd_ctx **out, int nx, int ny, int nz, double dt, double dx, co
                     for (int j = 0; j < ny; ++j)
                         for (int i = 0; i < nx; ++i) {
                             const size_t q = ((size_t)k * ny + j) * nx + i;
-                            const int faces = (i == 0 ? 1 : 0) + (j == 0 ? 2 : 0) + (k == 0 ? 4 : 0);
-                            pec[q] = (uint8_t)(1 + ids[q] + c->ntab * faces);
+                            pec[q] = (uint8_t)pec_code(ids[q], c->ntab, i, j, k);
                         }
                 if ((e = dmalloc(c, (void **)&c->id_pec, c->arr_elems)) != cudaSuccess) return cfail("id alloc", e);
                 if ((e = cudaMemset(c->id_pec, 0, c->arr_elems)) != cudaSuccess) return cfail("memset", e);
