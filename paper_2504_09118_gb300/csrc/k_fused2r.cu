@@ -15,6 +15,9 @@
 //   * the E coefficients of a level-1 E update (looked up by material id and masked at the PEC faces)
 //     are kept in registers for the level-2 E update of the same plane one iteration later.
 // Rows 0 .. TY + 2 are needed (TY even: the upper row of the last warp, TY + 3, is idle).
+// It reads the two-step map set, so a context with PEC-coded material ids hands it those ids and their
+// table (the tangential E coefficients on the faces already zero); its own masks then multiply the
+// same zeros, and the results stay those of the one-row kernel.
 //
 // Per z-plane iteration k: [H1(k)] bar [E1(k)] [H2(k-1)] bar [E2(k-1) + stores], as in k_fused2.cu; the
 // hazards on the shared planes are covered by the same two barriers (a plane written in one phase is
